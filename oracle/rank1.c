@@ -11,18 +11,18 @@
  * Problem: diag(d) + z z^T with d ascending (length m).
  *   1. deflation, Remark 4.1 (|z_k| < tau first; then a left-to-right Givens
  *      scan over the survivors with the test |(d_a-d_b) z_a z_b| < (z_a^2+z_b^2) tau);
- *   2. secular roots in shifted form, Section 4.2 (eq. (4.10)-(4.12)):
+ *   2. secular roots in shifted form, Section 4.2 (eqs. (4.13), (4.14), (4.17)):
  *      origin d_k or d_{k+1} chosen by the sign of f at the midpoint,
  *      gap eta = lambda - d_K; the sums are split into the triangular parts
- *      psi (j <= k) and phi (j > k) of eq. (4.5)/(4.7);
+ *      psi (j <= k) and phi (j > k) of eqs. (4.7)-(4.10);
  *      mode 0 = bisection of g_K to adjacent doubles ("exact"),
  *      mode 1 = middle-way modified Newton (Section 4.1.3, following Li's
- *      rational interpolation) with the stopping test eq. (4.8) and a
+ *      rational interpolation) with the stopping test eq. (4.12) and a
  *      bisection safeguard;
- *   3. Loewner's formula eq. (4.15) for zhat (paired ratios, shifted differences);
- *   4. normalisation b, eq. (4.18), with shifted differences eq. (4.19);
+ *   3. Loewner's formula eq. (4.23) for zhat (paired ratios, shifted differences);
+ *   4. normalisation b, eq. (4.27), with shifted differences eq. (4.28);
  *   5. the new eigenvalues sorted by (value, input index).
- * Plus the application of the Cauchy-like factor eq. (4.20) and its
+ * Plus the application of the Cauchy-like factor eqs. (4.26)/(4.29) and its
  * transpose (Algorithms 3 and 4).
  */
 #include <math.h>
@@ -60,7 +60,7 @@ int orc_deflate(int m, const double *d, const double *z, double tau,
             double lhs = fabs((dd[a] - dd[b]) * za * zb);
             double rhs = (za * za + zb * zb) * tau;
             if (lhs < rhs) {
-                double rho = hypot(za, zb);
+                double rho = sqrt(za * za + zb * zb);
                 double c = zb / rho, s = za / rho;
                 double da = dd[a], db = dd[b];
                 dd[a] = c * c * da + s * s * db;
@@ -192,7 +192,7 @@ int orc_secular_root(int m, const double *d, const double *w, int k, int mode,
         double psi, phi, dpsi, dphi;
         double f = geval(m, d, w, K, k, y, &psi, &phi, &dpsi, &dphi);
         sweeps++;
-        if (fabs(f) < eps_tol * (1.0 + fabs(psi) + fabs(phi))) {      /* eq. (4.8) */
+        if (fabs(f) < eps_tol * (1.0 + fabs(psi) + fabs(phi))) {      /* eq. (4.12) */
             *Kout = K; *etaout = y; if (iters) *iters = sweeps;
             return 0;
         }
@@ -249,7 +249,7 @@ int orc_secular_all(int m, const double *d, const double *z, int mode, double st
 }
 
 /* ------------------------------------------------------------------ */
-/* 3. Loewner's formula, eq. (4.15), paired as in Gu & Eisenstat         */
+/* 3. Loewner's formula, eq. (4.23), paired as in Gu & Eisenstat         */
 /* ------------------------------------------------------------------ */
 /* lambda_j - d_i evaluated as (d_{K_j} - d_i) + eta_j */
 void orc_lowner(int m, const double *d, const double *z, const int *K, const double *eta,
@@ -269,7 +269,7 @@ void orc_lowner(int m, const double *d, const double *z, const int *K, const dou
 }
 
 /* ------------------------------------------------------------------ */
-/* 4. b_j = (sum_i vhat_i^2 / ((d_i - d_{K_j}) - eta_j)^2)^(-1/2), eq. (4.18) */
+/* 4. b_j = (sum_i vhat_i^2 / ((d_i - d_{K_j}) - eta_j)^2)^(-1/2), eq. (4.27) */
 /* ------------------------------------------------------------------ */
 void orc_bnorm(int m, const double *d, const double *vhat, const int *K, const double *eta,
                double *b)
