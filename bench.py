@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Benchmark of the SuperDC conquering-stage hot path on GB300.
+
+Workload (one "step"): the batched secular solve of 4096 independent
+rank-one problems diag(d) + z z^T, m ~ U{32..2048}, poles U[0,1] with 10% in
+clusters of width 1e-10, z ~ N(0,1), rho = 1, tau = 1e-12: deflation, all
+shifted secular roots, Loewner zhat, b and the sorted eigenvalues -- the
+whole rank-one pipeline of the conquering stage, in one C-ABI call.
+
+Metric: secular roots per second (all roots of the batch / device time of
+the step).  Inputs are resident in HBM when the timed region starts; the L2
+is flushed (256 MiB write) before every timed step.  ``e2e`` repeats the
+measurement through the host-buffer API (pinned host -> device copies of the
+inputs and device -> host copies of the results inside the timed region).
+
+Multi-GPU: the path has no exchange step; N ranks run N independent replicas
+(weak scaling), ``value`` = roots of all ranks / max-over-ranks time.
+
+``--impl reference`` times the CPU oracle (plain C + OpenMP, FP64) on a
+bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HSS eigendecomp time at n=131072; secular roots/s; FP64-pipe % of peak"
+WORKLOAD = ("batched secular solve: 4096 independent rank-one problems, m~U{32..2048}, "
+            "poles U[0,1] with 10% in clusters of width 1e-10, z~N(0,1), rho=1, tau=1e-12; "
+            "deflation + shifted roots + Loewner zhat + b + sorted eigenvalues")
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 (no measured figure in the peaks file)
+SECULAR_FLOPS_PER_INTERACTION = 7.0   # 2 sub, 1 recip, 1 mul, 1 add, 1 fma (2)
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _fp64_peak():
+    pk = _peaks()
+    if "fp64_tflops" in pk:
+        return float(pk["fp64_tflops"]), "measured (MEASURED_PEAKS.json fp64_tflops)"
+    probe = os.path.join(ROOT, "profiles", "fp64_peak.json")
+    if os.path.exists(probe):
+        try:
+            v = json.load(open(probe))
+            return float(v["fp64_tflops"]), "measured by the DFMA probe (profiles/fp64_peak.json)"
+        except Exception:
+            pass
+    return FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 (1.25 TFLOP/s)"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(batch, budget_s=20.0, tau=1e-12):
+    """The oracle, as it stands, on a bounded prefix of the workload's problems."""
+    from oracle import rank1 as r1
+    t0 = time.perf_counter()
+    roots = 0
+    nprob = 0
+    for p in range(batch.nprob):
+        d, z = batch.problem(p)
+        r1.rank1_step(d, z, tau, mode=1)
+        roots += len(d)
+        nprob += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    return {"value": roots / dt, "unit": "roots/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of the 4096 problems (%d roots), oracle newton mode, %.1f s" % (nprob, roots, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2108_04209_gb300 import inputs
+    batch = inputs.cfg_secular_4096()
+    from oracle import rank1 as r1
+    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    nsample = 48
+    vals, times = [], []
+
+    def step(off):
+        roots = 0
+        t0 = time.perf_counter()
+        for p in range(off, off + nsample):
+            d, z = batch.problem(p % batch.nprob)
+            r1.rank1_step(d, z, 1e-12, mode=1)
+            roots += len(d)
+        return roots, time.perf_counter() - t0
+
+    for w in range(args.warmup):
+        step(w * nsample)
+    tot_r, tot_t = 0, 0.0
+    for s in range(args.steps):
+        r, t = step((args.warmup + s) * nsample)
+        tot_r += r
+        tot_t += t
+    v = tot_r / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "roots/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "roots/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d consecutive problems per step of the 4096-problem workload" % nsample},
+            "e2e": {"value": v, "unit": "roots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2108_04209_gb300 as sdc
+    from paper_2108_04209_gb300 import _lib as L, inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    batch = inputs.cfg_secular_4096()
+    total = int(batch.offsets[-1])
+    offs = torch.from_numpy(batch.offsets).to(dev)
+    d = torch.from_numpy(batch.d).to(dev)
+    z = torch.from_numpy(batch.z).to(dev)
+    opts = sdc.default_opts(tau=1e-12)
+    out = sdc.alloc_rank1_out(batch.nprob, total, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    lib = L.lib()
+
+    for _ in range(max(3, args.warmup)):
+        sdc.secular_batched(offs, d, z, 1.0, opts, out=out, check=False)
+    sdc.check_status(out["status"], "warmup")
+    torch.cuda.synchronize()
+
+    clk = Clocks(local)
+    lib.superdc_profile_reset()
+    lib.superdc_profile_enable(1)
+    st = torch.cuda.current_stream()
+    evs = []
+    barrier()
+    clk.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sdc.secular_batched(offs, d, z, 1.0, opts, out=out, check=False)
+        e1.record(st)
+        evs.append((e0, e1))
+    barrier()
+    clocks = clk.stop()
+    lib.superdc_profile_enable(0)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    sdc.check_status(out["status"], "timed")
+    kern = {}
+    import ctypes
+    for name in ("deflate", "tiles", "secular", "lowner", "bnorm", "merge"):
+        n_ = ctypes.c_int64(0)
+        t_ = ctypes.c_double(0.0)
+        lib.superdc_profile_read(name.encode(), ctypes.byref(n_), ctypes.byref(t_))
+        kern[name] = (n_.value, t_.value)
+    launches = sum(v[0] for v in kern.values())
+
+    # algorithmic work of the secular kernel (from the run's own sweep counts)
+    mk = out["mk"].cpu().numpy().astype(np.float64)
+    sw = out["sweeps"].cpu().numpy().astype(np.float64)
+    per_prob_sweeps = np.add.reduceat(sw, batch.offsets[:-1]) if total else np.zeros(0)
+    interactions = float(np.sum(mk * per_prob_sweeps))
+    sec_ms = kern["secular"][1] / max(1, kern["secular"][0])
+    achieved = SECULAR_FLOPS_PER_INTERACTION * interactions / (sec_ms * 1e-3) / 1e12
+    peak, peak_src = _fp64_peak()
+
+    # e2e: host buffers, copies inside the timed region
+    h_off = torch.from_numpy(batch.offsets).pin_memory()
+    h_d = torch.from_numpy(batch.d).pin_memory()
+    h_z = torch.from_numpy(batch.z).pin_memory()
+    fields = ("lam", "eta", "org", "vhat", "bnorm")
+    for _ in range(2):
+        sdc.secular_batched_host(h_off, h_d, h_z, 1.0, opts, fields=fields)
+    barrier()
+    e2e_t = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = sdc.secular_batched_host(h_off, h_d, h_z, 1.0, opts, fields=fields)
+        e2e_t += time.perf_counter() - t0
+    h2d = h_off.numel() * 8 + h_d.numel() * 8 + h_z.numel() * 8
+    d2h = sum(v.numel() * v.element_size() for v in res.values()) + 4
+
+    # max over ranks
+    tmax = ms
+    e2e_max = e2e_t
+    if pg is not None:
+        tt = torch.tensor([ms, e2e_t], dtype=torch.float64, device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        tmax, e2e_max = float(tt[0]), float(tt[1])
+    roots_all = float(total) * args.steps * ws
+    value = roots_all / (tmax * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "roots/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nprob": batch.nprob, "total_roots": total,
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "gpu_launches": int(launches),
+            "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kern.items()},
+            "roofline": {"bound": "alu", "kernel": "k_secular", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s (FP64)", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_src,
+                         "algorithmic": "%.0f flops/interaction x %.4g interactions per launch" % (
+                             SECULAR_FLOPS_PER_INTERACTION, interactions)},
+            "secular_sweeps_mean": float(sw[sw > 0].mean()) if np.any(sw > 0) else 0.0,
+            "e2e": {"value": roots_all / e2e_max, "unit": "roots/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(batch, budget_s=args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -9,9 +9,9 @@ in ``paper_2108_04209_gb300``; the two meet only through the seeded inputs of
 
 Modules
   * ``rank1.c``   -- deflation (Remark 4.1), shifted secular roots
-                    (Section 4.2, eqs. (4.10)-(4.12); stopping test eq. (4.8)),
-                    Loewner zhat (eq. (4.15)), b (eq. (4.18)), Cauchy-like factor
-                    application (eq. (4.20)), dense cyclic Jacobi;
+                    (Section 4.2, eqs. (4.13), (4.14), (4.17); stopping test eq. (4.12)),
+                    Loewner zhat (eq. (4.23)), b (eq. (4.27)), Cauchy-like factor
+                    application (eqs. (4.26), (4.29)), dense cyclic Jacobi;
   * ``rank1.py``  -- one complete rank-one step with its factor object;
   * ``superdc.py``-- Algorithm 1 (dividing), Algorithm 3 (conquering),
                     Algorithm 4 (superdcmv);

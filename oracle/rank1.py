@@ -4,12 +4,12 @@ diag(d) + rho z z^T of the conquering stage, and its Cauchy-like factor.
 Step order (Algorithm 3, inner loop; readings of the paper's silences are
 listed in the module docstrings of ``rank1.c``):
   1. deflation, Remark 4.1 -> rotations G, kept set, deflated values;
-  2. shifted secular roots (Algorithm 2; eq. (4.10)-(4.12));
-  3. Loewner zhat, eq. (4.15);  4. b, eq. (4.18);
+  2. shifted secular roots (Algorithm 2; eqs. (4.13), (4.14), (4.17));
+  3. Loewner zhat, eq. (4.23);  4. b, eq. (4.27);
   5. the new eigenvalues: kept roots and deflated values sorted by
      (value, input index) -> the next step's poles.
 The factor is Qhat = G^T [C (+) I] Pi^T with C the Cauchy-like matrix of
-eq. (4.20) on the kept set and Pi the sort of step 5.
+eq. (4.26) on the kept set and Pi the sort of step 5.
 """
 import ctypes
 import dataclasses

@@ -1,16 +1,16 @@
 """CPU ORACLE (test infrastructure): SuperDC dividing and conquering stages.
 
-* ``divide``   -- Algorithm 1 with the balanced dividing of eq. (3.6)/(3.7)
-                  (or eq. (3.8) when colsize(B) > rowsize(B)), generator
+* ``divide``   -- Algorithm 1 with the balanced dividing of eqs. (3.11)/(3.12)
+                  (or eq. (3.15) when colsize(B) > rowsize(B)), generator
                   updates by Lemma 2.1 (``updhss``), Z_i formed bottom-up.
 * ``conquer``  -- Algorithm 3: dense leaf eigendecompositions (cyclic
                   Jacobi), Zhat_i = diag(Q_c1^T, Q_c2^T) Z_i through
-                  ``superdcmv`` (eq. (2.6)), the sort P_i, then r rank-one
+                  ``superdcmv`` (eq. (2.8)), the sort P_i, then r rank-one
                   steps, each followed by the transpose of its factor applied
                   to the remaining columns.
 * ``superdcmv``-- Algorithm 4: y = Q_i x or Q_i^T x from the stored factors,
                   with Q_p = diag(Q_c1, Q_c2) P_p^T Qhat_p^(1) ... Qhat_p^(r)
-                  (eq. (4.22), Lemma 4.1).
+                  (eq. (4.32), Lemma 4.1).
 """
 import dataclasses
 
@@ -39,7 +39,7 @@ class Divided:
     Bt: dict          # node -> updated B (left children)
     beta: dict        # non-leaf node -> ||B_c1||_2 used at that node
     Z: dict           # non-leaf node -> Z_i (m_i x r)
-    swapped: dict     # non-leaf node -> True if eq. (3.8) was used
+    swapped: dict     # non-leaf node -> True if eq. (3.15) was used
 
 
 def divide(h) -> Divided:

@@ -1,0 +1,88 @@
+"""ctypes binding of libsuperdc.so (argument marshalling only).
+
+Every numeric step runs in the CUDA library; this module passes raw device
+pointers (``tensor.data_ptr()``) and the current CUDA stream.  There is no
+CPU fallback: if the library cannot be built or loaded, or no CUDA device is
+present, calls raise.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+c_double, c_int32, c_int64, c_void_p = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+STATUS = {0: "SUPERDC_OK", 1: "SUPERDC_ERR_ARG", 2: "SUPERDC_ERR_CUDA", 3: "SUPERDC_ERR_OOM",
+          4: "SUPERDC_ERR_NONFINITE", 5: "SUPERDC_ERR_NOCONV", 6: "SUPERDC_ERR_STATE"}
+DEV_NONFINITE, DEV_NOCONV, DEV_INDEX = 1, 2, 4
+
+
+class SuperDCError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__("%s%s" % (STATUS.get(code, "status %d" % code), (" in " + where) if where else ""))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tau", c_double), ("stop_c", c_double), ("max_iter", c_int32),
+                ("tile_roots", c_int32), ("batching", c_int32), ("reserved", c_int32)]
+
+
+class Rank1Out(ctypes.Structure):
+    _fields_ = [(n, c_void_p) for n in ("lam", "dk", "zk", "eta", "vhat", "bnorm", "org", "src", "perm",
+                                         "giv_ab", "giv_cs", "mk", "ngiv", "sweeps", "status")]
+
+
+_lib = None
+
+
+def lib():
+    """Load (building in-tree if needed) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libsuperdc.so missing at %s" % path)
+        L = ctypes.CDLL(path)
+        L.superdc_opts_default.argtypes = [ctypes.POINTER(Opts)]
+        L.superdc_opts_default.restype = c_int32
+        L.superdc_status_string.argtypes = [c_int32]
+        L.superdc_status_string.restype = ctypes.c_char_p
+        L.superdc_secular_batched.argtypes = [c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_double,
+                                              ctypes.POINTER(Opts), ctypes.POINTER(Rank1Out), c_void_p]
+        L.superdc_secular_batched.restype = c_int32
+        L.superdc_profile_enable.argtypes = [c_int32]
+        L.superdc_profile_enable.restype = c_int32
+        L.superdc_profile_reset.argtypes = []
+        L.superdc_profile_reset.restype = c_int32
+        L.superdc_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_double)]
+        L.superdc_profile_read.restype = c_int32
+        _lib = L
+    return _lib
+
+
+def check(code, where=""):
+    if code != 0:
+        raise SuperDCError(code, where)
+
+
+def default_opts(**kw):
+    o = Opts()
+    check(lib().superdc_opts_default(ctypes.byref(o)), "superdc_opts_default")
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def exported_symbols():
+    """Names declared in include/superdc.h that the shared library must export."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    names = []
+    for f in sorted(os.listdir(hdr)):
+        if f.endswith(".h"):
+            txt = open(os.path.join(hdr, f)).read()
+            names += re.findall(r"^\s*(?:superdc_status|const char \*|void|superdc_\w+ \*?)\s*\*?\s*(superdc_\w+)\s*\(",
+                                txt, re.M)
+    return sorted(set(names))

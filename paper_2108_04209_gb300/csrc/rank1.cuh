@@ -1,0 +1,25 @@
+// Internal interface of the batched rank-one step (see rank1.cu).
+#pragma once
+#include "common.cuh"
+
+// Device output arrays of one batched rank-one step (layout as documented
+// for superdc_rank1_out in superdc.h), plus library scratch.
+struct R1Out {
+    double *lam, *dk, *zk, *eta, *vhat, *bnorm;
+    int32_t *org, *src, *perm, *giv_ab;
+    double *giv_cs;
+    int32_t *mk, *ngiv, *sweeps, *status;
+    double *dorg;   // d_{K} of every kept root (scratch or stored), total entries
+    double *wsum;   // sum of kept z^2 per problem (scratch), nprob entries
+};
+
+struct R1Args {
+    int64_t nprob, total;
+    const int64_t *off;     // device, nprob+1
+    const double *d, *z;    // device inputs
+    double sqrt_rho, tau, stop_c;
+    int max_iter, tile_roots;
+    R1Out o;
+};
+
+superdc_status r1_run(const R1Args &a, cudaStream_t st);

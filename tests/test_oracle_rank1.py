@@ -74,7 +74,7 @@ def test_roots_gaps_vs_mpmath(mode, seed, cluster):
 def test_exact_mode_backward_error():
     """Bisection to adjacent doubles: at the returned gap the true g_K (50
     digits) is within the rounding level of one FP64 evaluation, i.e. well
-    inside the stopping test of eq. (4.8)."""
+    inside the stopping test of eq. (4.12)."""
     d, z = rand_problem(40, 7, cluster=True)
     f = r1.rank1_step(d, z, tau=1e-14, mode=0)
     w = f.zk ** 2
@@ -93,7 +93,7 @@ def test_exact_mode_backward_error():
 def test_zhat_and_b_vs_mpmath(mode):
     d, z = rand_problem(20, 11)
     f = r1.rank1_step(d, z, tau=1e-14, mode=mode)
-    # Loewner's formula reproduces |z| when the roots are exact (eq. (4.15)); P6
+    # Loewner's formula reproduces |z| when the roots are exact (eq. (4.23))
     assert np.allclose(np.abs(f.vhat), np.abs(f.zk), rtol=1e-10, atol=0)
     assert np.all(np.sign(f.vhat) == np.sign(f.zk))
     lam_star = mp_roots(f.dk, f.zk)

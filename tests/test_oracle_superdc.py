@@ -32,7 +32,7 @@ def test_dense_assembly_matches_generators():
 
 
 def _reassemble(h, dv):
-    """diag(Dhat_leaves) + sum over nodes of the Z_p Z_p^T blocks (eq. (2.3) applied recursively)."""
+    """diag(Dhat_leaves) + sum over nodes of the Z_p Z_p^T blocks (eq. (2.4) applied recursively)."""
     t = h.tree
     A = np.zeros((t.n, t.n))
     for i in t.leaves:
@@ -54,7 +54,7 @@ def test_dividing_reassembles_A(bscale):
 
 
 def test_prop32_norm_bound():
-    # Proposition 3.2: after balanced dividing ||B~_k|| <= 2^l beta
+    # Proposition 3.2, eq. (3.13): after balanced dividing ||B~_k|| <= 2^l beta
     h = inputs.hss_random(1024, 32, 4, seed=1, bscale=1e3)
     beta = max(np.linalg.norm(h.B[i], 2) for i in range(h.tree.nnodes))
     dv = sd.divide(h)
@@ -83,7 +83,7 @@ def test_small_hss_vs_dense(mode):
 
 
 def test_brute_force_dense_jacobi():
-    """P1: full SuperDC vs a brute-force dense cyclic Jacobi of the assembled matrix."""
+    """Full SuperDC vs a brute-force dense cyclic Jacobi of the assembled matrix."""
     h = inputs.hss_random(128, 16, 3, seed=12)
     A = dense.dense_from_hss(h)
     lj, _ = sd.jacobi_eig(A)
