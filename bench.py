@@ -47,17 +47,19 @@ def _peaks():
 
 
 def _fp64_peak():
+    """FP64 peak: the peaks file if it has one, else the DFMA probe run live on
+    this GPU (paper_2108_04209_gb300.probe), else the nominal figure."""
     pk = _peaks()
     if "fp64_tflops" in pk:
         return float(pk["fp64_tflops"]), "measured (MEASURED_PEAKS.json fp64_tflops)"
-    probe = os.path.join(ROOT, "profiles", "fp64_peak.json")
-    if os.path.exists(probe):
-        try:
-            v = json.load(open(probe))
-            return float(v["fp64_tflops"]), "measured by the DFMA probe (profiles/fp64_peak.json)"
-        except Exception:
-            pass
-    return FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 (1.25 TFLOP/s)"
+    try:
+        from paper_2108_04209_gb300.probe import build_probe
+        r = subprocess.run([build_probe()], capture_output=True, text=True, timeout=120)
+        v = json.loads(r.stdout.strip().splitlines()[-1])
+        return float(v["fp64_tflops"]), "measured: DFMA probe run live by bench.py (%.3f DFMA/clk/SM)" % (
+            v["dfma_per_clk_per_sm"])
+    except Exception:
+        return FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 (1.25 TFLOP/s)"
 
 
 class Clocks:
@@ -243,7 +245,7 @@ def main():
     sdc.check_status(out["status"], "timed")
     kern = {}
     import ctypes
-    for name in ("deflate", "tiles", "secular", "lowner", "bnorm", "merge"):
+    for name in ("deflate", "tiles", "units", "secular", "lowner", "bnorm", "merge"):
         n_ = ctypes.c_int64(0)
         t_ = ctypes.c_double(0.0)
         lib.superdc_profile_read(name.encode(), ctypes.byref(n_), ctypes.byref(t_))
@@ -297,7 +299,7 @@ def main():
             "gpu_launches": int(launches),
             "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kern.items()},
             "roofline": {"bound": "alu", "kernel": "k_secular", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s (FP64)", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "dtype": "fp64", "frac": achieved / peak, "traffic": None,
                          "peak_source": peak_src,
                          "algorithmic": "%.0f flops/interaction x %.4g interactions per launch" % (
                              SECULAR_FLOPS_PER_INTERACTION, interactions)},

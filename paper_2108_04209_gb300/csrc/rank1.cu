@@ -30,7 +30,56 @@ namespace {
 
 constexpr int SEC_CHUNK = 2048;   // poles staged per shared-memory chunk
 
-__device__ __forceinline__ double rcp(double t) { return 1.0 / t; }
+// ---------------------------------------------------------------------------
+// FP64 reciprocal without the FP64 divide sequence.  The GB300 FP64 pipe
+// retires ~2 DFMA per clock per SM, so every FP64 instruction of the inner
+// loops counts, while integer and MUFU pipes are nearly free.  Seed: the
+// leading 23 mantissa bits of |t| as a float in [1,2), reciprocal on the MUFU
+// (rcp.approx.f32, relative error < 2^-22 after the truncation), exponent and
+// sign rebuilt with integer arithmetic (valid for every normal double).  Then
+// Newton-Raphson r <- r + r (1 - t r), which squares the relative error:
+// one step -> < 2^-44, two steps -> correctly rounded up to ~1 ulp.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float mufu_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ double rcp_seed(double t)
+{
+    const int hi = __double2hiint(t);
+    const unsigned lo = (unsigned)__double2loint(t);
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    const int e = (hi >> 20) & 0x7FF;
+    const unsigned mb = (((unsigned)hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const float rm = mufu_rcp(__uint_as_float(0x3F800000u | mb));   // in (0.5, 1]
+    const unsigned rb = __float_as_uint(rm);
+    const int E = (int)(rb >> 23) - 127 - (e - 1023) + 1023;
+    const unsigned rmant = rb & 0x7FFFFFu;
+    return __hiloint2double((int)(sign | ((unsigned)E << 20) | (rmant >> 3)), (int)(rmant << 29));
+}
+
+// one Newton step: relative error < 2^-44 (secular sweeps: every term of psi
+// (phi) has the same sign, so the sum inherits the per-term bound, which is
+// below the stopping tolerance of eq. (4.12) for m >= 32)
+__device__ __forceinline__ double rcp_nr1(double t)
+{
+    double r = rcp_seed(t);
+    double e = fma(-t, r, 1.0);
+    return fma(r, e, r);
+}
+
+// two Newton steps: full FP64 accuracy (b, Cauchy-like applications)
+__device__ __forceinline__ double rcp_nr2(double t)
+{
+    double r = rcp_seed(t);
+    double e = fma(-t, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-t, r, 1.0);
+    return fma(r, e, r);
+}
 
 // root of a*y^2 + b*y + c = 0 strictly inside (lo, hi), else the bracket middle
 __device__ double quad_in(double a, double b, double c, double lo, double hi)
@@ -180,35 +229,46 @@ struct Acc { double psi, phi, dpsi, dphi; };
 // first pole has global index jg0.  Pole j goes to psi if j <= k, else to phi.
 // The warp's roots are consecutive (kwlo..kwhi), so the loop runs in three
 // warp-uniform regions; only the middle one selects per lane.
+template <bool DERIV>
 __device__ __forceinline__ void sweep(const double *__restrict__ sd, const double *__restrict__ sw,
                                       int j0, int j1, int jg0, int k, int kwlo, int kwhi,
                                       double dK, double y, Acc &A)
 {
     // region A: global j <= kwlo -> psi for every lane
     int ea = min(j1, max(j0, kwlo - jg0 + 1));
+#pragma unroll 4
     for (int j = j0; j < ea; j++) {
         double t = (sd[j] - dK) - y;
-        double r = rcp(t);
-        double a = sw[j] * r;
-        A.psi += a;
-        A.dpsi = fma(a, r, A.dpsi);
+        double r = rcp_nr1(t);
+        if (DERIV) {
+            double a = sw[j] * r;
+            A.psi += a;
+            A.dpsi = fma(a, r, A.dpsi);
+        } else {
+            A.psi = fma(sw[j], r, A.psi);
+        }
     }
     // region B: kwlo < j <= kwhi -> per lane
     int eb = min(j1, max(ea, kwhi - jg0 + 1));
     for (int j = ea; j < eb; j++) {
         double t = (sd[j] - dK) - y;
-        double r = rcp(t);
+        double r = rcp_nr1(t);
         double a = sw[j] * r;
-        if (jg0 + j <= k) { A.psi += a; A.dpsi = fma(a, r, A.dpsi); }
-        else              { A.phi += a; A.dphi = fma(a, r, A.dphi); }
+        if (jg0 + j <= k) { A.psi += a; if (DERIV) A.dpsi = fma(a, r, A.dpsi); }
+        else              { A.phi += a; if (DERIV) A.dphi = fma(a, r, A.dphi); }
     }
     // region C: j > kwhi -> phi for every lane
+#pragma unroll 4
     for (int j = eb; j < j1; j++) {
         double t = (sd[j] - dK) - y;
-        double r = rcp(t);
-        double a = sw[j] * r;
-        A.phi += a;
-        A.dphi = fma(a, r, A.dphi);
+        double r = rcp_nr1(t);
+        if (DERIV) {
+            double a = sw[j] * r;
+            A.phi += a;
+            A.dphi = fma(a, r, A.dphi);
+        } else {
+            A.phi = fma(sw[j], r, A.phi);
+        }
     }
 }
 
@@ -293,67 +353,169 @@ struct Root {
     }
 };
 
-template <int TR>
-__global__ void __launch_bounds__(TR)
-k_secular(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restrict__ tile_off,
+// Work units of the secular kernel: (problem, first root, end root).
+// Problems with at most SEC_CHUNK kept poles form one unit (their poles are
+// staged in shared memory once); larger ones are cut into units of
+// SEC_UNIT_BIG roots whose sweeps stream the poles in chunks.  Units are
+// ordered by decreasing problem size (largest first) so the long units start
+// early and the tail of the launch is short.
+constexpr int SEC_UNIT_BIG = 2048;
+constexpr int SORT_MAX = 8192;
+
+__global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int4 *__restrict__ units,
+                        int *__restrict__ nunits, int *__restrict__ counter)
+{
+    extern __shared__ unsigned long long keys[];   // SORT_MAX entries when sorting
+    __shared__ int part[1024];
+    const int T = blockDim.x;
+    const bool sorted = nprob <= SORT_MAX;
+    int64_t n2 = 1;
+    if (sorted) {
+        while (n2 < nprob) n2 <<= 1;
+        for (int64_t i = threadIdx.x; i < n2; i += T) {
+            // descending by size: key = (size << 32) | (~p) so that equal sizes keep index order
+            keys[i] = (i < nprob) ? (((unsigned long long)(unsigned)mk[i] << 32) |
+                                     (unsigned long long)(0xFFFFFFFFu - (unsigned)i))
+                                  : 0ull;
+        }
+        __syncthreads();
+        for (int64_t kk = 2; kk <= n2; kk <<= 1) {
+            for (int64_t j = kk >> 1; j > 0; j >>= 1) {
+                for (int64_t i = threadIdx.x; i < n2; i += T) {
+                    int64_t ixj = i ^ j;
+                    if (ixj > i) {
+                        bool desc = ((i & kk) == 0);
+                        unsigned long long a = keys[i], b = keys[ixj];
+                        if (desc ? (a < b) : (a > b)) { keys[i] = b; keys[ixj] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // units per problem (in the chosen order), block-wide prefix
+    int64_t per = (nprob + T - 1) / T;
+    int64_t beg = threadIdx.x * per, end = min(nprob, beg + per);
+    int cnt = 0;
+    for (int64_t q = beg; q < end; q++) {
+        int64_t pp = sorted ? (int64_t)(0xFFFFFFFFu - (unsigned)(keys[q] & 0xFFFFFFFFull)) : q;
+        int m = mk[pp];
+        cnt += (m <= SEC_CHUNK) ? (m > 0) : (m + SEC_UNIT_BIG - 1) / SEC_UNIT_BIG;
+    }
+    part[threadIdx.x] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int i = 0; i < T; i++) { int v = part[i]; part[i] = acc; acc += v; }
+        *nunits = acc;
+        *counter = 0;
+    }
+    __syncthreads();
+    int u = part[threadIdx.x];
+    for (int64_t q = beg; q < end; q++) {
+        int64_t pp = sorted ? (int64_t)(0xFFFFFFFFu - (unsigned)(keys[q] & 0xFFFFFFFFull)) : q;
+        int m = mk[pp];
+        if (m <= 0) continue;
+        if (m <= SEC_CHUNK) {
+            units[u++] = make_int4((int)pp, 0, m, 0);
+        } else {
+            for (int r = 0; r < m; r += SEC_UNIT_BIG) units[u++] = make_int4((int)pp, r, min(m, r + SEC_UNIT_BIG), 0);
+        }
+    }
+}
+
+// One CTA of NW warps per unit, persistent over an atomic unit queue.  Each
+// warp owns a contiguous quarter (1/NW) of the unit's roots; a lane whose root
+// has converged takes the next root of the warp's range, so the FP64 pipe
+// keeps working on live roots instead of waiting for the slowest root of a
+// fixed group of 32.  The live roots of a warp stay inside a short window, so
+// the psi/phi split keeps its three warp-uniform regions.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32)
+k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
+          const int *__restrict__ nunits, int *__restrict__ counter,
           R1Out o, double stop_c, int max_iter)
 {
     __shared__ double sd[SEC_CHUNK];
     __shared__ double sw[SEC_CHUNK];
-    const int64_t ntiles = tile_off[nprob];
-    const int lane = threadIdx.x & 31;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t p = sdc_upper_index(tile_off, nprob, tile);
+    __shared__ int s_unit;
+    const unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nu = *nunits;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= nu) break;
+        const int4 U = units[u];
+        const int64_t p = U.x;
         const int64_t b0 = off[p];
         const int m = o.mk[p];
         const double *dk = o.dk + b0, *zk = o.zk + b0;
-        const int k = (int)(tile - tile_off[p]) * TR + threadIdx.x;
-        const bool active = k < m;
-        const int kc = min(k, m - 1);
-        const int kwlo = __shfl_sync(0xffffffffu, kc, 0);
-        const int kwhi = __shfl_sync(0xffffffffu, kc, 31);
-        (void)lane;
+        const double W = o.wsum[p];
         const double tol = stop_c * (double)m * SDC_EPS;
+        const int len = U.z - U.y;
+        const int wbeg = U.y + (int)(((int64_t)len * warp) / NW);
+        const int wend = U.y + (int)(((int64_t)len * (warp + 1)) / NW);
+        int k = wbeg + lane;
+        bool act = k < wend;
+        int next = wbeg + 32;
         Root R;
-        bool done = true;
-        if (active) { R.init(dk, zk, k, m, o.wsum[p]); done = false; }
-        __syncthreads();   // previous tile finished with the shared arrays
-        if (m <= SEC_CHUNK) {
-            for (int j = threadIdx.x; j < m; j += TR) {
+        R.dK = 0.0; R.y = 1.0; R.phase = 1;     // defined values for lanes that stay idle
+        if (act) R.init(dk, zk, k, m, W);
+        const bool single = (m <= SEC_CHUNK);
+        if (single) {
+            for (int j = threadIdx.x; j < m; j += NW * 32) {
                 sd[j] = dk[j];
                 double zj = zk[j];
                 sw[j] = zj * zj;
             }
-            __syncthreads();
-            // every root iterates on its own: no block-wide barrier inside
-            while (!done) {
-                Acc A = {0.0, 0.0, 0.0, 0.0};
-                sweep(sd, sw, 0, m, 0, kc, kwlo, kwhi, R.dK, R.y, A);
-                done = R.update(A, tol, max_iter, o.status);
-            }
-        } else {
-            // lock-step sweeps, poles streamed through shared memory in chunks
-            while (__syncthreads_or(!done)) {
-                Acc A = {0.0, 0.0, 0.0, 0.0};
+        }
+        __syncthreads();
+        while (single ? __any_sync(FULL, act) : __syncthreads_or(act)) {
+            const int kwlo = __reduce_min_sync(FULL, act ? k : 0x7fffffff);
+            const int kwhi = __reduce_max_sync(FULL, act ? k : -1);
+            const int kk = act ? k : kwlo;
+            const bool p0 = __all_sync(FULL, !act || R.phase == 0);
+            Acc A = {0.0, 0.0, 0.0, 0.0};
+            if (single) {
+                if (p0) sweep<false>(sd, sw, 0, m, 0, kk, kwlo, kwhi, R.dK, R.y, A);
+                else    sweep<true>(sd, sw, 0, m, 0, kk, kwlo, kwhi, R.dK, R.y, A);
+            } else {
+                const bool any = __any_sync(FULL, act);
                 for (int c0 = 0; c0 < m; c0 += SEC_CHUNK) {
                     const int cn = min(SEC_CHUNK, m - c0);
                     __syncthreads();
-                    for (int j = threadIdx.x; j < cn; j += TR) {
+                    for (int j = threadIdx.x; j < cn; j += NW * 32) {
                         sd[j] = dk[c0 + j];
                         double zj = zk[c0 + j];
                         sw[j] = zj * zj;
                     }
                     __syncthreads();
-                    if (!done) sweep(sd, sw, 0, cn, c0, kc, kwlo, kwhi, R.dK, R.y, A);
+                    if (any) {
+                        if (p0) sweep<false>(sd, sw, 0, cn, c0, kk, kwlo, kwhi, R.dK, R.y, A);
+                        else    sweep<true>(sd, sw, 0, cn, c0, kk, kwlo, kwhi, R.dK, R.y, A);
+                    }
                 }
-                if (!done) done = R.update(A, tol, max_iter, o.status);
             }
-        }
-        if (active) {
-            o.org[b0 + k] = R.K;
-            o.eta[b0 + k] = R.y;
-            o.dorg[b0 + k] = R.dK;
-            if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
+            bool fin = false;
+            if (act) {
+                fin = R.update(A, tol, max_iter, o.status);
+                if (fin) {
+                    o.org[b0 + k] = R.K;
+                    o.eta[b0 + k] = R.y;
+                    o.dorg[b0 + k] = R.dK;
+                    if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
+                }
+            }
+            const unsigned mask = __ballot_sync(FULL, fin);
+            if (fin) {
+                k = next + __popc(mask & ((1u << lane) - 1u));
+                act = k < wend;
+                if (act) R.init(dk, zk, k, m, W);
+            }
+            next += __popc(mask);
         }
     }
 }
@@ -377,13 +539,32 @@ k_lowner(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restri
         if (i >= m) continue;
         const double *dk = o.dk + b0, *dorg = o.dorg + b0, *eta = o.eta + b0;
         const double di = dk[i];
-        double prod = (dorg[m - 1] - di) + eta[m - 1];
+        // numerator and denominator products kept apart (one division per
+        // entry instead of one per factor); every 8 factors both are brought
+        // back to [1/2, 1) by exponent arithmetic, the exponents summed in ex
+        double pn = (dorg[m - 1] - di) + eta[m - 1];
+        double pd = 1.0;
+        int ex = 0;
         for (int j = 0; j < m - 1; j++) {
             double num = (dorg[j] - di) + eta[j];
             double den = ((j < i) ? dk[j] : dk[j + 1]) - di;
-            prod *= num / den;
+            pn *= num;
+            pd *= den;
+            if ((j & 7) == 7) {
+                int hn = __double2hiint(pn), hd = __double2hiint(pd);
+                int en = (hn >> 20) & 0x7FF, ed = (hd >> 20) & 0x7FF;
+                if (en != 0 && ed != 0 && en != 0x7FF && ed != 0x7FF) {
+                    ex += en - ed;
+                    pn = __hiloint2double((hn & 0x800FFFFF) | (1022 << 20), __double2loint(pn));
+                    pd = __hiloint2double((hd & 0x800FFFFF) | (1022 << 20), __double2loint(pd));
+                }
+            }
         }
-        double v = sqrt(prod);
+        double prod = pn / pd;
+        if (ex & 1) { prod *= 2.0; ex -= 1; }
+        double vs = sqrt(prod);
+        vs = ldexp(vs, ex / 2);
+        double v = vs;
         if (!isfinite(v)) sdc_latch(o.status, SUPERDC_DEV_NONFINITE);
         o.vhat[b0 + i] = (o.zk[b0 + i] < 0.0) ? -v : v;
     }
@@ -408,7 +589,7 @@ k_bnorm(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restric
         double s = 0.0;
         for (int i = 0; i < m; i++) {
             double t = (dk[i] - dK) - e;
-            double r = rcp(t);
+            double r = rcp_nr2(t);
             double vr = v[i] * r;
             s = fma(vr, vr, s);
         }
@@ -476,6 +657,16 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     SDC_CHECK(sdc_alloc(&wz, a.total, st));
     SDC_CHECK(sdc_alloc(&kept, a.total, st));
     SDC_CHECK(sdc_alloc(&tile_off, a.nprob + 1, st));
+    int4 *units = nullptr;
+    int *ucount = nullptr;
+    SDC_CHECK(sdc_alloc(&units, a.nprob + a.total / SEC_UNIT_BIG + 2, st));
+    SDC_CHECK(sdc_alloc(&ucount, 2, st));
+    static bool attr_done = false;
+    if (!attr_done) {
+        SDC_CHECK(cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(SORT_MAX * sizeof(unsigned long long))));
+        attr_done = true;
+    }
 
     const int tpb = 128;
     PROF_LAUNCH("deflate", st, k_deflate<<<(unsigned)((a.nprob + tpb - 1) / tpb), tpb, 0, st>>>(
@@ -483,7 +674,10 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     const int TR = 128;
     PROF_LAUNCH("tiles", st, k_tiles<<<1, 1024, 0, st>>>(a.nprob, a.o.mk, TR, tile_off));
     const unsigned grid = (unsigned)(nsm * 8);
-    PROF_LAUNCH("secular", st, k_secular<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, a.stop_c, a.max_iter));
+    const size_t ksm = (a.nprob <= SORT_MAX) ? (size_t)SORT_MAX * sizeof(unsigned long long) : 0;
+    PROF_LAUNCH("units", st, k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, units, ucount, ucount + 1));
+    PROF_LAUNCH("secular", st, k_secular<4><<<(unsigned)(nsm * 6), 128, 0, st>>>(a.off, units, ucount, ucount + 1,
+                                                                           a.o, a.stop_c, a.max_iter));
     PROF_LAUNCH("lowner", st, k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o));
     PROF_LAUNCH("bnorm", st, k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o));
     PROF_LAUNCH("merge", st, k_merge<<<(unsigned)(nsm * 8), 256, 0, st>>>(a.nprob, a.off, a.total, a.o));
@@ -493,5 +687,7 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     SDC_CHECK(cudaFreeAsync(wz, st));
     SDC_CHECK(cudaFreeAsync(kept, st));
     SDC_CHECK(cudaFreeAsync(tile_off, st));
+    SDC_CHECK(cudaFreeAsync(units, st));
+    SDC_CHECK(cudaFreeAsync(ucount, st));
     return SUPERDC_OK;
 }
