@@ -124,6 +124,89 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
                                        cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Symmetric HSS matrix (Section 2, eq. (2.1)) and its eigendecomposition.
+ *
+ * Tree (HOST arrays): a postordered full binary tree with nnodes nodes, the
+ * root is node nnodes-1; lchild/rchild are -1 at leaves; every leaf lies at
+ * the same depth (perfect tree); leaf_size[i] = rows of leaf i (ignored for
+ * non-leaves), 1 <= leaf_size <= 256; rank = r, the common HSS rank
+ * (1 <= r <= 32): every U_i is m_i x r, every R_i and B_i is r x r.
+ *
+ * Generators (DEVICE, FP64, column-major blocks, caller-owned, read only):
+ *   D : leaf diagonal blocks m_i x m_i concatenated over the leaves in
+ *       postorder (= left-to-right);
+ *   U : leaf bases m_i x r concatenated the same way;
+ *   R : nnodes blocks r x r (node i at R + i r^2); the entries of the root
+ *       and of its two children are not used;
+ *   B : nnodes blocks r x r; B_i of a left child i couples it with its
+ *       sibling: A(i, j) = U_i B_i U_j^T (nested U_p = [U_i R_i; U_j R_j]).
+ * superdc_build_hss copies them into a library-owned handle (stream-ordered);
+ * the caller may free its arrays once the stream has passed the call.
+ * -------------------------------------------------------------------- */
+typedef struct superdc_hss superdc_hss;
+typedef struct superdc_eigfact superdc_eigfact;
+
+typedef struct {
+    int64_t n;
+    int32_t nnodes;
+    const int32_t *lchild;
+    const int32_t *rchild;
+    const int64_t *leaf_size;
+    int32_t rank;
+} superdc_tree;
+
+superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, const double *U,
+                                 const double *R, const double *B, cudaStream_t stream,
+                                 superdc_hss **out);
+void superdc_hss_free(superdc_hss *h);
+
+/* Eigendecomposition A = Q diag(lambda) Q^T (Algorithms 1-3):
+ *   dividing stage (Algorithm 1, balanced eqs. (3.11)/(3.12), generator
+ *   updates of Lemma 2.1); leaf eigendecompositions (parallel cyclic
+ *   Jacobi); conquering stage bottom-up over the tree levels: merge sort P_p
+ *   (eq. (4.31)), Zhat_p = diag(Q_c1^T, Q_c2^T) Z_p (eq. (2.8)), r rank-one
+ *   steps per node, each step applied to the remaining columns.
+ * lambda: DEVICE, n entries, ascending (caller-allocated).
+ * *fact receives a library-owned handle holding Q in structured form
+ * (Lemma 4.1, eq. (4.34)): dense leaf blocks, the permutations and, for every
+ * node and step, the factor vectors of eq. (4.30) plus the deflation
+ * rotations.  Device-detected errors are latched in the handle; the call
+ * synchronises the stream once at the end and returns them. */
+superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaStream_t stream,
+                           double *lambda, superdc_eigfact **fact);
+void superdc_eigfact_free(superdc_eigfact *f);
+
+/* Y = Q X (trans = 0) or Y = Q^T X (trans = 1), Algorithm 4 applied at the
+ * root.  X, Y: DEVICE, n x ncols column-major with leading dimensions
+ * ldx, ldy >= n; X and Y must not overlap.  Work buffers come from the
+ * stream-ordered allocator. */
+superdc_status superdc_apply_Q(const superdc_eigfact *f, int32_t trans, int64_t ncols,
+                               const double *X, int64_t ldx, double *Y, int64_t ldy,
+                               cudaStream_t stream);
+
+/* Latched device status of a handle (synchronises the handle's last work):
+ * SUPERDC_OK, SUPERDC_ERR_NONFINITE or SUPERDC_ERR_NOCONV. */
+superdc_status superdc_sync_status(const superdc_eigfact *f);
+
+/* Statistics of the last superdc_eig on this handle (HOST outputs, any may be
+ * NULL): total deflated entries over all steps, total secular sweeps, and the
+ * largest number of sweeps used by a root. */
+superdc_status superdc_eigfact_stats(const superdc_eigfact *f, int64_t *deflated, int64_t *sweeps,
+                                     int32_t *max_sweeps);
+
+/* Copy one stored array of the structured Q to HOST memory `dst` (test and
+ * inspection access).  level: 0 (root) .. lmax-1; step: 0 .. r-1.  Fields of
+ * length n (one entry per row of the level; node i owns its row range):
+ *   "dk", "eta", "dorg", "vhat", "bnorm"  (double), "src", "pinv" (int32),
+ *   "P" (int32, the merge order of eq. (4.31); step ignored),
+ *   "giv_cs" (double, 2n), "giv_ab" (int32, 2n);
+ * per node of the level: "mk", "ngiv" (int32).  Synchronous. */
+superdc_status superdc_eigfact_get(const superdc_eigfact *f, int32_t level, int32_t step,
+                                   const char *field, void *dst);
+/* Tree depth lmax (levels of non-leaf nodes are 0 .. lmax-1), rank r, order n. */
+superdc_status superdc_eigfact_shape(const superdc_eigfact *f, int32_t *lmax, int32_t *r, int64_t *n);
+
+/* ------------------------------------------------------------------------
  * Kernel timing (instrumentation; no counterpart in the paper).
  * superdc_profile_enable(1) makes every later call record CUDA events on its
  * stream around each kernel; superdc_profile_read synchronises on those

@@ -59,3 +59,36 @@ def fro2_from_generators(h):
         if t.lchild[i] >= 0:
             s += 2.0 * np.sum(h.B[int(t.lchild[i])] ** 2)
     return s
+
+
+def hss_matvec(h, X):
+    """A X from the generators (eq. (2.1)) in O(n r k): upward pass
+    Ut_c = U_c^T X_c (nested through R), downward pass of the incoming
+    coupling F_c, leaves D X + U F."""
+    t = h.tree
+    X = np.asarray(X, np.float64).reshape(t.n, -1)
+    Ut, F = {}, {}
+    for i in range(t.nnodes):                        # postorder: upward
+        if t.lchild[i] < 0:
+            o, m = int(t.offset[i]), int(t.leaf_size[i])
+            Ut[i] = h.leaf_U(i).T @ X[o:o + m]
+        elif i != t.root:
+            a, b = int(t.lchild[i]), int(t.rchild[i])
+            Ut[i] = h.R[a].T @ Ut[a] + h.R[b].T @ Ut[b]
+    Y = np.zeros_like(X)
+    F[t.root] = None
+    for i in range(t.nnodes - 1, -1, -1):            # reverse postorder: downward
+        if t.lchild[i] < 0:
+            o, m = int(t.offset[i]), int(t.leaf_size[i])
+            Y[o:o + m] = h.leaf_D(i) @ X[o:o + m]
+            if F[i] is not None:
+                Y[o:o + m] += h.leaf_U(i) @ F[i]
+            continue
+        a, b = int(t.lchild[i]), int(t.rchild[i])
+        Fa = h.B[a] @ Ut[b]
+        Fb = h.B[a].T @ Ut[a]
+        if F[i] is not None:
+            Fa = Fa + h.R[a] @ F[i]
+            Fb = Fb + h.R[b] @ F[i]
+        F[a], F[b] = Fa, Fb
+    return Y

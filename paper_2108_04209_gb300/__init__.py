@@ -86,3 +86,99 @@ def secular_batched_host(offsets, d, z, rho=1.0, opts=None, fields=("lam", "eta"
     torch.cuda.current_stream().synchronize()
     check_status(st, "superdc_secular_batched")
     return res
+
+
+# ---------------------------------------------------------------------------
+# HSS eigendecomposition
+# ---------------------------------------------------------------------------
+class HSSMatrix:
+    """Library-owned device copy of a symmetric HSS matrix (superdc_build_hss).
+
+    ``h`` is an ``inputs.HSS`` (tree + generators); the generators are copied
+    to the GPU and then into the library handle."""
+
+    def __init__(self, h, device=None):
+        import numpy as np
+        dev = torch.device(device or "cuda")
+        t = h.tree
+        self.n, self.rank = int(t.n), int(t.rank)
+        self._lch = np.ascontiguousarray(t.lchild, np.int32)
+        self._rch = np.ascontiguousarray(t.rchild, np.int32)
+        self._sz = np.ascontiguousarray(t.leaf_size, np.int64)
+        tree = L.Tree(self.n, int(t.nnodes), self._lch.ctypes.data, self._rch.ctypes.data,
+                      self._sz.ctypes.data, self.rank)
+        D, U, R, B = (torch.from_numpy(x).to(dev) for x in h.packed())
+        self._h = ctypes.c_void_p()
+        code = L.lib().superdc_build_hss(ctypes.byref(tree), _ptr(D), _ptr(U), _ptr(R), _ptr(B), _stream(),
+                                         ctypes.byref(self._h))
+        L.check(code, "superdc_build_hss")
+
+    def eig(self, opts=None):
+        """Eigendecomposition; returns (lambda [n] device tensor ascending, EigFactor)."""
+        if opts is None:
+            opts = default_opts()
+        lam = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        f = ctypes.c_void_p()
+        code = L.lib().superdc_eig(self._h, ctypes.byref(opts), _stream(), _ptr(lam), ctypes.byref(f))
+        fac = EigFactor(f, self) if f.value else None
+        L.check(code, "superdc_eig")
+        return lam, fac
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value:
+                L.lib().superdc_hss_free(self._h)
+                self._h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+class EigFactor:
+    """Structured Q of an HSS eigendecomposition (superdc_eigfact)."""
+
+    def __init__(self, handle, owner):
+        self._f = handle
+        self._owner = owner   # keeps the HSS handle alive
+        lm, r, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        L.check(L.lib().superdc_eigfact_shape(self._f, ctypes.byref(lm), ctypes.byref(r), ctypes.byref(n)))
+        self.lmax, self.rank, self.n = lm.value, r.value, n.value
+
+    def apply_Q(self, X, trans=False):
+        """Y = Q X (trans False) or Q^T X; X: float64 CUDA tensor n or n x k."""
+        vec = X.dim() == 1
+        Xc = X.reshape(self.n, -1)
+        Xf = Xc.t().contiguous().t() if not Xc.t().is_contiguous() else Xc    # column-major view
+        k = Xf.shape[1]
+        Y = torch.empty((k, self.n), dtype=torch.float64, device=X.device).t()
+        ldx = Xf.stride(1) if k > 1 else self.n
+        code = L.lib().superdc_apply_Q(self._f, 1 if trans else 0, k, _ptr(Xf), ldx, _ptr(Y),
+                                       self.n, _stream())
+        L.check(code, "superdc_apply_Q")
+        return Y.reshape(-1) if vec else Y
+
+    def stats(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        L.check(L.lib().superdc_eigfact_stats(self._f, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"deflated": a.value, "sweeps": b.value, "max_sweeps": c.value}
+
+    def get(self, level, step, field):
+        import numpy as np
+        n = self.n
+        nn = 2 ** level
+        spec = {"dk": (n, np.float64), "eta": (n, np.float64), "dorg": (n, np.float64), "vhat": (n, np.float64),
+                "bnorm": (n, np.float64), "src": (n, np.int32), "pinv": (n, np.int32), "P": (n, np.int32),
+                "giv_cs": (2 * n, np.float64), "giv_ab": (2 * n, np.int32), "mk": (nn, np.int32),
+                "ngiv": (nn, np.int32)}
+        cnt, dt = spec[field]
+        out = np.empty(cnt, dt)
+        L.check(L.lib().superdc_eigfact_get(self._f, level, step, field.encode(), out.ctypes.data),
+                "superdc_eigfact_get")
+        return out
+
+    def __del__(self):
+        try:
+            if self._f and self._f.value:
+                L.lib().superdc_eigfact_free(self._f)
+                self._f = ctypes.c_void_p()
+        except Exception:
+            pass

@@ -28,6 +28,11 @@ class Opts(ctypes.Structure):
                 ("tile_roots", c_int32), ("batching", c_int32), ("reserved", c_int32)]
 
 
+class Tree(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("nnodes", c_int32), ("lchild", c_void_p), ("rchild", c_void_p),
+                ("leaf_size", c_void_p), ("rank", c_int32)]
+
+
 class Rank1Out(ctypes.Structure):
     _fields_ = [(n, c_void_p) for n in ("lam", "dk", "zk", "eta", "vhat", "bnorm", "org", "src", "perm",
                                          "giv_ab", "giv_cs", "mk", "ngiv", "sweeps", "status")]
@@ -51,6 +56,27 @@ def lib():
         L.superdc_secular_batched.argtypes = [c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_double,
                                               ctypes.POINTER(Opts), ctypes.POINTER(Rank1Out), c_void_p]
         L.superdc_secular_batched.restype = c_int32
+        L.superdc_build_hss.argtypes = [ctypes.POINTER(Tree), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        ctypes.POINTER(c_void_p)]
+        L.superdc_build_hss.restype = c_int32
+        L.superdc_hss_free.argtypes = [c_void_p]
+        L.superdc_hss_free.restype = None
+        L.superdc_eig.argtypes = [c_void_p, ctypes.POINTER(Opts), c_void_p, c_void_p, ctypes.POINTER(c_void_p)]
+        L.superdc_eig.restype = c_int32
+        L.superdc_eigfact_free.argtypes = [c_void_p]
+        L.superdc_eigfact_free.restype = None
+        L.superdc_apply_Q.argtypes = [c_void_p, c_int32, c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p]
+        L.superdc_apply_Q.restype = c_int32
+        L.superdc_sync_status.argtypes = [c_void_p]
+        L.superdc_sync_status.restype = c_int32
+        L.superdc_eigfact_stats.argtypes = [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),
+                                            ctypes.POINTER(c_int32)]
+        L.superdc_eigfact_stats.restype = c_int32
+        L.superdc_eigfact_get.argtypes = [c_void_p, c_int32, c_int32, ctypes.c_char_p, c_void_p]
+        L.superdc_eigfact_get.restype = c_int32
+        L.superdc_eigfact_shape.argtypes = [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                            ctypes.POINTER(c_int64)]
+        L.superdc_eigfact_shape.restype = c_int32
         L.superdc_profile_enable.argtypes = [c_int32]
         L.superdc_profile_enable.restype = c_int32
         L.superdc_profile_reset.argtypes = []

@@ -80,9 +80,11 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
     a.o.ngiv = out->ngiv; a.o.sweeps = out->sweeps; a.o.status = out->status;
     SDC_CHECK(sdc_alloc(&a.o.dorg, total, stream));
     SDC_CHECK(sdc_alloc(&a.o.wsum, nprob, stream));
+    SDC_CHECK(sdc_alloc(&a.o.pinv, total, stream));
     superdc_status st = r1_run(a, stream);
     cudaFreeAsync(a.o.dorg, stream);
     cudaFreeAsync(a.o.wsum, stream);
+    cudaFreeAsync(a.o.pinv, stream);
     return st;
 }
 

@@ -1,0 +1,299 @@
+// Cauchy-like factor application kernels (direct tiled evaluator).
+//
+// Transpose (conquering stage, Algorithm 3; superdcmv with transpose,
+// Algorithm 4):   y_j = b_j sum_i vhat_i x_i / ((d_i - d_{K_j}) - eta_j)
+// Forward (superdcmv without transpose):
+//                 y_i = vhat_i sum_j b_j x_j / ((d_i - d_{K_j}) - eta_j)
+// Every entry uses the shifted difference of eq. (4.28).  One reciprocal per
+// (i, j) pair is shared by all columns of the block; the column sums run as
+// FP64 FMAs in registers, the operands of the other side are staged in shared
+// memory in chunks of TI rows.
+#include "common.cuh"
+#include "cauchy.cuh"
+#include "prof.cuh"
+
+namespace {
+
+__device__ __forceinline__ float mufu_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// full-accuracy FP64 reciprocal: MUFU seed on the mantissa, exponent by
+// integer arithmetic, two Newton-Raphson steps (see rank1.cu)
+__device__ __forceinline__ double rcp2(double t)
+{
+    const int hi = __double2hiint(t);
+    const unsigned lo = (unsigned)__double2loint(t);
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    const int e = (hi >> 20) & 0x7FF;
+    const unsigned mb = (((unsigned)hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const float rm = mufu_rcp(__uint_as_float(0x3F800000u | mb));
+    const unsigned rb = __float_as_uint(rm);
+    const int E = (int)(rb >> 23) - 127 - (e - 1023) + 1023;
+    const unsigned rmant = rb & 0x7FFFFFu;
+    double r = __hiloint2double((int)(sign | ((unsigned)E << 20) | (rmant >> 3)), (int)(rmant << 29));
+    double q = fma(-t, r, 1.0);
+    r = fma(r, q, r);
+    q = fma(-t, r, 1.0);
+    return fma(r, q, r);
+}
+
+constexpr int TJ = 128;   // outputs per CTA (one per thread)
+constexpr int TI = 128;   // staged rows per chunk
+
+__global__ void k_tiles_c(int64_t nprob, const int32_t *__restrict__ mk, int tr, int64_t *__restrict__ tile_off)
+{
+    __shared__ int64_t part[1024];
+    const int T = blockDim.x;
+    int64_t per = (nprob + T - 1) / T;
+    int64_t beg = threadIdx.x * per, end = min(nprob, beg + per);
+    int64_t s = 0;
+    for (int64_t p = beg; p < end; p++) s += (mk[p] + tr - 1) / tr;
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < T; i++) { int64_t v = part[i]; part[i] = acc; acc += v; }
+        tile_off[nprob] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int64_t p = beg; p < end; p++) { tile_off[p] = acc; acc += (mk[p] + tr - 1) / tr; }
+}
+
+// rotations of the deflation, in scan order (forward) or reversed with the
+// transposed rotation (inverse); one thread per (problem, column)
+__global__ void k_givens(FactorView f, double *X, int64_t ldx, int ncols, int inverse)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= f.nprob * ncols) return;
+    const int64_t p = t / ncols;
+    const int col = (int)(t - p * ncols);
+    const int ng = f.ngiv[p];
+    if (ng == 0) return;
+    const int64_t b0 = f.off[p];
+    double *x = X + b0 + (int64_t)col * ldx;
+    const int32_t *ab = f.giv_ab + 2 * b0;
+    const double *cs = f.giv_cs + 2 * b0;
+    for (int g0 = 0; g0 < ng; g0++) {
+        const int g = inverse ? ng - 1 - g0 : g0;
+        const int a = ab[2 * g], b = ab[2 * g + 1];
+        const double c = cs[2 * g], s = cs[2 * g + 1];
+        const double xa = x[a], xb = x[b];
+        if (!inverse) { x[a] = c * xa - s * xb; x[b] = s * xa + c * xb; }
+        else          { x[a] = c * xa + s * xb; x[b] = -s * xa + c * xb; }
+    }
+}
+
+// y_j = b_j sum_i vhat_i x_{src_i} / ((d_i - d_{K_j}) - eta_j), written at
+// merged position pinv[j]; columns [col0, col0 + NC) (fewer at the tail)
+template <int NC>
+__global__ void __launch_bounds__(TJ)
+k_cauchy_T(FactorView f, const int64_t *__restrict__ tile_off, const double *__restrict__ X, int64_t ldx,
+           double *__restrict__ Y, int64_t ldy, int col0, int ncols)
+{
+    __shared__ double sd[TI];
+    __shared__ double sx[NC][TI];
+    const int64_t ntiles = tile_off[f.nprob];
+    const int nc = min(NC, ncols - col0);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t p = sdc_upper_index(tile_off, f.nprob, tile);
+        const int64_t b0 = f.off[p];
+        const int m = f.mk[p];
+        const int j = (int)(tile - tile_off[p]) * TJ + threadIdx.x;
+        const bool act = j < m;
+        const double dK = act ? f.dorg[b0 + j] : 0.0;
+        const double e = act ? f.eta[b0 + j] : 1.0;
+        double acc[NC];
+#pragma unroll
+        for (int q = 0; q < NC; q++) acc[q] = 0.0;
+        for (int i0 = 0; i0 < m; i0 += TI) {
+            const int cn = min(TI, m - i0);
+            __syncthreads();
+            for (int ii = threadIdx.x; ii < cn; ii += TJ) {
+                const int64_t row = b0 + f.src[b0 + i0 + ii];
+                const double v = f.vhat[b0 + i0 + ii];
+                sd[ii] = f.dk[b0 + i0 + ii];
+#pragma unroll
+                for (int q = 0; q < NC; q++)
+                    sx[q][ii] = (q < nc) ? v * X[row + (int64_t)(col0 + q) * ldx] : 0.0;
+            }
+            __syncthreads();
+            if (act) {
+                for (int ii = 0; ii < cn; ii++) {
+                    const double r = rcp2((sd[ii] - dK) - e);
+#pragma unroll
+                    for (int q = 0; q < NC; q++) acc[q] = fma(sx[q][ii], r, acc[q]);
+                }
+            }
+        }
+        if (act) {
+            const double bj = f.bnorm[b0 + j];
+            const int64_t row = b0 + f.pinv[b0 + j];
+#pragma unroll
+            for (int q = 0; q < NC; q++)
+                if (q < nc) Y[row + (int64_t)(col0 + q) * ldy] = bj * acc[q];
+        }
+    }
+}
+
+// y_{src_i} = vhat_i sum_j b_j x_{pinv_j} / ((d_i - d_{K_j}) - eta_j)
+template <int NC>
+__global__ void __launch_bounds__(TJ)
+k_cauchy_N(FactorView f, const int64_t *__restrict__ tile_off, const double *__restrict__ X, int64_t ldx,
+           double *__restrict__ Y, int64_t ldy, int col0, int ncols)
+{
+    __shared__ double sk[TI], se[TI];
+    __shared__ double sx[NC][TI];
+    const int64_t ntiles = tile_off[f.nprob];
+    const int nc = min(NC, ncols - col0);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t p = sdc_upper_index(tile_off, f.nprob, tile);
+        const int64_t b0 = f.off[p];
+        const int m = f.mk[p];
+        const int i = (int)(tile - tile_off[p]) * TJ + threadIdx.x;
+        const bool act = i < m;
+        const double di = act ? f.dk[b0 + i] : 0.0;
+        double acc[NC];
+#pragma unroll
+        for (int q = 0; q < NC; q++) acc[q] = 0.0;
+        for (int j0 = 0; j0 < m; j0 += TI) {
+            const int cn = min(TI, m - j0);
+            __syncthreads();
+            for (int jj = threadIdx.x; jj < cn; jj += TJ) {
+                const int64_t row = b0 + f.pinv[b0 + j0 + jj];
+                const double bj = f.bnorm[b0 + j0 + jj];
+                sk[jj] = f.dorg[b0 + j0 + jj];
+                se[jj] = f.eta[b0 + j0 + jj];
+#pragma unroll
+                for (int q = 0; q < NC; q++)
+                    sx[q][jj] = (q < nc) ? bj * X[row + (int64_t)(col0 + q) * ldx] : 0.0;
+            }
+            __syncthreads();
+            if (act) {
+                for (int jj = 0; jj < cn; jj++) {
+                    const double r = rcp2((di - sk[jj]) - se[jj]);
+#pragma unroll
+                    for (int q = 0; q < NC; q++) acc[q] = fma(sx[q][jj], r, acc[q]);
+                }
+            }
+        }
+        if (act) {
+            const double v = f.vhat[b0 + i];
+            const int64_t row = b0 + f.src[b0 + i];
+#pragma unroll
+            for (int q = 0; q < NC; q++)
+                if (q < nc) Y[row + (int64_t)(col0 + q) * ldy] = v * acc[q];
+        }
+    }
+}
+
+// deflated slots: identity part of the factor
+__global__ void k_defl_copy(FactorView f, int64_t total, const double *__restrict__ X, int64_t ldx,
+                            double *__restrict__ Y, int64_t ldy, int ncols, int trans)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total * ncols;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slotg = x % total;
+        const int col = (int)(x / total);
+        const int64_t p = sdc_upper_index(f.off, f.nprob, slotg);
+        const int64_t b0 = f.off[p];
+        const int s = (int)(slotg - b0);
+        if (s < f.mk[p]) continue;
+        if (trans) Y[b0 + f.pinv[slotg] + (int64_t)col * ldy] = X[b0 + f.src[slotg] + (int64_t)col * ldx];
+        else       Y[b0 + f.src[slotg] + (int64_t)col * ldy] = X[b0 + f.pinv[slotg] + (int64_t)col * ldx];
+    }
+}
+
+template <template <int> class K>
+struct Dummy {};
+
+int pick_nc(int c)
+{
+    if (c <= 4) return 4;
+    if (c <= 8) return 8;
+    if (c <= 12) return 12;
+    if (c <= 16) return 16;
+    if (c <= 20) return 20;
+    if (c <= 24) return 24;
+    return 32;
+}
+
+template <int NC>
+void launch_T(const FactorView &f, const int64_t *tile_off, const double *X, int64_t ldx, double *Y, int64_t ldy,
+              int col0, int ncols, unsigned grid, cudaStream_t st)
+{
+    k_cauchy_T<NC><<<grid, TJ, 0, st>>>(f, tile_off, X, ldx, Y, ldy, col0, ncols);
+}
+
+template <int NC>
+void launch_N(const FactorView &f, const int64_t *tile_off, const double *X, int64_t ldx, double *Y, int64_t ldy,
+              int col0, int ncols, unsigned grid, cudaStream_t st)
+{
+    k_cauchy_N<NC><<<grid, TJ, 0, st>>>(f, tile_off, X, ldx, Y, ldy, col0, ncols);
+}
+
+typedef void (*LaunchFn)(const FactorView &, const int64_t *, const double *, int64_t, double *, int64_t, int, int,
+                         unsigned, cudaStream_t);
+
+LaunchFn pick(bool trans, int nc)
+{
+    switch (nc) {
+    case 4: return trans ? launch_T<4> : launch_N<4>;
+    case 8: return trans ? launch_T<8> : launch_N<8>;
+    case 12: return trans ? launch_T<12> : launch_N<12>;
+    case 16: return trans ? launch_T<16> : launch_N<16>;
+    case 20: return trans ? launch_T<20> : launch_N<20>;
+    case 24: return trans ? launch_T<24> : launch_N<24>;
+    default: return trans ? launch_T<32> : launch_N<32>;
+    }
+}
+
+superdc_status run(const FactorView &f, int64_t total, double *Xmut, const double *X, int64_t ldx, double *Y,
+                   int64_t ldy, int ncols, bool trans, cudaStream_t st)
+{
+    if (ncols <= 0 || total <= 0) return SUPERDC_OK;
+    const int nsm = sdc_num_sms();
+    int64_t *tile_off = nullptr;
+    SDC_CHECK(sdc_alloc(&tile_off, f.nprob + 1, st));
+    k_tiles_c<<<1, 1024, 0, st>>>(f.nprob, f.mk, TJ, tile_off);
+    const int gthreads = 128;
+    if (trans) {
+        int64_t nt = f.nprob * ncols;
+        PROF_LAUNCH("givens", st, k_givens<<<(unsigned)((nt + gthreads - 1) / gthreads), gthreads, 0, st>>>(
+            f, Xmut, ldx, ncols, 0));
+    }
+    const unsigned grid = (unsigned)(nsm * 4);
+    for (int c0 = 0; c0 < ncols; c0 += 32) {
+        const int c = min(32, ncols - c0);
+        LaunchFn fn = pick(trans, pick_nc(c));
+        PROF_LAUNCH("cauchy", st, fn(f, tile_off, X, ldx, Y, ldy, c0, ncols, grid, st));
+    }
+    PROF_LAUNCH("deflcopy", st, k_defl_copy<<<(unsigned)(nsm * 8), 256, 0, st>>>(f, total, X, ldx, Y, ldy, ncols,
+                                                                                  trans ? 1 : 0));
+    if (!trans) {
+        int64_t nt = f.nprob * ncols;
+        PROF_LAUNCH("givens", st, k_givens<<<(unsigned)((nt + gthreads - 1) / gthreads), gthreads, 0, st>>>(
+            f, Y, ldy, ncols, 1));
+    }
+    SDC_CHECK(cudaGetLastError());
+    SDC_CHECK(cudaFreeAsync(tile_off, st));
+    return SUPERDC_OK;
+}
+
+}  // namespace
+
+superdc_status cauchy_apply_T(const FactorView &f, int64_t total, double *X, int64_t ldx, double *Y, int64_t ldy,
+                              int ncols, cudaStream_t st)
+{
+    return run(f, total, X, X, ldx, Y, ldy, ncols, true, st);
+}
+
+superdc_status cauchy_apply_N(const FactorView &f, int64_t total, const double *X, int64_t ldx, double *Y,
+                              int64_t ldy, int ncols, cudaStream_t st)
+{
+    return run(f, total, nullptr, X, ldx, Y, ldy, ncols, false, st);
+}

@@ -1,0 +1,27 @@
+// Application of one batched rank-one factor Qhat = G^T [C (+) I] Pi^T
+// (Cauchy-like block C_ij = vhat_i b_j / ((d_i - d_{K_j}) - eta_j), eqs. (4.26)
+// and (4.28); rotations G of the deflation; sort Pi of the new eigenvalues) to
+// a block of columns.  Used inside the conquering stage (Algorithm 3: the
+// transpose applied to the remaining columns) and by superdc_apply_Q
+// (Algorithm 4).
+#pragma once
+#include "common.cuh"
+
+struct FactorView {
+    int64_t nprob;
+    const int64_t *off;                 // device, nprob+1 (problem row ranges)
+    const int32_t *mk, *ngiv;           // device, nprob
+    const double *dk, *eta, *dorg, *vhat, *bnorm;   // device, per slot
+    const int32_t *src, *perm, *pinv, *giv_ab;      // device
+    const double *giv_cs;
+};
+
+// Y = Qhat^T X.  X (rows in the step's input order) is overwritten by the
+// rotations; Y rows in merged order.  Column-major with leading dims ldx/ldy;
+// row r of problem p lives at off[p] + r.  ncols columns.
+superdc_status cauchy_apply_T(const FactorView &f, int64_t total, double *X, int64_t ldx,
+                              double *Y, int64_t ldy, int ncols, cudaStream_t st);
+
+// Y = Qhat X.  X rows in merged order (read only); Y rows in input order.
+superdc_status cauchy_apply_N(const FactorView &f, int64_t total, const double *X, int64_t ldx,
+                              double *Y, int64_t ldy, int ncols, cudaStream_t st);

@@ -1,0 +1,873 @@
+// SuperDC eigendecomposition of a symmetric HSS matrix on sm_103a (FP64).
+//
+//   superdc_build_hss -- library-owned copy of the generators + tree levels;
+//   superdc_eig       -- Algorithm 1 (dividing, balanced form eqs. (3.11)/(3.12),
+//                        accumulated generator updates of Lemma 2.1), leaf
+//                        eigendecompositions, then Algorithm 3 level by level:
+//                        every node of a level is one problem of the batched
+//                        rank-one pipeline (rank1.cu), so a whole level runs
+//                        in one launch per kernel;
+//   superdc_apply_Q   -- Algorithm 4 at the root (Q or Q^T times a block).
+//
+// Zhat_p = diag(Q_c1^T, Q_c2^T) Z_p (eq. (2.8)) is formed from W_c = Q_c^T U_c:
+// with Z_p = [U_c1 Bt/sqrt(beta); sqrt(beta) U_c2] (eq. (3.12)),
+// Zhat_p = [W_c1 Bt/sqrt(beta); sqrt(beta) W_c2], and W_p = Qhat_p^T P_p
+// [W_c1 R_c1; W_c2 R_c2] is carried through the r rank-one steps of node p
+// as r extra columns.  This equals Algorithm 3's superdcmv route in exact
+// arithmetic and avoids re-applying whole subtrees.
+#include <algorithm>
+#include <string>
+#include <cmath>
+#include <vector>
+#include <cuda_runtime.h>
+#include "common.cuh"
+#include "rank1.cuh"
+#include "cauchy.cuh"
+#include "prof.cuh"
+
+struct superdc_hss {
+    int64_t n = 0;
+    int nnodes = 0, r = 0, lmax = 0, nleaves = 0, mmax = 0;
+    std::vector<int> lch, rch, level;
+    std::vector<int64_t> size, off;
+    std::vector<std::vector<int>> lev_nodes;       // nodes of each level, left to right
+    std::vector<int> leaves;                       // left to right
+    // device
+    double *D = nullptr, *U = nullptr, *R = nullptr, *B = nullptr;
+    int32_t *d_lch = nullptr, *d_rch = nullptr;
+    int64_t *d_size = nullptr;
+    int64_t *d_leaf_off = nullptr, *d_leaf_m = nullptr, *d_leaf_doff = nullptr, *d_leaf_uoff = nullptr;
+    int32_t *d_leaf_id = nullptr;
+    std::vector<int64_t *> d_lev_off;              // per level: node row offsets (nodes+1)
+    std::vector<int32_t *> d_lev_nodes;            // per level: node ids
+};
+
+struct StepF {   // stored factor of one rank-one step of one level
+    double *dk, *eta, *dorg, *vhat, *bnorm, *giv_cs;
+    int32_t *src, *pinv, *giv_ab, *mk, *ngiv, *sweeps;
+};
+
+struct superdc_eigfact {
+    const superdc_hss *h = nullptr;
+    int64_t n = 0;
+    int r = 0, lmax = 0;
+    std::vector<char *> slabs;             // device allocations owned by the handle
+    double *Qleaf = nullptr;               // concatenated leaf eigenvector blocks (column-major)
+    int64_t *d_qoff = nullptr;             // offset of each leaf's block
+    std::vector<int32_t *> P;              // per non-leaf level: merge order (node-local old position)
+    std::vector<std::vector<StepF>> F;     // [level][step]
+    int32_t *status = nullptr;             // device status word
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n, std::vector<char *> *own)
+{
+    cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess && own) own->push_back((char *)*p);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Dividing stage, one CTA per non-leaf node of a level (top-down).
+// For node i with children c1, c2 and accumulated update H_i (D_i -> D_i - U_i H_i U_i^T):
+//   Bt = B_c1 - R_c1 H_i R_c2^T                    (Lemma 2.1)
+//   beta = ||Bt||_2
+//   H_c1 = R_c1 H_i R_c1^T + Bt Bt^T / beta,  H_c2 = R_c2 H_i R_c2^T + beta I   (eq. (3.12))
+//   Zhat scale: Bts = Bt / sqrt(beta), sqb = sqrt(beta)
+// H_root = 0 (the R generators of the root's children are never read).
+// ---------------------------------------------------------------------------
+__device__ void jacobi_small_maxeig(double *G, int r, double *out)
+{
+    // cyclic Jacobi on the r x r symmetric matrix G (column-major), one thread
+    double fro = 0;
+    for (int i = 0; i < r * r; i++) fro += G[i] * G[i];
+    fro = sqrt(fro);
+    for (int sw = 0; sw < 60; sw++) {
+        double off = 0;
+        for (int j = 0; j < r; j++)
+            for (int i = 0; i < r; i++)
+                if (i != j) off += G[i + r * j] * G[i + r * j];
+        if (sqrt(off) <= SDC_EPS * fro) break;
+        for (int p = 0; p < r - 1; p++)
+            for (int q = p + 1; q < r; q++) {
+                double apq = G[p + r * q];
+                if (apq == 0.0) continue;
+                double app = G[p + r * p], aqq = G[q + r * q];
+                double zeta = (aqq - app) / (2.0 * apq);
+                double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                                : ((zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < r; k++) {
+                    double gp = G[p + r * k], gq = G[q + r * k];
+                    G[p + r * k] = c * gp - s * gq;
+                    G[q + r * k] = s * gp + c * gq;
+                }
+                for (int k = 0; k < r; k++) {
+                    double gp = G[k + r * p], gq = G[k + r * q];
+                    G[k + r * p] = c * gp - s * gq;
+                    G[k + r * q] = s * gp + c * gq;
+                }
+            }
+    }
+    double mx = 0;
+    for (int i = 0; i < r; i++) mx = fmax(mx, G[i + r * i]);
+    *out = mx;
+}
+
+__global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, const int32_t *__restrict__ lch,
+                         const int32_t *__restrict__ rch, const double *__restrict__ R,
+                         const double *__restrict__ B, double *__restrict__ H, double *__restrict__ Bts,
+                         double *__restrict__ sqb, int32_t *status)
+{
+    extern __shared__ double sm[];
+    const int rr = r * r;
+    double *Hi = sm, *R1 = sm + rr, *R2 = sm + 2 * rr, *Bt = sm + 3 * rr, *T1 = sm + 4 * rr, *T2 = sm + 5 * rr,
+           *G = sm + 6 * rr;
+    __shared__ double s_beta;
+    const int i = nodes[blockIdx.x];
+    const int c1 = lch[i], c2 = rch[i];
+    const bool isroot = (i == root);
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+        Hi[e] = isroot ? 0.0 : H[(int64_t)i * rr + e];
+        R1[e] = isroot ? 0.0 : R[(int64_t)c1 * rr + e];
+        R2[e] = isroot ? 0.0 : R[(int64_t)c2 * rr + e];
+        Bt[e] = B[(int64_t)c1 * rr + e];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) {      // T1 = R1 Hi, T2 = R2 Hi
+        int a = e % r, b = e / r;
+        double s1 = 0, s2 = 0;
+        for (int k = 0; k < r; k++) { s1 += R1[a + r * k] * Hi[k + r * b]; s2 += R2[a + r * k] * Hi[k + r * b]; }
+        T1[e] = s1;
+        T2[e] = s2;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) {      // Bt - T1 R2^T, staged in G
+        int a = e % r, b = e / r;
+        double s = 0;
+        for (int k = 0; k < r; k++) s += T1[a + r * k] * R2[b + r * k];
+        G[e] = Bt[e] - s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) Bt[e] = G[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) {       // G = Bt^T Bt
+        int a = e % r, b = e / r;
+        double s = 0;
+        for (int k = 0; k < r; k++) s += Bt[k + r * a] * Bt[k + r * b];
+        G[e] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx;
+        jacobi_small_maxeig(G, r, &mx);
+        s_beta = sqrt(fmax(mx, 0.0));
+        if (!isfinite(s_beta)) sdc_latch(status, SUPERDC_DEV_NONFINITE);
+    }
+    __syncthreads();
+    const double beta = s_beta;
+    const double sb = sqrt(beta);
+    for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+        int a = e % r, b = e / r;
+        double h1 = 0, h2 = 0, bb = 0;
+        for (int k = 0; k < r; k++) {
+            h1 += T1[a + r * k] * R1[b + r * k];
+            h2 += T2[a + r * k] * R2[b + r * k];
+            bb += Bt[a + r * k] * Bt[b + r * k];
+        }
+        if (beta > 0) h1 += bb / beta;
+        if (a == b) h2 += beta;
+        H[(int64_t)c1 * rr + e] = h1;
+        H[(int64_t)c2 * rr + e] = h2;
+        Bts[(int64_t)i * rr + e] = (beta > 0) ? Bt[e] / sb : 0.0;
+    }
+    if (threadIdx.x == 0) sqb[i] = sb;
+}
+
+// ---------------------------------------------------------------------------
+// Leaf eigendecompositions: Dhat = D - U H U^T, parallel cyclic Jacobi
+// (round-robin pairing, rotations J^T A J with Rutishauser's angle formula),
+// ascending sort, Q_leaf and W_leaf = Q_leaf^T U_leaf.  One CTA per leaf,
+// A in shared memory with an odd row stride (no bank conflicts on columns),
+// the accumulated rotations in a global scratch block.
+// ---------------------------------------------------------------------------
+constexpr int LEAF_T = 256;
+
+__global__ void __launch_bounds__(LEAF_T)
+k_leaf(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
+       const int64_t *__restrict__ leaf_doff, const int64_t *__restrict__ leaf_uoff, const int32_t *__restrict__ leaf_id,
+       const double *__restrict__ D, const double *__restrict__ U, const double *__restrict__ H,
+       double *__restrict__ Vs, double *__restrict__ Qleaf, const int64_t *__restrict__ qoff,
+       double *__restrict__ lam, double *__restrict__ W, int32_t *status)
+{
+    extern __shared__ double sm[];
+    __shared__ int sp[128], sq[128];
+    __shared__ double sc[128], ss[128];
+    __shared__ double red[LEAF_T / 32];
+    const int L = blockIdx.x;
+    const int m = (int)leaf_m[L];
+    const int lda = m | 1;
+    double *A = sm;                           // m x lda
+    double *T = sm + (size_t)m * lda;         // m x r  (U H)
+    const double *Dl = D + leaf_doff[L];
+    const double *Ul = U + leaf_uoff[L];
+    const double *Hl = H + (int64_t)leaf_id[L] * r * r;
+    double *V = Vs + qoff[L];
+    const int tid = threadIdx.x;
+    // T = U H
+    for (int e = tid; e < m * r; e += LEAF_T) {
+        int i = e % m, k = e / m;
+        double s = 0;
+        for (int q = 0; q < r; q++) s += Ul[i + (int64_t)m * q] * Hl[q + r * k];
+        T[i + m * k] = s;
+    }
+    __syncthreads();
+    // A = D - T U^T, symmetric (upper triangle mirrored)
+    for (int e = tid; e < m * m; e += LEAF_T) {
+        int i = e % m, j = e / m;
+        if (i > j) continue;
+        double s = 0;
+        for (int q = 0; q < r; q++) s += T[i + m * q] * Ul[j + (int64_t)m * q];
+        double v = Dl[i + (int64_t)m * j] - s;
+        A[i * lda + j] = v;
+        A[j * lda + i] = v;
+    }
+    for (int e = tid; e < m * m; e += LEAF_T) V[e] = ((e % m) == (e / m)) ? 1.0 : 0.0;
+    __syncthreads();
+    // ||A||_F
+    double part = 0;
+    for (int e = tid; e < m * m; e += LEAF_T) { double v = A[(e / m) * lda + (e % m)]; part += v * v; }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    double fro2 = 0;
+    for (int w = 0; w < LEAF_T / 32; w++) fro2 += red[w];
+    // threshold rule: a pair is left alone when |a_pq| <= eps sqrt(|a_pp a_qq|)
+    // or |a_pq| is negligible against ||A||_F; the sweeps stop when a whole
+    // sweep performs no rotation
+    const double negl = SDC_EPS * SDC_EPS * sqrt(fro2);
+    __shared__ int s_rot;
+    const int M = m + (m & 1);
+    const int np = M / 2;
+    int sweep;
+    for (sweep = 0; sweep < 60; sweep++) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int rho = 0; rho < M - 1; rho++) {
+            if (tid < np) {
+                int pa = (tid == 0) ? 0 : ((tid - 1 + rho) % (M - 1)) + 1;
+                int pb = ((M - 1 - tid - 1 + rho) % (M - 1)) + 1;
+                int p = min(pa, pb), q = max(pa, pb);
+                double c = 1.0, s = 0.0;
+                if (q < m) {
+                    double apq = A[p * lda + q];
+                    double app = A[p * lda + p], aqq = A[q * lda + q];
+                    if (fabs(apq) > SDC_EPS * sqrt(fabs(app) * fabs(aqq)) && fabs(apq) > negl) {
+                        double zeta = (aqq - app) / (2.0 * apq);
+                        double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                   : ((zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                        s_rot = 1;
+                    }
+                } else {
+                    q = -1;
+                }
+                sp[tid] = p; sq[tid] = (s == 0.0) ? -1 : q; sc[tid] = c; ss[tid] = s;
+            }
+            __syncthreads();
+            for (int it = tid; it < np * m; it += LEAF_T) {          // rows: J^T A
+                int k = it / m, col = it % m;
+                int q = sq[k];
+                if (q < 0) continue;
+                int p = sp[k];
+                double c = sc[k], s = ss[k];
+                double ap = A[p * lda + col], aq = A[q * lda + col];
+                A[p * lda + col] = c * ap - s * aq;
+                A[q * lda + col] = s * ap + c * aq;
+            }
+            __syncthreads();
+            for (int it = tid; it < np * m; it += LEAF_T) {          // columns: (J^T A) J, and V J
+                int k = it / m, row = it % m;
+                int q = sq[k];
+                if (q < 0) continue;
+                int p = sp[k];
+                double c = sc[k], s = ss[k];
+                double ap = A[row * lda + p], aq = A[row * lda + q];
+                A[row * lda + p] = c * ap - s * aq;
+                A[row * lda + q] = s * ap + c * aq;
+                double vp = V[(int64_t)p * m + row], vq = V[(int64_t)q * m + row];
+                V[(int64_t)p * m + row] = c * vp - s * vq;
+                V[(int64_t)q * m + row] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+        if (s_rot == 0) break;
+        __syncthreads();
+    }
+    if (sweep >= 60 && tid == 0) sdc_latch(status, SUPERDC_DEV_NOCONV);
+    // ascending order (ties by index), outputs
+    __shared__ int rank[256];
+    for (int i = tid; i < m; i += LEAF_T) {
+        double li = A[i * lda + i];
+        int rk = 0;
+        for (int j = 0; j < m; j++) {
+            double lj = A[j * lda + j];
+            rk += (lj < li) || (lj == li && j < i);
+        }
+        rank[i] = rk;
+        lam[leaf_off[L] + rk] = li;
+        if (!isfinite(li)) sdc_latch(status, SUPERDC_DEV_NONFINITE);
+    }
+    __syncthreads();
+    double *Q = Qleaf + qoff[L];
+    for (int e = tid; e < m * m; e += LEAF_T) {
+        int row = e % m, i = e / m;
+        Q[(int64_t)rank[i] * m + row] = V[(int64_t)i * m + row];
+    }
+    for (int e = tid; e < m * r; e += LEAF_T) {
+        int i = e % m, k = e / m;
+        double s = 0;
+        for (int row = 0; row < m; row++) s += V[(int64_t)i * m + row] * Ul[row + (int64_t)m * k];
+        W[leaf_off[L] + rank[i] + n * k] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Level setup: merge the children's eigenvalues (stable, left child first on
+// ties) -> d^(0) and P_p; rows of Zhat_p (r columns) and of [W_c1 R_c1; W_c2 R_c2]
+// (r more columns, not at the root) in merged order.
+// ---------------------------------------------------------------------------
+__global__ void k_build(int64_t n, int r, int nl, const int64_t *__restrict__ loff, const int32_t *__restrict__ lnodes,
+                        int root, const int32_t *__restrict__ lch, const int32_t *__restrict__ rch,
+                        const int64_t *__restrict__ size, const double *__restrict__ R,
+                        const double *__restrict__ Bts, const double *__restrict__ sqb,
+                        const double *__restrict__ lam_prev, const double *__restrict__ Wp,
+                        double *__restrict__ d0, int32_t *__restrict__ P, double *__restrict__ WK)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = sdc_upper_index(loff, (int64_t)nl, x);
+        const int64_t o = loff[q];
+        const int node = lnodes[q];
+        const int c1 = lch[node], c2 = rch[node];
+        const int m = (int)(loff[q + 1] - o);
+        const int m1 = (int)size[c1];
+        const int i = (int)(x - o);
+        const double *l1 = lam_prev + o, *l2 = lam_prev + o + m1;
+        const double val = lam_prev[x];
+        int pos;
+        if (i < m1) {             // + number of right-child values strictly smaller
+            int lo = 0, hi = m - m1;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (l2[mid] < val) lo = mid + 1; else hi = mid; }
+            pos = i + lo;
+        } else {                  // + number of left-child values smaller or equal
+            int lo = 0, hi = m1;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (l1[mid] <= val) lo = mid + 1; else hi = mid; }
+            pos = (i - m1) + lo;
+        }
+        const int64_t y = o + pos;
+        d0[y] = val;
+        P[y] = i;
+        const int rr = r * r;
+        const bool top = i < m1;
+        const double *Rc = R + (int64_t)(top ? c1 : c2) * rr;
+        const double *Bs = Bts + (int64_t)node * rr;
+        const double sb = sqb[node];
+        for (int col = 0; col < r; col++) {
+            double zv = 0.0, xv = 0.0;
+            for (int k = 0; k < r; k++) {
+                const double w = Wp[x + n * k];
+                if (top) zv += w * Bs[k + r * col];
+                xv += w * Rc[k + r * col];
+            }
+            if (!top) zv = sb * Wp[x + n * col];
+            WK[y + n * col] = zv;
+            if (node != root) WK[y + n * (r + col)] = xv;
+        }
+    }
+}
+
+// row permutations inside every node of a level: gather (Y[o+pos] = X[o+P[o+pos]])
+// or scatter (Y[o+P[o+pos]] = X[o+pos])
+__global__ void k_permute(int64_t n, int nl, const int64_t *__restrict__ loff, const int32_t *__restrict__ P,
+                          const double *__restrict__ X, int64_t ldx, double *__restrict__ Y, int64_t ldy,
+                          int ncols, int scatter)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * ncols;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = t % n;
+        const int col = (int)(t / n);
+        const int64_t q = sdc_upper_index(loff, (int64_t)nl, x);
+        const int64_t o = loff[q];
+        const int64_t src = o + P[x];
+        if (scatter) Y[src + ldy * col] = X[x + ldx * col];
+        else         Y[x + ldy * col] = X[src + ldx * col];
+    }
+}
+
+// dense leaf blocks: Y_leaf = Q_leaf^T X_leaf (trans) or Q_leaf X_leaf
+__global__ void k_leaf_apply(int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
+                             const double *__restrict__ Qleaf, const int64_t *__restrict__ qoff,
+                             const double *__restrict__ X, int64_t ldx, double *__restrict__ Y, int64_t ldy,
+                             int ncols, int trans)
+{
+    const int L = blockIdx.x;
+    const int m = (int)leaf_m[L];
+    const int64_t o = leaf_off[L];
+    const double *Q = Qleaf + qoff[L];
+    for (int e = threadIdx.x; e < m * ncols; e += blockDim.x) {
+        const int i = e % m, col = e / m;
+        const double *x = X + o + ldx * col;
+        double s = 0.0;
+        if (trans) for (int k = 0; k < m; k++) s += Q[(int64_t)i * m + k] * x[k];
+        else       for (int k = 0; k < m; k++) s += Q[i + (int64_t)k * m] * x[k];
+        Y[o + i + ldy * col] = s;
+    }
+}
+
+__global__ void k_copy_cols(int64_t n, int ncols, const double *__restrict__ X, int64_t ldx, double *__restrict__ Y,
+                            int64_t ldy)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * ncols;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = t % n;
+        const int col = (int)(t / n);
+        Y[x + ldy * col] = X[x + ldx * col];
+    }
+}
+
+__global__ void k_stats(int64_t nprob, const int64_t *__restrict__ off, const int32_t *__restrict__ mk,
+                        const int32_t *__restrict__ sweeps, unsigned long long *acc)
+{
+    // acc[0] += deflated, acc[1] += sweeps, acc[2] = max sweeps
+    for (int64_t p = blockIdx.x; p < nprob; p += gridDim.x) {
+        const int64_t o = off[p];
+        const int m = (int)(off[p + 1] - o), k = mk[p];
+        unsigned long long s = 0, mx = 0;
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            unsigned long long v = (unsigned long long)sweeps[o + i];
+            s += v;
+            mx = v > mx ? v : mx;
+        }
+        for (int w = 16; w > 0; w >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, w);
+            unsigned long long o2 = __shfl_xor_sync(0xffffffffu, mx, w);
+            mx = o2 > mx ? o2 : mx;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&acc[1], s);
+            atomicMax(&acc[2], mx);
+        }
+        if (threadIdx.x == 0) atomicAdd(&acc[0], (unsigned long long)(m - k));
+    }
+}
+
+superdc_status status_from_word(int32_t w)
+{
+    if (w & SUPERDC_DEV_NONFINITE) return SUPERDC_ERR_NONFINITE;
+    if (w & SUPERDC_DEV_NOCONV) return SUPERDC_ERR_NOCONV;
+    if (w & SUPERDC_DEV_INDEX) return SUPERDC_ERR_CUDA;
+    return SUPERDC_OK;
+}
+
+FactorView view(const superdc_eigfact *f, int l, int j)
+{
+    const superdc_hss *h = f->h;
+    const StepF &S = f->F[l][j];
+    FactorView v;
+    v.nprob = (int64_t)h->lev_nodes[l].size();
+    v.off = h->d_lev_off[l];
+    v.mk = S.mk; v.ngiv = S.ngiv;
+    v.dk = S.dk; v.eta = S.eta; v.dorg = S.dorg; v.vhat = S.vhat; v.bnorm = S.bnorm;
+    v.src = S.src; v.perm = nullptr; v.pinv = S.pinv; v.giv_ab = S.giv_ab; v.giv_cs = S.giv_cs;
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, const double *U, const double *R,
+                                 const double *B, cudaStream_t stream, superdc_hss **out)
+{
+    if (!tree || !out || !D || !U || !B || !tree->lchild || !tree->rchild || !tree->leaf_size) return SUPERDC_ERR_ARG;
+    const int nn = tree->nnodes, r = tree->rank;
+    if (nn < 1 || (nn % 2) == 0 || r < 1 || r > 32 || tree->n < 1) return SUPERDC_ERR_ARG;
+    if (nn > 1 && !R) return SUPERDC_ERR_ARG;
+    superdc_hss *h = new superdc_hss();
+    h->nnodes = nn; h->r = r; h->n = tree->n;
+    h->lch.assign(tree->lchild, tree->lchild + nn);
+    h->rch.assign(tree->rchild, tree->rchild + nn);
+    h->level.assign(nn, -1);
+    h->size.assign(nn, 0);
+    h->off.assign(nn, 0);
+    // postorder: children precede parents; every non-root has one parent
+    std::vector<int> parent(nn, -1);
+    bool ok = true;
+    for (int i = 0; i < nn && ok; i++) {
+        int a = h->lch[i], b = h->rch[i];
+        if ((a < 0) != (b < 0)) ok = false;
+        if (a >= 0) {
+            if (a >= i || b >= i || parent[a] >= 0 || parent[b] >= 0) ok = false;
+            else { parent[a] = i; parent[b] = i; }
+        }
+    }
+    for (int i = 0; i < nn - 1 && ok; i++) if (parent[i] < 0) ok = false;
+    if (!ok) { delete h; return SUPERDC_ERR_ARG; }
+    // levels top-down, sizes bottom-up, offsets top-down
+    h->level[nn - 1] = 0;
+    for (int i = nn - 1; i >= 0; i--)
+        if (h->lch[i] >= 0) { h->level[h->lch[i]] = h->level[i] + 1; h->level[h->rch[i]] = h->level[i] + 1; }
+    int lmax = 0;
+    for (int i = 0; i < nn; i++) lmax = std::max(lmax, h->level[i]);
+    int64_t ntot = 0;
+    int mmax = 0;
+    for (int i = 0; i < nn; i++) {
+        if (h->lch[i] < 0) {
+            if (h->level[i] != lmax) ok = false;          // perfect tree
+            int64_t m = tree->leaf_size[i];
+            if (m < 1 || m > 128) ok = false;
+            h->size[i] = m;
+            ntot += m;
+            mmax = std::max<int>(mmax, (int)m);
+        } else {
+            h->size[i] = h->size[h->lch[i]] + h->size[h->rch[i]];
+        }
+    }
+    if (!ok || ntot != tree->n) { delete h; return SUPERDC_ERR_ARG; }
+    h->off[nn - 1] = 0;
+    for (int i = nn - 1; i >= 0; i--)
+        if (h->lch[i] >= 0) { h->off[h->lch[i]] = h->off[i]; h->off[h->rch[i]] = h->off[i] + h->size[h->lch[i]]; }
+    h->lmax = lmax;
+    h->mmax = mmax;
+    h->lev_nodes.assign(lmax + 1, {});
+    for (int i = 0; i < nn; i++) h->lev_nodes[h->level[i]].push_back(i);
+    for (auto &v : h->lev_nodes) std::sort(v.begin(), v.end(), [&](int a, int b) { return h->off[a] < h->off[b]; });
+    h->leaves = h->lev_nodes[lmax];
+    h->nleaves = (int)h->leaves.size();
+    // device copies
+    int64_t dsz = 0, usz = 0;
+    std::vector<int64_t> loff, lm, ldo, luo;
+    std::vector<int32_t> lid;
+    for (int L : h->leaves) {
+        loff.push_back(h->off[L]);
+        lm.push_back(h->size[L]);
+        ldo.push_back(dsz);
+        luo.push_back(usz);
+        lid.push_back(L);
+        dsz += h->size[L] * h->size[L];
+        usz += h->size[L] * r;
+    }
+    // the caller's D and U are packed in postorder; leaves in postorder are left to right
+    const int rr = r * r;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
+    chk(cudaMalloc(&h->D, dsz * sizeof(double)));
+    chk(cudaMalloc(&h->U, usz * sizeof(double)));
+    chk(cudaMalloc(&h->R, (size_t)nn * rr * sizeof(double)));
+    chk(cudaMalloc(&h->B, (size_t)nn * rr * sizeof(double)));
+    chk(cudaMalloc(&h->d_lch, nn * sizeof(int32_t)));
+    chk(cudaMalloc(&h->d_rch, nn * sizeof(int32_t)));
+    chk(cudaMalloc(&h->d_size, nn * sizeof(int64_t)));
+    chk(cudaMalloc(&h->d_leaf_off, h->nleaves * sizeof(int64_t)));
+    chk(cudaMalloc(&h->d_leaf_m, h->nleaves * sizeof(int64_t)));
+    chk(cudaMalloc(&h->d_leaf_doff, h->nleaves * sizeof(int64_t)));
+    chk(cudaMalloc(&h->d_leaf_uoff, h->nleaves * sizeof(int64_t)));
+    chk(cudaMalloc(&h->d_leaf_id, h->nleaves * sizeof(int32_t)));
+    if (e != cudaSuccess) { superdc_hss_free(h); return e == cudaErrorMemoryAllocation ? SUPERDC_ERR_OOM : SUPERDC_ERR_CUDA; }
+    chk(cudaMemcpyAsync(h->D, D, dsz * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    chk(cudaMemcpyAsync(h->U, U, usz * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    if (R) chk(cudaMemcpyAsync(h->R, R, (size_t)nn * rr * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    else chk(cudaMemsetAsync(h->R, 0, (size_t)nn * rr * sizeof(double), stream));
+    chk(cudaMemcpyAsync(h->B, B, (size_t)nn * rr * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    chk(cudaMemcpyAsync(h->d_lch, h->lch.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    chk(cudaMemcpyAsync(h->d_rch, h->rch.data(), nn * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    chk(cudaMemcpyAsync(h->d_size, h->size.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    chk(cudaMemcpyAsync(h->d_leaf_off, loff.data(), loff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    chk(cudaMemcpyAsync(h->d_leaf_m, lm.data(), lm.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    chk(cudaMemcpyAsync(h->d_leaf_doff, ldo.data(), ldo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    chk(cudaMemcpyAsync(h->d_leaf_uoff, luo.data(), luo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    chk(cudaMemcpyAsync(h->d_leaf_id, lid.data(), lid.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    h->d_lev_off.assign(lmax + 1, nullptr);
+    h->d_lev_nodes.assign(lmax + 1, nullptr);
+    for (int l = 0; l <= lmax; l++) {
+        std::vector<int64_t> lo;
+        for (int i : h->lev_nodes[l]) lo.push_back(h->off[i]);
+        lo.push_back(h->n);
+        chk(cudaMalloc(&h->d_lev_off[l], lo.size() * sizeof(int64_t)));
+        chk(cudaMalloc(&h->d_lev_nodes[l], h->lev_nodes[l].size() * sizeof(int32_t)));
+        if (e != cudaSuccess) break;
+        chk(cudaMemcpyAsync(h->d_lev_off[l], lo.data(), lo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+        chk(cudaMemcpyAsync(h->d_lev_nodes[l], h->lev_nodes[l].data(), h->lev_nodes[l].size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, stream));
+    }
+    // host vectors passed to async copies must live until the copies ran
+    chk(cudaStreamSynchronize(stream));
+    if (e != cudaSuccess) { superdc_hss_free(h); return e == cudaErrorMemoryAllocation ? SUPERDC_ERR_OOM : SUPERDC_ERR_CUDA; }
+    *out = h;
+    return SUPERDC_OK;
+}
+
+void superdc_hss_free(superdc_hss *h)
+{
+    if (!h) return;
+    cudaFree(h->D); cudaFree(h->U); cudaFree(h->R); cudaFree(h->B);
+    cudaFree(h->d_lch); cudaFree(h->d_rch); cudaFree(h->d_size);
+    cudaFree(h->d_leaf_off); cudaFree(h->d_leaf_m); cudaFree(h->d_leaf_doff); cudaFree(h->d_leaf_uoff);
+    cudaFree(h->d_leaf_id);
+    for (auto p : h->d_lev_off) cudaFree(p);
+    for (auto p : h->d_lev_nodes) cudaFree(p);
+    delete h;
+}
+
+void superdc_eigfact_free(superdc_eigfact *f)
+{
+    if (!f) return;
+    for (auto p : f->slabs) cudaFree(p);
+    delete f;
+}
+
+superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaStream_t st, double *lambda,
+                           superdc_eigfact **fact)
+{
+    superdc_opts def;
+    if (!opts) { superdc_opts_default(&def); opts = &def; }
+    if (!h || !lambda || !fact || !(opts->tau >= 0) || !(opts->stop_c > 0) || opts->max_iter < 1) return SUPERDC_ERR_ARG;
+    const int64_t n = h->n;
+    const int r = h->r, lmax = h->lmax, rr = r * r, nn = h->nnodes;
+    superdc_eigfact *f = new superdc_eigfact();
+    f->h = h; f->n = n; f->r = r; f->lmax = lmax;
+    auto fail = [&](cudaError_t e) {
+        superdc_eigfact_free(f);
+        return e == cudaErrorMemoryAllocation ? SUPERDC_ERR_OOM : SUPERDC_ERR_CUDA;
+    };
+#define EIG_CHECK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return fail(e_); } while (0)
+    // ---- persistent storage of the handle
+    std::vector<int64_t> qoff(h->nleaves + 1, 0);
+    for (int k = 0; k < h->nleaves; k++) qoff[k + 1] = qoff[k] + h->size[h->leaves[k]] * h->size[h->leaves[k]];
+    EIG_CHECK(dalloc(&f->Qleaf, qoff.back(), &f->slabs));
+    EIG_CHECK(dalloc(&f->d_qoff, qoff.size(), &f->slabs));
+    EIG_CHECK(dalloc(&f->status, 1, &f->slabs));
+    EIG_CHECK(cudaMemsetAsync(f->status, 0, sizeof(int32_t), st));
+    EIG_CHECK(cudaMemcpyAsync(f->d_qoff, qoff.data(), qoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    f->P.assign(lmax, nullptr);
+    f->F.assign(lmax, std::vector<StepF>(r));
+    for (int l = 0; l < lmax; l++) {
+        EIG_CHECK(dalloc(&f->P[l], n, &f->slabs));
+        const int64_t np = (int64_t)h->lev_nodes[l].size();
+        for (int j = 0; j < r; j++) {
+            StepF &S = f->F[l][j];
+            // one slab per step: 7 double arrays (dk, eta, dorg, vhat, bnorm, giv_cs x2), int arrays
+            double *dslab;
+            EIG_CHECK(dalloc(&dslab, 7 * n, &f->slabs));
+            S.dk = dslab; S.eta = dslab + n; S.dorg = dslab + 2 * n; S.vhat = dslab + 3 * n;
+            S.bnorm = dslab + 4 * n; S.giv_cs = dslab + 5 * n;
+            int32_t *islab;
+            EIG_CHECK(dalloc(&islab, 5 * n + 2 * np, &f->slabs));
+            S.src = islab; S.pinv = islab + n; S.giv_ab = islab + 2 * n; S.sweeps = islab + 4 * n;
+            S.mk = islab + 5 * n; S.ngiv = islab + 5 * n + np;
+        }
+    }
+    // ---- work buffers (released at the end of the call)
+    double *H, *Bts, *sqb, *lamA, *lamB, *Wp, *WK, *WK2, *zk, *wsum, *Vs;
+    int32_t *org, *perm;
+    std::vector<char *> tmp;
+    auto talloc = [&](auto **p, size_t cnt) { return dalloc(p, cnt, &tmp); };
+    auto free_tmp = [&]() { for (auto p : tmp) cudaFree(p); tmp.clear(); };
+#undef EIG_CHECK
+#define EIG_CHECK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { free_tmp(); return fail(e_); } } while (0)
+    EIG_CHECK(talloc(&H, (size_t)nn * rr));
+    EIG_CHECK(talloc(&Bts, (size_t)nn * rr));
+    EIG_CHECK(talloc(&sqb, nn));
+    EIG_CHECK(talloc(&lamA, n));
+    EIG_CHECK(talloc(&lamB, n));
+    EIG_CHECK(talloc(&Wp, (size_t)n * r));
+    EIG_CHECK(talloc(&WK, (size_t)n * 2 * r));
+    EIG_CHECK(talloc(&WK2, (size_t)n * 2 * r));
+    EIG_CHECK(talloc(&zk, n));
+    EIG_CHECK(talloc(&wsum, nn));
+    EIG_CHECK(talloc(&org, n));
+    EIG_CHECK(talloc(&perm, n));
+    EIG_CHECK(talloc(&Vs, qoff.back()));
+    EIG_CHECK(cudaMemsetAsync(H, 0, (size_t)nn * rr * sizeof(double), st));
+    const int nsm = sdc_num_sms();
+    // ---- 1. dividing stage, top-down
+    for (int l = 0; l < lmax; l++) {
+        std::vector<int> nodes;
+        for (int i : h->lev_nodes[l]) if (h->lch[i] >= 0) nodes.push_back(i);
+        if (nodes.empty()) continue;
+        PROF_LAUNCH("divide", st, k_divide<<<(unsigned)nodes.size(), 128, 7 * rr * sizeof(double), st>>>(
+            h->d_lev_nodes[l], nn - 1, r, h->d_lch, h->d_rch, h->R, h->B, H, Bts, sqb, f->status));
+    }
+    // ---- 2. leaves
+    {
+        const size_t smem = ((size_t)h->mmax * (h->mmax | 1) + (size_t)h->mmax * r) * sizeof(double);
+        EIG_CHECK(cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PROF_LAUNCH("leaf", st, k_leaf<<<(unsigned)h->nleaves, LEAF_T, smem, st>>>(
+            r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H, Vs,
+            f->Qleaf, f->d_qoff, lamA, Wp, f->status));
+    }
+    // ---- 3. conquering stage, bottom-up over levels
+    double *dcur = lamA, *dnxt = lamB;
+    for (int l = lmax - 1; l >= 0; l--) {
+        const int nl = (int)h->lev_nodes[l].size();
+        const bool root = (l == 0);
+        const int ctot = root ? r : 2 * r;
+        PROF_LAUNCH("build", st, k_build<<<(unsigned)(nsm * 4), 256, 0, st>>>(
+            n, r, nl, h->d_lev_off[l], h->d_lev_nodes[l], nn - 1, h->d_lch, h->d_rch, h->d_size, h->R, Bts, sqb,
+            dcur, Wp, dnxt, f->P[l], WK));
+        std::swap(dcur, dnxt);
+        for (int j = 0; j < r; j++) {
+            StepF &S = f->F[l][j];
+            R1Args a;
+            a.nprob = nl; a.total = n; a.off = h->d_lev_off[l];
+            a.d = dcur; a.z = WK + (int64_t)j * n;
+            a.sqrt_rho = 1.0; a.tau = opts->tau; a.stop_c = opts->stop_c; a.max_iter = opts->max_iter;
+            a.tile_roots = opts->tile_roots;
+            a.o.lam = dnxt; a.o.dk = S.dk; a.o.zk = zk; a.o.eta = S.eta; a.o.vhat = S.vhat; a.o.bnorm = S.bnorm;
+            a.o.org = org; a.o.src = S.src; a.o.perm = perm; a.o.giv_ab = S.giv_ab; a.o.giv_cs = S.giv_cs;
+            a.o.mk = S.mk; a.o.ngiv = S.ngiv; a.o.sweeps = S.sweeps; a.o.status = f->status;
+            a.o.dorg = S.dorg; a.o.pinv = S.pinv; a.o.wsum = wsum;
+            superdc_status s1 = r1_run(a, st);
+            if (s1 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s1; }
+            const int c = ctot - (j + 1);
+            if (c > 0) {
+                superdc_status s2 = cauchy_apply_T(view(f, l, j), n, WK + (int64_t)(j + 1) * n, n,
+                                                   WK2 + (int64_t)(j + 1) * n, n, c, st);
+                if (s2 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s2; }
+                std::swap(WK, WK2);
+            }
+            std::swap(dcur, dnxt);
+        }
+        if (!root) EIG_CHECK(cudaMemcpyAsync(Wp, WK + (int64_t)r * n, (size_t)n * r * sizeof(double),
+                                             cudaMemcpyDeviceToDevice, st));
+    }
+    EIG_CHECK(cudaMemcpyAsync(lambda, dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    EIG_CHECK(cudaGetLastError());
+    int32_t word = 0;
+    EIG_CHECK(cudaMemcpyAsync(&word, f->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    EIG_CHECK(cudaStreamSynchronize(st));
+    free_tmp();
+#undef EIG_CHECK
+    f->last_stream = st;
+    *fact = f;
+    return status_from_word(word);
+}
+
+superdc_status superdc_apply_Q(const superdc_eigfact *f, int32_t trans, int64_t ncols, const double *X, int64_t ldx,
+                               double *Y, int64_t ldy, cudaStream_t st)
+{
+    if (!f || !X || !Y || ncols < 0 || (trans != 0 && trans != 1)) return SUPERDC_ERR_ARG;
+    const superdc_hss *h = f->h;
+    const int64_t n = f->n;
+    if (ldx < n || ldy < n || ncols > INT32_MAX) return SUPERDC_ERR_ARG;
+    if (ncols == 0) return SUPERDC_OK;
+    const int nc = (int)ncols;
+    const int nsm = sdc_num_sms();
+    double *B0 = nullptr, *B1 = nullptr;
+    SDC_CHECK(sdc_alloc(&B0, (size_t)n * nc, st));
+    SDC_CHECK(sdc_alloc(&B1, (size_t)n * nc, st));
+    const unsigned g = (unsigned)(nsm * 8);
+    superdc_status s = SUPERDC_OK;
+    if (trans) {
+        PROF_LAUNCH("leafapply", st, k_leaf_apply<<<(unsigned)h->nleaves, 256, 0, st>>>(
+            n, h->d_leaf_off, h->d_leaf_m, f->Qleaf, f->d_qoff, X, ldx, B0, n, nc, 1));
+        for (int l = f->lmax - 1; l >= 0 && s == SUPERDC_OK; l--) {
+            const int nl = (int)h->lev_nodes[l].size();
+            PROF_LAUNCH("permute", st, k_permute<<<g, 256, 0, st>>>(n, nl, h->d_lev_off[l], f->P[l], B0, n, B1, n,
+                                                                    nc, 0));
+            std::swap(B0, B1);
+            for (int j = 0; j < f->r && s == SUPERDC_OK; j++) {
+                s = cauchy_apply_T(view(f, l, j), n, B0, n, B1, n, nc, st);
+                std::swap(B0, B1);
+            }
+        }
+        k_copy_cols<<<g, 256, 0, st>>>(n, nc, B0, n, Y, ldy);
+    } else {
+        k_copy_cols<<<g, 256, 0, st>>>(n, nc, X, ldx, B0, n);
+        for (int l = 0; l < f->lmax && s == SUPERDC_OK; l++) {
+            const int nl = (int)h->lev_nodes[l].size();
+            for (int j = f->r - 1; j >= 0 && s == SUPERDC_OK; j--) {
+                s = cauchy_apply_N(view(f, l, j), n, B0, n, B1, n, nc, st);
+                std::swap(B0, B1);
+            }
+            PROF_LAUNCH("permute", st, k_permute<<<g, 256, 0, st>>>(n, nl, h->d_lev_off[l], f->P[l], B0, n, B1, n,
+                                                                    nc, 1));
+            std::swap(B0, B1);
+        }
+        PROF_LAUNCH("leafapply", st, k_leaf_apply<<<(unsigned)h->nleaves, 256, 0, st>>>(
+            n, h->d_leaf_off, h->d_leaf_m, f->Qleaf, f->d_qoff, B0, n, Y, ldy, nc, 0));
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(B0, st);
+    cudaFreeAsync(B1, st);
+    if (s != SUPERDC_OK) return s;
+    return e == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+}
+
+superdc_status superdc_sync_status(const superdc_eigfact *f)
+{
+    if (!f) return SUPERDC_ERR_ARG;
+    int32_t word = 0;
+    if (cudaMemcpy(&word, f->status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return SUPERDC_ERR_CUDA;
+    return status_from_word(word);
+}
+
+superdc_status superdc_eigfact_stats(const superdc_eigfact *f, int64_t *deflated, int64_t *sweeps, int32_t *max_sweeps)
+{
+    if (!f) return SUPERDC_ERR_ARG;
+    unsigned long long *acc = nullptr;
+    if (cudaMalloc(&acc, 3 * sizeof(unsigned long long)) != cudaSuccess) return SUPERDC_ERR_OOM;
+    cudaMemset(acc, 0, 3 * sizeof(unsigned long long));
+    for (int l = 0; l < f->lmax; l++)
+        for (int j = 0; j < f->r; j++)
+            k_stats<<<256, 128>>>((int64_t)f->h->lev_nodes[l].size(), f->h->d_lev_off[l], f->F[l][j].mk,
+                                  f->F[l][j].sweeps, acc);
+    unsigned long long hv[3] = {0, 0, 0};
+    cudaError_t e = cudaMemcpy(hv, acc, sizeof(hv), cudaMemcpyDeviceToHost);
+    cudaFree(acc);
+    if (e != cudaSuccess) return SUPERDC_ERR_CUDA;
+    if (deflated) *deflated = (int64_t)hv[0];
+    if (sweeps) *sweeps = (int64_t)hv[1];
+    if (max_sweeps) *max_sweeps = (int32_t)hv[2];
+    return SUPERDC_OK;
+}
+
+superdc_status superdc_eigfact_get(const superdc_eigfact *f, int32_t level, int32_t step, const char *field,
+                                   void *dst)
+{
+    if (!f || !field || !dst || level < 0 || level >= f->lmax || step < 0 || step >= f->r) return SUPERDC_ERR_ARG;
+    const StepF &S = f->F[level][step];
+    const int64_t n = f->n, np = (int64_t)f->h->lev_nodes[level].size();
+    const void *src = nullptr;
+    size_t bytes = 0;
+    std::string fld(field);
+    if (fld == "dk") { src = S.dk; bytes = n * 8; }
+    else if (fld == "eta") { src = S.eta; bytes = n * 8; }
+    else if (fld == "dorg") { src = S.dorg; bytes = n * 8; }
+    else if (fld == "vhat") { src = S.vhat; bytes = n * 8; }
+    else if (fld == "bnorm") { src = S.bnorm; bytes = n * 8; }
+    else if (fld == "src") { src = S.src; bytes = n * 4; }
+    else if (fld == "pinv") { src = S.pinv; bytes = n * 4; }
+    else if (fld == "P") { src = f->P[level]; bytes = n * 4; }
+    else if (fld == "giv_cs") { src = S.giv_cs; bytes = 2 * n * 8; }
+    else if (fld == "giv_ab") { src = S.giv_ab; bytes = 2 * n * 4; }
+    else if (fld == "mk") { src = S.mk; bytes = np * 4; }
+    else if (fld == "ngiv") { src = S.ngiv; bytes = np * 4; }
+    else return SUPERDC_ERR_ARG;
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+}
+
+superdc_status superdc_eigfact_shape(const superdc_eigfact *f, int32_t *lmax, int32_t *r, int64_t *n)
+{
+    if (!f) return SUPERDC_ERR_ARG;
+    if (lmax) *lmax = f->lmax;
+    if (r) *r = f->r;
+    if (n) *n = f->n;
+    return SUPERDC_OK;
+}
+
+}  // extern "C"

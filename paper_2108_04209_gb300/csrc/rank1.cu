@@ -639,6 +639,7 @@ __global__ void k_merge(int64_t nprob, const int64_t *__restrict__ off, int64_t 
         }
         o.lam[b0 + pos] = val;
         o.perm[b0 + pos] = s;
+        o.pinv[b0 + s] = pos;
     }
 }
 

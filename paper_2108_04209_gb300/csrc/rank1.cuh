@@ -10,6 +10,7 @@ struct R1Out {
     double *giv_cs;
     int32_t *mk, *ngiv, *sweeps, *status;
     double *dorg;   // d_{K} of every kept root (scratch or stored), total entries
+    int32_t *pinv;  // merged position of every slot (inverse of perm), total entries
     double *wsum;   // sum of kept z^2 per problem (scratch), nprob entries
 };
 

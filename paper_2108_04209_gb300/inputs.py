@@ -143,19 +143,26 @@ def _qfactor(g):
     return q
 
 
+def _expm(S):
+    from scipy.linalg import expm
+    return expm(S)
+
+
 def hss_random(n: int, leaf: int, rank: int, seed: int, bscale: float = 1.0,
-               clustered: bool = False) -> HSS:
+               clustered: bool = False, tilt: float = 1e-5) -> HSS:
     """Random symmetric HSS matrix as in the plain configurations.
 
-    * leaf D = (G + G^T)/2, G ~ N(0,1)  (or, with ``clustered``, a leaf with a
-      clustered spectrum: V diag(mu) V^T, V Haar, mu = N(0,1) values each
-      repeated 4 times plus U[0, 1e-12] offsets);
+    * leaf D = (G + G^T)/2, G ~ N(0,1);
+    * with ``clustered``: leaf D = V diag(mu) V^T with V = [U_k, U_perp] exp(S):
+      r eigenvalues N(0,1) on span(U_k); the other m - r eigenvalues are N(0,1)
+      values repeated 4 times plus U[0, 1e-12] offsets; U_perp completes U_k
+      to an orthonormal basis (QR of [U_k, N(0,1)]); S is skew-symmetric with
+      N(0, tilt^2) entries (tilt = 1e-5), tilting the clustered eigenvectors
+      slightly into span(U_k) so that they reach the rank-one updates;
     * leaf U = Q-factor of an m x r N(0,1) matrix;
-    * for a non-leaf non-root node k with children c1, c2: [R_c1; R_c2] =
-      Q-factor of a 2r x r N(0,1) matrix (so every nested U_k is orthonormal);
-    * for a non-leaf node: B of its left child = G diag(2^0, 2^-1, ..., 2^-(r-1)),
-      G ~ N(0,1), times ``bscale``.
-    Draw order: nodes in postorder; leaf: D then U; non-leaf: R pair (non-root), then B.
+    Draw order: nodes in postorder; leaf: D then U (clustered: U, then the
+    completion, cluster values, offsets, span(U) values, S); non-leaf: R pair
+    (non-root), then B.
     """
     tree = perfect_tree(n, leaf, rank)
     rng = np.random.default_rng(seed)
@@ -166,16 +173,22 @@ def hss_random(n: int, leaf: int, rank: int, seed: int, bscale: float = 1.0,
         m = int(tree.leaf_size[i])
         if tree.lchild[i] < 0:
             if clustered:
-                base = rng.standard_normal((m + 3) // 4)
-                mu = np.repeat(base, 4)[:m] + rng.uniform(0.0, 1e-12, m)
-                V = _qfactor(rng.standard_normal((m, m)))
-                Dl = (V * mu) @ V.T
+                Ul = _qfactor(rng.standard_normal((m, rank)))
+                full = _qfactor(np.hstack([Ul, rng.standard_normal((m, m - rank))]))
+                base = rng.standard_normal((m - rank + 3) // 4)
+                mu = np.repeat(base, 4)[:m - rank] + rng.uniform(0.0, 1e-12, m - rank)
+                muU = rng.standard_normal(rank)
+                Sk = rng.standard_normal((m, m)) * tilt
+                Sk = Sk - Sk.T
+                V = np.hstack([Ul, full[:, rank:]]) @ _expm(Sk)
+                Dl = (V * np.concatenate([muU, mu])) @ V.T
                 Dl = 0.5 * (Dl + Dl.T)
+                h.leaf_D(i)[:, :] = Dl
+                h.leaf_U(i)[:, :] = Ul
             else:
                 G = rng.standard_normal((m, m))
-                Dl = 0.5 * (G + G.T)
-            h.leaf_D(i)[:, :] = Dl
-            h.leaf_U(i)[:, :] = _qfactor(rng.standard_normal((m, rank)))
+                h.leaf_D(i)[:, :] = 0.5 * (G + G.T)
+                h.leaf_U(i)[:, :] = _qfactor(rng.standard_normal((m, rank)))
         else:
             c1, c2 = int(tree.lchild[i]), int(tree.rchild[i])
             if i != tree.root:

@@ -1,0 +1,135 @@
+"""GPU parity of the HSS eigendecomposition (C-ABI superdc_build_hss /
+superdc_eig / superdc_apply_Q) against the CPU oracle (Algorithms 1, 3, 4)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2108_04209_gb300 as sdc  # noqa: E402
+from paper_2108_04209_gb300 import inputs  # noqa: E402
+from oracle import dense, superdc as osd  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+LAM_RTOL = 1e-10      # spec eigenvalue bound
+METRIC_TOL = 1e-12    # residual and orthogonality (the paper's gamma, theta)
+
+
+def lam_close(lam, ref, anorm):
+    return np.all(np.abs(lam - ref) <= LAM_RTOL * np.maximum(np.abs(ref), 1e-6 * anorm))
+
+
+def gpu_eig(h, tau=1e-10):
+    H = sdc.HSSMatrix(h)
+    lam, F = H.eig(sdc.default_opts(tau=tau))
+    return H, lam.cpu().numpy(), F
+
+
+def dense_Q(F, n):
+    I = torch.eye(n, dtype=torch.float64, device="cuda")
+    return F.apply_Q(I, trans=False).cpu().numpy(), F.apply_Q(I, trans=True).cpu().numpy()
+
+
+def test_small_hss_vs_oracle_and_dense():
+    h = inputs.cfg_small_hss()
+    A = dense.dense_from_hss(h)
+    H, lam, F = gpu_eig(h)
+    O = osd.superdc(h, tau=1e-10, mode=0)
+    an = np.linalg.norm(A, 2)
+    assert lam_close(lam, O.eigenvalues, an), np.abs(lam - O.eigenvalues).max()
+    assert lam_close(lam, np.linalg.eigvalsh(A), an)
+    Q, QT = dense_Q(F, h.tree.n)
+    assert np.abs(QT - Q.T).max() < 1e-13
+    assert dense.gamma(A, lam, Q) <= METRIC_TOL
+    assert dense.theta(Q) <= METRIC_TOL
+    # unnormalised too
+    assert np.abs(Q.T @ Q - np.eye(h.tree.n)).max() < 1e-12
+    assert np.abs(A @ Q - Q * lam).max() / an < 1e-12
+
+
+def test_per_node_deflation_and_permutations_vs_oracle():
+    """Deflation decisions (kept sets, rotation pairs) and the tree permutations
+    P_p agree node by node with the oracle (the two form Zhat by different
+    routes, so decisions may differ only when a test sits at its threshold)."""
+    h = inputs.hss_random(1024, 32, 4, seed=7, clustered=True)
+    H, lam, F = gpu_eig(h)
+    O = osd.superdc(h, tau=1e-10, mode=0)
+    t = h.tree
+    for lev in range(F.lmax):
+        P = F.get(lev, 0, "P")
+        nodes = sorted([i for i in range(t.nnodes) if t.level[i] == lev], key=lambda i: t.offset[i])
+        for q, node in enumerate(nodes):
+            o, m = int(t.offset[node]), int(t.leaf_size[node])
+            assert np.array_equal(P[o:o + m], O.P[node]), (lev, node)
+        for j in range(F.rank):
+            mk = F.get(lev, j, "mk")
+            src = F.get(lev, j, "src")
+            ng = F.get(lev, j, "ngiv")
+            ab = F.get(lev, j, "giv_ab")
+            for q, node in enumerate(nodes):
+                o, m = int(t.offset[node]), int(t.leaf_size[node])
+                fo = O.fac[node][j]
+                assert mk[q] == fo.mk, (lev, node, j, mk[q], fo.mk)
+                assert np.array_equal(src[o:o + mk[q]], fo.kidx)
+                assert ng[q] == len(fo.giv[0])
+                if ng[q]:
+                    pairs = ab[2 * o:2 * o + 2 * ng[q]].reshape(-1, 2)
+                    assert np.array_equal(pairs[:, 0], fo.giv[0]) and np.array_equal(pairs[:, 1], fo.giv[1])
+    an = np.abs(O.eigenvalues).max()
+    assert lam_close(lam, O.eigenvalues, an)
+
+
+def test_tridiagonal_closed_form_gpu():
+    n = 4096
+    h = inputs.hss_tridiag(n, 64)
+    H, lam, F = gpu_eig(h)
+    k = np.arange(1, n + 1)
+    exact = np.sort(3.0 - 2.0 * np.cos(k * np.pi / (n + 1)))
+    assert np.abs(lam - exact).max() < 1e-12
+    X = torch.from_numpy(inputs.normal_block(n, 8, seed=5)).cuda()
+    QX = F.apply_Q(X)
+    back = F.apply_Q(QX, trans=True)
+    assert (back - X).abs().max().item() < 1e-12 * X.abs().max().item() * 10
+
+
+def test_clustered_16384_vs_oracle_probes():
+    """Clustered leaf spectra at n=16384 (leaf 64, rank 8): eigenvalues against
+    the oracle; residual and orthogonality through 64 probe columns."""
+    h = inputs.cfg_clustered_16384()
+    H, lam, F = gpu_eig(h)
+    O = osd.superdc(h, tau=1e-10, mode=1)
+    an = max(np.abs(O.eigenvalues).max(), 1.0)
+    assert lam_close(lam, O.eigenvalues, an), np.abs(lam - O.eigenvalues).max()
+    n = h.tree.n
+    Xn = inputs.normal_block(n, 64, seed=102)
+    X = torch.from_numpy(Xn).cuda()
+    QX = F.apply_Q(X).cpu().numpy()
+    QLX = F.apply_Q(torch.from_numpy(lam[:, None] * Xn).cuda()).cpu().numpy()
+    res = np.linalg.norm(dense.hss_matvec(h, QX) - QLX) / (an * np.linalg.norm(Xn))
+    orth = (F.apply_Q(torch.from_numpy(QX).cuda(), trans=True).cpu().numpy() - Xn)
+    assert res < 1e-12 * np.sqrt(n)
+    assert np.linalg.norm(orth) / np.linalg.norm(Xn) < 1e-12 * np.sqrt(n)
+    st = F.stats()
+    assert st["deflated"] > 0
+
+
+def test_full_size_131072_invariants_and_probes():
+    """n=131072, leaf 128, rank 10: trace and Frobenius invariants from the
+    generators, residual and orthogonality on a 131072 x 64 N(0,1) block."""
+    h = inputs.cfg_large_131072()
+    H, lam, F = gpu_eig(h)
+    tr = dense.trace_from_generators(h)
+    fro2 = dense.fro2_from_generators(h)
+    assert np.all(np.diff(lam) >= 0)
+    assert abs(lam.sum() - tr) <= 1e-10 * np.abs(lam).sum()
+    assert abs((lam ** 2).sum() - fro2) <= 1e-10 * fro2
+    n = h.tree.n
+    Xn = inputs.normal_block(n, 64, seed=104)
+    X = torch.from_numpy(Xn).cuda()
+    QX = F.apply_Q(X).cpu().numpy()
+    QLX = F.apply_Q(torch.from_numpy(lam[:, None] * Xn).cuda()).cpu().numpy()
+    an = np.abs(lam).max()
+    res = np.linalg.norm(dense.hss_matvec(h, QX) - QLX) / (an * np.linalg.norm(Xn))
+    orth = F.apply_Q(torch.from_numpy(QX).cuda(), trans=True).cpu().numpy() - Xn
+    assert res < 1e-12 * np.sqrt(n)
+    assert np.linalg.norm(orth) / np.linalg.norm(Xn) < 1e-12 * np.sqrt(n)

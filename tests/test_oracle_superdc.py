@@ -127,3 +127,10 @@ def test_clustered_leaves_deflate():
     Q = sd.superdcmv(F, h.tree.root, np.eye(1024), 0)
     assert dense.theta(Q) < 1e-15
     assert dense.gamma(A, F.eigenvalues, Q) < 1e-12
+
+
+def test_hss_matvec_vs_dense():
+    for h in (inputs.hss_random(512, 32, 4, seed=0), inputs.hss_tridiag(256, 16)):
+        A = dense.dense_from_hss(h)
+        X = np.random.default_rng(1).standard_normal((h.tree.n, 3))
+        assert np.abs(dense.hss_matvec(h, X) - A @ X).max() < 1e-13 * np.abs(A).max() * 10
