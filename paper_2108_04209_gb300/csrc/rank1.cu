@@ -25,10 +25,12 @@
 #include "common.cuh"
 #include "rank1.cuh"
 #include "prof.cuh"
+#include <algorithm>
 
 namespace {
 
 constexpr int SEC_CHUNK = 2048;   // poles staged per shared-memory chunk
+constexpr int DEFL_BIG = 128;     // problems larger than this deflate with a whole CTA
 
 // ---------------------------------------------------------------------------
 // FP64 reciprocal without the FP64 divide sequence.  The GB300 FP64 pipe
@@ -114,6 +116,7 @@ __global__ void k_deflate(int64_t nprob, const int64_t *__restrict__ off,
     if (p >= nprob) return;
     const int64_t b0 = off[p];
     const int m = (int)(off[p + 1] - b0);
+    if (m > DEFL_BIG) return;            // handled by k_deflate_big
     bool bad = false;
     for (int i = 0; i < m; i++) {
         double di = d[b0 + i], zi = z[b0 + i] * sqrt_rho;
@@ -195,6 +198,197 @@ __global__ void k_deflate(int64_t nprob, const int64_t *__restrict__ off,
     o.mk[p] = mk;
     o.ngiv[p] = ng;
     o.wsum[p] = W;
+}
+
+
+// ---------------------------------------------------------------------------
+// Deflation of large problems, one CTA (DB_T threads) per problem: the
+// |z| < tau mask and the compactions run in parallel; the Givens scan, whose
+// every test depends on the previous rotation, runs in warp 0 over the
+// survivors, 32 at a time broadcast from registers.  The arithmetic is the
+// same explicitly rounded sequence as k_deflate, so decisions and rotated
+// values agree bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int DB_T = 512;
+
+// exclusive block scan of one int per thread; returns the prefix, *total = sum
+__device__ __forceinline__ int block_exscan(int v, int *sh, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = (lane < DB_T / 32) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;   // inclusive warp totals
+    }
+    __syncthreads();
+    const int before = (warp > 0) ? sh[warp - 1] : 0;
+    *total = sh[DB_T / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(DB_T)
+k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__restrict__ d,
+              const double *__restrict__ z, double sqrt_rho, double tau, double *__restrict__ wd,
+              double *__restrict__ wz, int8_t *__restrict__ kept, int32_t *__restrict__ surv, R1Out o)
+{
+    __shared__ int sh[32];
+    __shared__ int s_bad, s_ng;
+    __shared__ double s_w[DB_T / 32];
+    const int64_t p = blockIdx.x;
+    if (p >= nprob) return;
+    const int64_t b0 = off[p];
+    const int m = (int)(off[p + 1] - b0);
+    if (m <= DEFL_BIG) return;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    // A: copy, mask, survivor list
+    int S = 0;
+    for (int c = 0; c < m; c += DB_T) {
+        const int i = c + tid;
+        int keep = 0;
+        if (i < m) {
+            double di = d[b0 + i], zi = z[b0 + i] * sqrt_rho;
+            if (!isfinite(di) || !isfinite(zi)) s_bad = 1;
+            keep = !(fabs(zi) < tau);
+            wd[b0 + i] = di;
+            wz[b0 + i] = keep ? zi : 0.0;
+            kept[b0 + i] = (int8_t)keep;
+        }
+        int tot;
+        int pre = block_exscan(keep, sh, &tot);
+        if (keep) surv[b0 + S + pre] = i;
+        S += tot;
+    }
+    __syncthreads();
+    if (tid == 0 && s_bad) sdc_latch(o.status, SUPERDC_DEV_NONFINITE);
+    // B: Givens scan over the survivors (warp 0)
+    if (tid < 32) {
+        const int lane = tid;
+        int ng = 0;
+        bool has_a = false;
+        int ia = 0;
+        double da = 0.0, za = 0.0;
+        for (int c = 0; c < S; c += 32) {
+            int idx = 0;
+            double dv = 0.0, zv = 0.0;
+            if (c + lane < S) {
+                idx = surv[b0 + c + lane];
+                dv = wd[b0 + idx];
+                zv = wz[b0 + idx];
+            }
+            const int cnt = min(32, S - c);
+            for (int t = 0; t < cnt; t++) {
+                const int ib = __shfl_sync(0xffffffffu, idx, t);
+                double db = __shfl_sync(0xffffffffu, dv, t);
+                double zb = __shfl_sync(0xffffffffu, zv, t);
+                if (has_a) {
+                    double lhs = fabs(__dmul_rn(__dmul_rn(__dsub_rn(da, db), za), zb));
+                    double nrm2 = __dadd_rn(__dmul_rn(za, za), __dmul_rn(zb, zb));
+                    double rhs = __dmul_rn(nrm2, tau);
+                    if (lhs < rhs) {
+                        double r = __dsqrt_rn(nrm2);
+                        double cc0 = __ddiv_rn(zb, r), ss0 = __ddiv_rn(za, r);
+                        double cc = __dmul_rn(cc0, cc0), ss = __dmul_rn(ss0, ss0);
+                        double na = __dadd_rn(__dmul_rn(cc, da), __dmul_rn(ss, db));
+                        double nb = __dadd_rn(__dmul_rn(ss, da), __dmul_rn(cc, db));
+                        if (lane == 0) {
+                            wd[b0 + ia] = na;
+                            wz[b0 + ia] = 0.0;
+                            kept[b0 + ia] = 0;
+                            wd[b0 + ib] = nb;
+                            wz[b0 + ib] = r;
+                            o.giv_ab[2 * (b0 + ng)] = ia;
+                            o.giv_ab[2 * (b0 + ng) + 1] = ib;
+                            o.giv_cs[2 * (b0 + ng)] = cc0;
+                            o.giv_cs[2 * (b0 + ng) + 1] = ss0;
+                        }
+                        ng++;
+                        db = nb;
+                        zb = r;
+                    }
+                }
+                ia = ib; da = db; za = zb; has_a = true;
+            }
+        }
+        if (lane == 0) s_ng = ng;
+    }
+    __syncthreads();
+    // C: compaction, kept slots in index order, then deflated slots in index order
+    int mk = 0;
+    double wpart = 0.0;
+    for (int c = 0; c < m; c += DB_T) {
+        const int i = c + tid;
+        const int k = (i < m) ? (int)kept[b0 + i] : 0;
+        int tot;
+        int pre = block_exscan(k, sh, &tot);
+        if (k) {
+            double zi = wz[b0 + i];
+            o.dk[b0 + mk + pre] = wd[b0 + i];
+            o.zk[b0 + mk + pre] = zi;
+            o.src[b0 + mk + pre] = i;
+            wpart = __dadd_rn(wpart, __dmul_rn(zi, zi));
+        }
+        mk += tot;
+    }
+    int nd = 0;
+    for (int c = 0; c < m; c += DB_T) {
+        const int i = c + tid;
+        const int dflt = (i < m) ? (int)(kept[b0 + i] == 0) : 0;
+        int tot;
+        int pre = block_exscan(dflt, sh, &tot);
+        if (dflt) {
+            o.dk[b0 + mk + nd + pre] = wd[b0 + i];
+            o.src[b0 + mk + nd + pre] = i;
+        }
+        nd += tot;
+    }
+    // deterministic sum of kept z^2
+    for (int of = 16; of > 0; of >>= 1) wpart += __shfl_xor_sync(0xffffffffu, wpart, of);
+    if ((tid & 31) == 0) s_w[tid >> 5] = wpart;
+    __syncthreads();
+    // D: deflated values sorted by (value, index): they are in index order and
+    // out of order only inside tau-sized intervals, so insertion is short
+    if (tid == 0) {
+        double W = 0.0;
+        for (int w = 0; w < DB_T / 32; w++) W += s_w[w];
+        o.wsum[p] = W;
+        o.mk[p] = mk;
+        o.ngiv[p] = s_ng;
+        for (int q = mk + 1; q < m; q++) {
+            double v = o.dk[b0 + q];
+            int sv = o.src[b0 + q];
+            int s2 = q;
+            while (s2 > mk && o.dk[b0 + s2 - 1] > v) {
+                o.dk[b0 + s2] = o.dk[b0 + s2 - 1];
+                o.src[b0 + s2] = o.src[b0 + s2 - 1];
+                s2--;
+            }
+            o.dk[b0 + s2] = v;
+            o.src[b0 + s2] = sv;
+        }
+    }
+    __syncthreads();
+    for (int s2 = mk + tid; s2 < m; s2 += DB_T) {
+        o.zk[b0 + s2] = 0.0;
+        o.org[b0 + s2] = -1;
+        o.eta[b0 + s2] = 0.0;
+        o.dorg[b0 + s2] = o.dk[b0 + s2];
+        o.vhat[b0 + s2] = 0.0;
+        o.bnorm[b0 + s2] = 1.0;
+        if (o.sweeps) o.sweeps[b0 + s2] = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -362,8 +556,8 @@ struct Root {
 constexpr int SEC_UNIT_BIG = 2048;
 constexpr int SORT_MAX = 8192;
 
-__global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int4 *__restrict__ units,
-                        int *__restrict__ nunits, int *__restrict__ counter)
+__global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int ubig, int whole_small,
+                        int4 *__restrict__ units, int *__restrict__ nunits, int *__restrict__ counter)
 {
     extern __shared__ unsigned long long keys[];   // SORT_MAX entries when sorting
     __shared__ int part[1024];
@@ -400,7 +594,7 @@ __global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int4 *__r
     for (int64_t q = beg; q < end; q++) {
         int64_t pp = sorted ? (int64_t)(0xFFFFFFFFu - (unsigned)(keys[q] & 0xFFFFFFFFull)) : q;
         int m = mk[pp];
-        cnt += (m <= SEC_CHUNK) ? (m > 0) : (m + SEC_UNIT_BIG - 1) / SEC_UNIT_BIG;
+        cnt += (whole_small && m <= SEC_CHUNK) ? (m > 0) : (m + ubig - 1) / ubig;
     }
     part[threadIdx.x] = cnt;
     __syncthreads();
@@ -416,21 +610,28 @@ __global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int4 *__r
         int64_t pp = sorted ? (int64_t)(0xFFFFFFFFu - (unsigned)(keys[q] & 0xFFFFFFFFull)) : q;
         int m = mk[pp];
         if (m <= 0) continue;
-        if (m <= SEC_CHUNK) {
+        if (whole_small && m <= SEC_CHUNK) {
             units[u++] = make_int4((int)pp, 0, m, 0);
         } else {
-            for (int r = 0; r < m; r += SEC_UNIT_BIG) units[u++] = make_int4((int)pp, r, min(m, r + SEC_UNIT_BIG), 0);
+            for (int r = 0; r < m; r += ubig) units[u++] = make_int4((int)pp, r, min(m, r + ubig), 0);
         }
     }
 }
 
-// One CTA of NW warps per unit, persistent over an atomic unit queue.  Each
-// warp owns a contiguous quarter (1/NW) of the unit's roots; a lane whose root
-// has converged takes the next root of the warp's range, so the FP64 pipe
-// keeps working on live roots instead of waiting for the slowest root of a
-// fixed group of 32.  The live roots of a warp stay inside a short window, so
-// the psi/phi split keeps its three warp-uniform regions.
-template <int NW>
+// One CTA of NW warps per unit, persistent over an atomic unit queue.
+//
+// SPLIT = false (many roots per launch, e.g. thousands of independent
+// problems): each warp owns a contiguous 1/NW of the unit's roots; a lane
+// whose root has converged takes the next root of the warp's range, so the
+// FP64 pipe keeps working on live roots instead of waiting for the slowest
+// root of a fixed group of 32.
+// SPLIT = true (few large problems, e.g. the top levels of the tree): the NW
+// warps share one 32-lane root range and split the poles NW ways; the partial
+// sums are reduced through shared memory after every sweep and each warp
+// applies the same update, so the replicated root state stays identical.
+// Both keep the live roots of a warp inside a short window, so the psi/phi
+// split keeps its three warp-uniform regions.
+template <int NW, bool SPLIT>
 __global__ void __launch_bounds__(NW * 32)
 k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
           const int *__restrict__ nunits, int *__restrict__ counter,
@@ -438,6 +639,7 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
 {
     __shared__ double sd[SEC_CHUNK];
     __shared__ double sw[SEC_CHUNK];
+    __shared__ double red[SPLIT ? NW : 1][4][32];
     __shared__ int s_unit;
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -456,8 +658,8 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
         const double W = o.wsum[p];
         const double tol = stop_c * (double)m * SDC_EPS;
         const int len = U.z - U.y;
-        const int wbeg = U.y + (int)(((int64_t)len * warp) / NW);
-        const int wend = U.y + (int)(((int64_t)len * (warp + 1)) / NW);
+        const int wbeg = SPLIT ? U.y : U.y + (int)(((int64_t)len * warp) / NW);
+        const int wend = SPLIT ? U.z : U.y + (int)(((int64_t)len * (warp + 1)) / NW);
         int k = wbeg + lane;
         bool act = k < wend;
         int next = wbeg + 32;
@@ -473,19 +675,17 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
             }
         }
         __syncthreads();
-        while (single ? __any_sync(FULL, act) : __syncthreads_or(act)) {
+        const bool lockstep = SPLIT || !single;
+        while (lockstep ? __syncthreads_or(act) : __any_sync(FULL, act)) {
             const int kwlo = __reduce_min_sync(FULL, act ? k : 0x7fffffff);
             const int kwhi = __reduce_max_sync(FULL, act ? k : -1);
             const int kk = act ? k : kwlo;
             const bool p0 = __all_sync(FULL, !act || R.phase == 0);
+            const bool any = __any_sync(FULL, act);
             Acc A = {0.0, 0.0, 0.0, 0.0};
-            if (single) {
-                if (p0) sweep<false>(sd, sw, 0, m, 0, kk, kwlo, kwhi, R.dK, R.y, A);
-                else    sweep<true>(sd, sw, 0, m, 0, kk, kwlo, kwhi, R.dK, R.y, A);
-            } else {
-                const bool any = __any_sync(FULL, act);
-                for (int c0 = 0; c0 < m; c0 += SEC_CHUNK) {
-                    const int cn = min(SEC_CHUNK, m - c0);
+            for (int c0 = 0; c0 < m; c0 += SEC_CHUNK) {
+                const int cn = min(SEC_CHUNK, m - c0);
+                if (!single) {
                     __syncthreads();
                     for (int j = threadIdx.x; j < cn; j += NW * 32) {
                         sd[j] = dk[c0 + j];
@@ -493,16 +693,35 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
                         sw[j] = zj * zj;
                     }
                     __syncthreads();
-                    if (any) {
-                        if (p0) sweep<false>(sd, sw, 0, cn, c0, kk, kwlo, kwhi, R.dK, R.y, A);
-                        else    sweep<true>(sd, sw, 0, cn, c0, kk, kwlo, kwhi, R.dK, R.y, A);
-                    }
                 }
+                const int j0 = SPLIT ? (int)(((int64_t)cn * warp) / NW) : 0;
+                const int j1 = SPLIT ? (int)(((int64_t)cn * (warp + 1)) / NW) : cn;
+                if (any) {
+                    if (p0) sweep<false>(sd, sw, j0, j1, c0, kk, kwlo, kwhi, R.dK, R.y, A);
+                    else    sweep<true>(sd, sw, j0, j1, c0, kk, kwlo, kwhi, R.dK, R.y, A);
+                }
+            }
+            if (SPLIT) {
+                red[SPLIT ? warp : 0][0][lane] = A.psi;
+                red[SPLIT ? warp : 0][1][lane] = A.phi;
+                red[SPLIT ? warp : 0][2][lane] = A.dpsi;
+                red[SPLIT ? warp : 0][3][lane] = A.dphi;
+                __syncthreads();
+                Acc T = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+                for (int w = 0; w < (SPLIT ? NW : 1); w++) {      // same order in every warp
+                    T.psi += red[w][0][lane];
+                    T.phi += red[w][1][lane];
+                    T.dpsi += red[w][2][lane];
+                    T.dphi += red[w][3][lane];
+                }
+                A = T;
+                __syncthreads();
             }
             bool fin = false;
             if (act) {
                 fin = R.update(A, tol, max_iter, o.status);
-                if (fin) {
+                if (fin && (!SPLIT || warp == 0)) {
                     o.org[b0 + k] = R.K;
                     o.eta[b0 + k] = R.y;
                     o.dorg[b0 + k] = R.dK;
@@ -658,9 +877,11 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     SDC_CHECK(sdc_alloc(&wz, a.total, st));
     SDC_CHECK(sdc_alloc(&kept, a.total, st));
     SDC_CHECK(sdc_alloc(&tile_off, a.nprob + 1, st));
+    int32_t *surv = nullptr;
+    SDC_CHECK(sdc_alloc(&surv, a.total, st));
     int4 *units = nullptr;
     int *ucount = nullptr;
-    SDC_CHECK(sdc_alloc(&units, a.nprob + a.total / SEC_UNIT_BIG + 2, st));
+    SDC_CHECK(sdc_alloc(&units, a.nprob + a.total / 32 + 2, st));
     SDC_CHECK(sdc_alloc(&ucount, 2, st));
     static bool attr_done = false;
     if (!attr_done) {
@@ -672,13 +893,30 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     const int tpb = 128;
     PROF_LAUNCH("deflate", st, k_deflate<<<(unsigned)((a.nprob + tpb - 1) / tpb), tpb, 0, st>>>(
         a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau, wd, wz, kept, a.o));
+    if (a.total > DEFL_BIG)
+        PROF_LAUNCH("deflate", st, k_deflate_big<<<(unsigned)a.nprob, DB_T, 0, st>>>(
+            a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau, wd, wz, kept, surv, a.o));
     const int TR = 128;
     PROF_LAUNCH("tiles", st, k_tiles<<<1, 1024, 0, st>>>(a.nprob, a.o.mk, TR, tile_off));
     const unsigned grid = (unsigned)(nsm * 8);
     const size_t ksm = (a.nprob <= SORT_MAX) ? (size_t)SORT_MAX * sizeof(unsigned long long) : 0;
-    PROF_LAUNCH("units", st, k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, units, ucount, ucount + 1));
-    PROF_LAUNCH("secular", st, k_secular<4><<<(unsigned)(nsm * 6), 128, 0, st>>>(a.off, units, ucount, ucount + 1,
-                                                                           a.o, a.stop_c, a.max_iter));
+    // Scheduling: with many roots per CTA slot, whole problems (or 2048-root
+    // pieces) go to CTAs whose warps own separate root ranges; with few roots
+    // per slot (the top levels of a tree), units shrink so every SM gets work
+    // and the warps of a CTA split the poles instead of the roots.
+    const int slots = nsm * 6;
+    const int64_t per = a.total / slots;
+    const bool split = per < 512;
+    int ubig = SEC_UNIT_BIG;
+    if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
+    PROF_LAUNCH("units", st, k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, ubig, split ? 0 : 1, units, ucount,
+                                                           ucount + 1));
+    if (split)
+        PROF_LAUNCH("secular", st, (k_secular<4, true><<<(unsigned)slots, 128, 0, st>>>(
+                                       a.off, units, ucount, ucount + 1, a.o, a.stop_c, a.max_iter)));
+    else
+        PROF_LAUNCH("secular", st, (k_secular<4, false><<<(unsigned)slots, 128, 0, st>>>(
+                                       a.off, units, ucount, ucount + 1, a.o, a.stop_c, a.max_iter)));
     PROF_LAUNCH("lowner", st, k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o));
     PROF_LAUNCH("bnorm", st, k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o));
     PROF_LAUNCH("merge", st, k_merge<<<(unsigned)(nsm * 8), 256, 0, st>>>(a.nprob, a.off, a.total, a.o));
@@ -689,6 +927,7 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     SDC_CHECK(cudaFreeAsync(kept, st));
     SDC_CHECK(cudaFreeAsync(tile_off, st));
     SDC_CHECK(cudaFreeAsync(units, st));
+    SDC_CHECK(cudaFreeAsync(surv, st));
     SDC_CHECK(cudaFreeAsync(ucount, st));
     return SUPERDC_OK;
 }
