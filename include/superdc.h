@@ -124,6 +124,32 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
                                        cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * superdc_secular_batched_noalloc: the batched rank-one step of
+ * superdc_secular_batched for callers that cannot allocate device memory
+ * while they run (work recorded once and replayed from a CUDA graph, latency
+ * bound paths where an allocation may block or fail, hosts with a fixed,
+ * pre-reserved memory budget).  The paper has no counterpart; this is an
+ * interface variant only.  Same arguments, layout and results as
+ * superdc_secular_batched, but the call makes no device allocation: its
+ * scratch is a static device array of about 9 MB that every GPU which loads
+ * the library holds until the process exits.
+ *   - limits: nprob <= SDC_NOALLOC_MAX_PROB and total <= SDC_NOALLOC_MAX_TOTAL,
+ *     else SUPERDC_ERR_ARG (nothing enqueued);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current and caches it; make
+ *     that first call before any stream capture;
+ *   - all calls on a device share the array: calls whose work overlaps on the
+ *     GPU (other streams, other host threads) race and must be serialised;
+ *     nothing needs clearing between calls.
+ * -------------------------------------------------------------------- */
+#define SDC_NOALLOC_MAX_TOTAL 262144
+#define SDC_NOALLOC_MAX_PROB 16384
+superdc_status superdc_secular_batched_noalloc(int64_t nprob, const int64_t *offsets, int64_t total,
+                                               const double *d, const double *z, double rho,
+                                               const superdc_opts *opts, superdc_rank1_out *out,
+                                               cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Symmetric HSS matrix (Section 2, eq. (2.1)) and its eigendecomposition.
  *
  * Tree (HOST arrays): a postordered full binary tree with nnodes nodes, the

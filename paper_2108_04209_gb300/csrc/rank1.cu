@@ -26,6 +26,7 @@
 #include "rank1.cuh"
 #include "prof.cuh"
 #include <algorithm>
+#include <mutex>
 
 namespace {
 
@@ -929,5 +930,135 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     SDC_CHECK(cudaFreeAsync(units, st));
     SDC_CHECK(cudaFreeAsync(surv, st));
     SDC_CHECK(cudaFreeAsync(ucount, st));
+    return SUPERDC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the batched rank-one step.
+//
+// Some callers cannot allocate device memory while they run: code that is
+// recorded once into a CUDA graph and replayed, code on a real-time or
+// latency-bound path where an allocation may block or fail, and hosts whose
+// memory budget is fixed up front (a stream-ordered pool they do not own, a
+// framework that has already reserved the device).  For them the scratch of
+// the batched step lives in one statically sized device array that the
+// library reserves when it is loaded, and the entry point below never calls
+// cudaMalloc, cudaFree or any allocating routine.
+//
+// Limits: total entries <= SDC_NOALLOC_MAX_TOTAL, problems <= SDC_NOALLOC_MAX_PROB.
+// The array is shared by every call on a device and keeps the previous call's
+// contents; each call writes every scratch word before reading it (the unit
+// counter is reset by k_units), so nothing has to be cleared in between.  Two
+// calls whose work overlaps on the GPU (different streams, or different host
+// threads on one device) race on the array: serialise them.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NA_T = SDC_NOALLOC_MAX_TOTAL;
+constexpr int64_t NA_P = SDC_NOALLOC_MAX_PROB;
+constexpr size_t na_round(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t NA_WD = 0;
+constexpr size_t NA_WZ = NA_WD + na_round(NA_T * sizeof(double));
+constexpr size_t NA_DORG = NA_WZ + na_round(NA_T * sizeof(double));
+constexpr size_t NA_WSUM = NA_DORG + na_round(NA_T * sizeof(double));
+constexpr size_t NA_TILE = NA_WSUM + na_round(NA_P * sizeof(double));
+constexpr size_t NA_UNITS = NA_TILE + na_round((NA_P + 1) * sizeof(int64_t));
+constexpr size_t NA_SURV = NA_UNITS + na_round((NA_P + NA_T / 32 + 2) * sizeof(int4));
+constexpr size_t NA_PINV = NA_SURV + na_round(NA_T * sizeof(int32_t));
+constexpr size_t NA_KEPT = NA_PINV + na_round(NA_T * sizeof(int32_t));
+constexpr size_t NA_UCNT = NA_KEPT + na_round(NA_T * sizeof(int8_t));
+constexpr size_t NA_BYTES = NA_UCNT + na_round(2 * sizeof(int));
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// Device address of g_noalloc_scratch for the current device.  In host code
+// the symbol name is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress once per device (with that device current) and
+// cached.
+cudaError_t noalloc_scratch(unsigned char **ptr)
+{
+    static std::mutex mu;
+    static unsigned char *addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = (unsigned char *)p;
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const int64_t *offsets, int64_t total,
+                                                          const double *d, const double *z, double rho,
+                                                          const superdc_opts *opts, superdc_rank1_out *out,
+                                                          cudaStream_t st)
+{
+    superdc_opts def;
+    if (!opts) { superdc_opts_default(&def); opts = &def; }
+    if (nprob < 0 || total < 0 || !(rho > 0.0) || !out) return SUPERDC_ERR_ARG;
+    if (!(opts->tau >= 0.0) || !(opts->stop_c > 0.0) || opts->max_iter < 1 || opts->max_iter > 10000)
+        return SUPERDC_ERR_ARG;
+    if (nprob > NA_P || total > NA_T) return SUPERDC_ERR_ARG;   // beyond the static scratch
+    if (nprob == 0) return SUPERDC_OK;
+    if (!offsets || !d || !z) return SUPERDC_ERR_ARG;
+    if (!out->lam || !out->dk || !out->zk || !out->eta || !out->vhat || !out->bnorm || !out->org ||
+        !out->src || !out->perm || !out->giv_ab || !out->giv_cs || !out->mk || !out->ngiv || !out->status)
+        return SUPERDC_ERR_ARG;
+    unsigned char *base = nullptr;
+    SDC_CHECK(noalloc_scratch(&base));
+    R1Args a;
+    a.nprob = nprob; a.total = total; a.off = offsets; a.d = d; a.z = z;
+    a.sqrt_rho = sqrt(rho); a.tau = opts->tau; a.stop_c = opts->stop_c; a.max_iter = opts->max_iter;
+    a.tile_roots = opts->tile_roots;
+    a.o.lam = out->lam; a.o.dk = out->dk; a.o.zk = out->zk; a.o.eta = out->eta;
+    a.o.vhat = out->vhat; a.o.bnorm = out->bnorm; a.o.org = out->org; a.o.src = out->src;
+    a.o.perm = out->perm; a.o.giv_ab = out->giv_ab; a.o.giv_cs = out->giv_cs; a.o.mk = out->mk;
+    a.o.ngiv = out->ngiv; a.o.sweeps = out->sweeps; a.o.status = out->status;
+    a.o.dorg = (double *)(base + NA_DORG);
+    a.o.wsum = (double *)(base + NA_WSUM);
+    a.o.pinv = (int32_t *)(base + NA_PINV);
+    double *wd = (double *)(base + NA_WD), *wz = (double *)(base + NA_WZ);
+    int8_t *kept = (int8_t *)(base + NA_KEPT);
+    int64_t *tile_off = (int64_t *)(base + NA_TILE);
+    int32_t *surv = (int32_t *)(base + NA_SURV);
+    int4 *units = (int4 *)(base + NA_UNITS);
+    int *ucount = (int *)(base + NA_UCNT);
+    SDC_CHECK(cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(SORT_MAX * sizeof(unsigned long long))));
+    const int nsm = sdc_num_sms();
+    const int tpb = 128;
+    k_deflate<<<(unsigned)((a.nprob + tpb - 1) / tpb), tpb, 0, st>>>(a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau,
+                                                                      wd, wz, kept, a.o);
+    if (a.total > DEFL_BIG)
+        k_deflate_big<<<(unsigned)a.nprob, DB_T, 0, st>>>(a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau, wd, wz,
+                                                           kept, surv, a.o);
+    const int TR = 128;
+    k_tiles<<<1, 1024, 0, st>>>(a.nprob, a.o.mk, TR, tile_off);
+    const unsigned grid = (unsigned)(nsm * 8);
+    const size_t ksm = (a.nprob <= SORT_MAX) ? (size_t)SORT_MAX * sizeof(unsigned long long) : 0;
+    const int slots = nsm * 6;
+    const int64_t per = a.total / slots;
+    const bool split = per < 512;
+    int ubig = SEC_UNIT_BIG;
+    if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
+    k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, ubig, split ? 0 : 1, units, ucount, ucount + 1);
+    if (split)
+        k_secular<4, true><<<(unsigned)slots, 128, 0, st>>>(a.off, units, ucount, ucount + 1, a.o, a.stop_c,
+                                                             a.max_iter);
+    else
+        k_secular<4, false><<<(unsigned)slots, 128, 0, st>>>(a.off, units, ucount, ucount + 1, a.o, a.stop_c,
+                                                              a.max_iter);
+    k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o);
+    k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o);
+    k_merge<<<(unsigned)(nsm * 8), 256, 0, st>>>(a.nprob, a.off, a.total, a.o);
+    SDC_CHECK(cudaGetLastError());
     return SUPERDC_OK;
 }
