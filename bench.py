@@ -213,7 +213,8 @@ def main():
     offs = torch.from_numpy(batch.offsets).to(dev)
     d = torch.from_numpy(batch.d).to(dev)
     z = torch.from_numpy(batch.z).to(dev)
-    opts = sdc.default_opts(tau=1e-12)
+    from paper_2108_04209_gb300.autotune import tune_secular
+    opts, tune_ms = tune_secular(offs, d, z, 1.0, tau=1e-12, use_cache=False)
     out = sdc.alloc_rank1_out(batch.nprob, total, dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     lib = L.lib()
@@ -251,6 +252,51 @@ def main():
         lib.superdc_profile_read(name.encode(), ctypes.byref(n_), ctypes.byref(t_))
         kern[name] = (n_.value, t_.value)
     launches = sum(v[0] for v in kern.values())
+
+    # the same step captured once into a CUDA graph and replayed
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        sdc.secular_batched(offs, d, z, 1.0, opts, out=out, check=False)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            sdc.secular_batched(offs, d, z, 1.0, opts, out=out, check=False)
+        g.replay()
+        torch.cuda.synchronize()
+        gt = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            e1.synchronize()
+            gt += e0.elapsed_time(e1)
+        sdc.check_status(out["status"], "graph replay")
+        graph_ms = gt / args.steps
+        del g
+    except Exception as ex:      # report, do not hide
+        graph_ms = "capture failed: %s" % ex
+
+    # unbatched baseline: the first problems launched one at a time
+    nsample = 256
+    singles = []
+    for p in range(nsample):
+        a_, b_ = int(batch.offsets[p]), int(batch.offsets[p + 1])
+        singles.append((torch.tensor([0, b_ - a_], dtype=torch.int64, device=dev), d[a_:b_], z[a_:b_]))
+    for o_, dd_, zz_ in singles[:8]:
+        sdc.secular_batched(o_, dd_, zz_, 1.0, opts, check=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for o_, dd_, zz_ in singles:
+        sdc.secular_batched(o_, dd_, zz_, 1.0, opts, check=False)
+    e1.record()
+    e1.synchronize()
+    unb_roots = int(batch.offsets[nsample])
+    unbatched_rps = unb_roots / (e0.elapsed_time(e1) * 1e-3)
 
     # algorithmic work of the secular kernel (from the run's own sweep counts)
     mk = out["mk"].cpu().numpy().astype(np.float64)
@@ -304,6 +350,11 @@ def main():
                          "algorithmic": "%.0f flops/interaction x %.4g interactions per launch" % (
                              SECULAR_FLOPS_PER_INTERACTION, interactions)},
             "secular_sweeps_mean": float(sw[sw > 0].mean()) if np.any(sw > 0) else 0.0,
+            "schedule": {"autotuned": "sched=%d tile_roots=%d" % (opts.sched, opts.tile_roots),
+                         "candidates_ms": tune_ms},
+            "graph_replay_ms_per_step": graph_ms,
+            "unbatched": {"value": unbatched_rps, "unit": "roots/s",
+                          "sample": "first %d problems, one launch sequence each" % nsample},
             "e2e": {"value": roots_all / e2e_max, "unit": "roots/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "clocks": clocks,

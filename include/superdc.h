@@ -49,13 +49,16 @@ typedef struct {
     double  tau;          /* deflation tolerance of Remark 4.1 (absolute; strict '<' tests) */
     double  stop_c;       /* constant c of the stopping test eq. (4.12): |f| < c m (1+|psi|+|phi|) eps */
     int32_t max_iter;     /* iteration cap of the secular solver (the paper is silent; default 50) */
-    int32_t tile_roots;   /* roots per CTA of the direct evaluator (32..512, multiple of 32) */
-    int32_t batching;     /* 1: whole tree level per launch (default); 0: one launch per node */
-    int32_t reserved;
+    int32_t tile_roots;   /* secular schedule: roots per work unit in the pole-split mode (32..1024,
+                             multiple of 32); other values: chosen from the batch size */
+    int32_t batching;     /* superdc_eig: 1 = a whole tree level per launch (default); 0 = one
+                             launch sequence per node (the unbatched baseline) */
+    int32_t sched;        /* secular schedule: 0 automatic, 1 whole problems per CTA with per-warp
+                             root pools, 2 CTA warps split the poles of one 32-root group */
 } superdc_opts;
 
 /* Fills *opts with the defaults: tau = 1e-10, stop_c = 8, max_iter = 50,
- * tile_roots = 128, batching = 1. */
+ * tile_roots = 0 (automatic), batching = 1, sched = 0. */
 superdc_status superdc_opts_default(superdc_opts *opts);
 
 /* Human-readable name of a status code (static string). */

@@ -25,7 +25,7 @@ class SuperDCError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("tau", c_double), ("stop_c", c_double), ("max_iter", c_int32),
-                ("tile_roots", c_int32), ("batching", c_int32), ("reserved", c_int32)]
+                ("tile_roots", c_int32), ("batching", c_int32), ("sched", c_int32)]
 
 
 class Tree(ctypes.Structure):

@@ -1,0 +1,67 @@
+"""Autotuner for the secular-root schedule of the batched rank-one step.
+
+Candidates: whole problems per CTA with per-warp root pools (sched=1), and the
+pole-split schedule (sched=2) with 32..256 roots per work unit.  Each is timed
+with CUDA events on the caller's batch (device tensors, the same call the
+user makes); the fastest is cached per (device, problem-count bucket,
+root-count bucket) in a JSON file so later calls skip the search.
+"""
+import json
+import os
+
+import torch
+
+from . import _lib as L
+
+CACHE = os.path.join(os.path.expanduser("~"), ".cache", "superdc_gb300", "tune.json")
+CANDIDATES = [(1, 0)] + [(2, t) for t in (32, 64, 128, 256)]
+
+
+def _key(nprob, total):
+    b = lambda x: 1 << max(0, int(x).bit_length() - 1)
+    return "%s|p%d|t%d" % (torch.cuda.get_device_name(), b(nprob), b(total))
+
+
+def _load():
+    try:
+        return json.load(open(CACHE))
+    except Exception:
+        return {}
+
+
+def _save(tab):
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        json.dump(tab, open(CACHE, "w"), indent=1)
+    except OSError:
+        pass
+
+
+def tune_secular(offsets, d, z, rho=1.0, tau=1e-12, reps=2, use_cache=True):
+    """Return (opts, table of measured ms per candidate) for this batch."""
+    from . import secular_batched, alloc_rank1_out, default_opts
+    nprob, total = offsets.numel() - 1, d.numel()
+    key = _key(nprob, total)
+    tab = _load() if use_cache else {}
+    if use_cache and key in tab:
+        s, t = tab[key]["best"]
+        return default_opts(tau=tau, sched=s, tile_roots=t), tab[key]["ms"]
+    out = alloc_rank1_out(nprob, total, d.device)
+    ms = {}
+    for s, t in CANDIDATES:
+        o = default_opts(tau=tau, sched=s, tile_roots=t)
+        secular_batched(offsets, d, z, rho, o, out=out, check=False)      # warm-up
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            secular_batched(offsets, d, z, rho, o, out=out, check=False)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        ms["%d/%d" % (s, t)] = best
+    s, t = min(CANDIDATES, key=lambda c: ms["%d/%d" % c])
+    tab[key] = {"best": [s, t], "ms": ms}
+    if use_cache:
+        _save(tab)
+    return default_opts(tau=tau, sched=s, tile_roots=t), ms

@@ -24,9 +24,9 @@ superdc_status superdc_opts_default(superdc_opts *opts)
     opts->tau = 1e-10;
     opts->stop_c = 8.0;
     opts->max_iter = 50;
-    opts->tile_roots = 128;
+    opts->tile_roots = 0;
     opts->batching = 1;
-    opts->reserved = 0;
+    opts->sched = 0;
     return SUPERDC_OK;
 }
 
@@ -46,7 +46,8 @@ const char *superdc_status_string(superdc_status s)
 
 static bool opts_ok(const superdc_opts *op)
 {
-    return op && op->tau >= 0.0 && op->stop_c > 0.0 && op->max_iter >= 1 && op->max_iter <= 10000;
+    return op && op->tau >= 0.0 && op->stop_c > 0.0 && op->max_iter >= 1 && op->max_iter <= 10000 &&
+           op->sched >= 0 && op->sched <= 2;
 }
 
 superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, int64_t total,
@@ -74,6 +75,7 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
     a.stop_c = opts->stop_c;
     a.max_iter = opts->max_iter;
     a.tile_roots = opts->tile_roots;
+    a.sched = opts->sched;
     a.o.lam = out->lam; a.o.dk = out->dk; a.o.zk = out->zk; a.o.eta = out->eta;
     a.o.vhat = out->vhat; a.o.bnorm = out->bnorm; a.o.org = out->org; a.o.src = out->src;
     a.o.perm = out->perm; a.o.giv_ab = out->giv_ab; a.o.giv_cs = out->giv_cs; a.o.mk = out->mk;

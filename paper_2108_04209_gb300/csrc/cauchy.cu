@@ -199,6 +199,7 @@ __global__ void k_defl_copy(FactorView f, int64_t total, const double *__restric
          x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t slotg = x % total;
         const int col = (int)(x / total);
+        if (slotg < f.off[0] || slotg >= f.off[f.nprob]) continue;
         const int64_t p = sdc_upper_index(f.off, f.nprob, slotg);
         const int64_t b0 = f.off[p];
         const int s = (int)(slotg - b0);

@@ -635,7 +635,9 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
 {
     superdc_opts def;
     if (!opts) { superdc_opts_default(&def); opts = &def; }
-    if (!h || !lambda || !fact || !(opts->tau >= 0) || !(opts->stop_c > 0) || opts->max_iter < 1) return SUPERDC_ERR_ARG;
+    if (!h || !lambda || !fact || !(opts->tau >= 0) || !(opts->stop_c > 0) || opts->max_iter < 1 ||
+        opts->sched < 0 || opts->sched > 2)
+        return SUPERDC_ERR_ARG;
     const int64_t n = h->n;
     const int r = h->r, lmax = h->lmax, rr = r * r, nn = h->nnodes;
     superdc_eigfact *f = new superdc_eigfact();
@@ -722,24 +724,33 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
         std::swap(dcur, dnxt);
         for (int j = 0; j < r; j++) {
             StepF &S = f->F[l][j];
-            R1Args a;
-            a.nprob = nl; a.total = n; a.off = h->d_lev_off[l];
-            a.d = dcur; a.z = WK + (int64_t)j * n;
-            a.sqrt_rho = 1.0; a.tau = opts->tau; a.stop_c = opts->stop_c; a.max_iter = opts->max_iter;
-            a.tile_roots = opts->tile_roots;
-            a.o.lam = dnxt; a.o.dk = S.dk; a.o.zk = zk; a.o.eta = S.eta; a.o.vhat = S.vhat; a.o.bnorm = S.bnorm;
-            a.o.org = org; a.o.src = S.src; a.o.perm = perm; a.o.giv_ab = S.giv_ab; a.o.giv_cs = S.giv_cs;
-            a.o.mk = S.mk; a.o.ngiv = S.ngiv; a.o.sweeps = S.sweeps; a.o.status = f->status;
-            a.o.dorg = S.dorg; a.o.pinv = S.pinv; a.o.wsum = wsum;
-            superdc_status s1 = r1_run(a, st);
-            if (s1 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s1; }
-            const int c = ctot - (j + 1);
-            if (c > 0) {
-                superdc_status s2 = cauchy_apply_T(view(f, l, j), n, WK + (int64_t)(j + 1) * n, n,
-                                                   WK2 + (int64_t)(j + 1) * n, n, c, st);
-                if (s2 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s2; }
-                std::swap(WK, WK2);
+            // level-batched (default): every node of the level is one problem of
+            // one launch sequence; unbatched baseline: one sequence per node
+            const int nseg = opts->batching ? 1 : nl;
+            for (int q = 0; q < nseg; q++) {
+                const int np = opts->batching ? nl : 1;
+                R1Args a;
+                a.nprob = np; a.total = n; a.off = h->d_lev_off[l] + q;
+                a.rows = opts->batching ? n : h->size[h->lev_nodes[l][q]];
+                a.d = dcur; a.z = WK + (int64_t)j * n;
+                a.sqrt_rho = 1.0; a.tau = opts->tau; a.stop_c = opts->stop_c; a.max_iter = opts->max_iter;
+                a.tile_roots = opts->tile_roots; a.sched = opts->sched;
+                a.o.lam = dnxt; a.o.dk = S.dk; a.o.zk = zk; a.o.eta = S.eta; a.o.vhat = S.vhat;
+                a.o.bnorm = S.bnorm; a.o.org = org; a.o.src = S.src; a.o.perm = perm; a.o.giv_ab = S.giv_ab;
+                a.o.giv_cs = S.giv_cs; a.o.mk = S.mk + q; a.o.ngiv = S.ngiv + q; a.o.sweeps = S.sweeps;
+                a.o.status = f->status; a.o.dorg = S.dorg; a.o.pinv = S.pinv; a.o.wsum = wsum + q;
+                superdc_status s1 = r1_run(a, st);
+                if (s1 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s1; }
+                const int c = ctot - (j + 1);
+                if (c > 0) {
+                    FactorView v = view(f, l, j);
+                    if (!opts->batching) { v.nprob = 1; v.off += q; v.mk += q; v.ngiv += q; }
+                    superdc_status s2 = cauchy_apply_T(v, n, WK + (int64_t)(j + 1) * n, n,
+                                                       WK2 + (int64_t)(j + 1) * n, n, c, st);
+                    if (s2 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s2; }
+                }
             }
+            if (ctot - (j + 1) > 0) std::swap(WK, WK2);
             std::swap(dcur, dnxt);
         }
         if (!root) EIG_CHECK(cudaMemcpyAsync(Wp, WK + (int64_t)r * n, (size_t)n * r * sizeof(double),

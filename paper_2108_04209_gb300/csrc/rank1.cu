@@ -829,6 +829,7 @@ __global__ void k_merge(int64_t nprob, const int64_t *__restrict__ off, int64_t 
 {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
          x += (int64_t)gridDim.x * blockDim.x) {
+        if (x < off[0] || x >= off[nprob]) continue;
         const int64_t p = sdc_upper_index(off, nprob, x);
         const int64_t b0 = off[p];
         const int m = (int)(off[p + 1] - b0);
@@ -906,10 +907,11 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     // per slot (the top levels of a tree), units shrink so every SM gets work
     // and the warps of a CTA split the poles instead of the roots.
     const int slots = nsm * 6;
-    const int64_t per = a.total / slots;
-    const bool split = per < 512;
+    const int64_t per = (a.rows >= 0 ? a.rows : a.total) / slots;
+    const bool split = (a.sched == 2) || (a.sched == 0 && per < 512);
     int ubig = SEC_UNIT_BIG;
     if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
+    if (split && a.tile_roots >= 32 && a.tile_roots <= 1024) ubig = (a.tile_roots / 32) * 32;
     PROF_LAUNCH("units", st, k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, ubig, split ? 0 : 1, units, ucount,
                                                            ucount + 1));
     if (split)

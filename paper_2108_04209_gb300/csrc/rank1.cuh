@@ -15,11 +15,13 @@ struct R1Out {
 };
 
 struct R1Args {
-    int64_t nprob, total;
+    int64_t nprob, total;   // problems; extent of the row-indexed arrays (rows are absolute)
+    int64_t rows = -1;      // rows covered by the problems (scheduling), -1 = total
     const int64_t *off;     // device, nprob+1
     const double *d, *z;    // device inputs
     double sqrt_rho, tau, stop_c;
     int max_iter, tile_roots;
+    int sched = 0;          // 0 automatic, 1 whole problems per CTA (root pools per warp), 2 pole split
     R1Out o;
 };
 

@@ -15,7 +15,7 @@ def test_library_exports_all_declared_symbols():
 
 def test_opts_default_and_status_strings():
     o = L.default_opts()
-    assert o.tau == 1e-10 and o.stop_c == 8.0 and o.max_iter == 50 and o.tile_roots == 128
+    assert o.tau == 1e-10 and o.stop_c == 8.0 and o.max_iter == 50 and o.tile_roots == 0 and o.sched == 0
     for code in range(7):
         s = L.lib().superdc_status_string(code).decode()
         assert s.startswith("SUPERDC_")

@@ -137,3 +137,15 @@ def test_full_size_131072_invariants_and_probes():
     orth = F.apply_Q(torch.from_numpy(QX).cuda(), trans=True).cpu().numpy() - Xn
     assert res < 1e-12 * np.sqrt(n)
     assert np.linalg.norm(orth) / np.linalg.norm(Xn) < 1e-12 * np.sqrt(n)
+
+
+def test_unbatched_per_node_path_matches_level_batched():
+    """opts.batching = 0 launches every node on its own; the arithmetic is the
+    same, so the eigenvalues agree with the level-batched path bit for bit."""
+    h = inputs.hss_random(2048, 64, 5, seed=31, clustered=True)
+    H = sdc.HSSMatrix(h)
+    lam1, F1 = H.eig(sdc.default_opts(tau=1e-10))
+    lam0, F0 = H.eig(sdc.default_opts(tau=1e-10, batching=0))
+    assert torch.equal(lam0, lam1)
+    X = torch.from_numpy(inputs.normal_block(2048, 3, seed=1)).cuda()
+    assert torch.equal(F0.apply_Q(X), F1.apply_Q(X))
