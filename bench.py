@@ -39,6 +39,20 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 (no measured figure in the p
 SECULAR_FLOPS_PER_INTERACTION = 7.0   # 2 sub, 1 recip, 1 mul, 1 add, 1 fma (2)
 
 
+def _profiled(name, src):
+    """Numbers of a committed ncu summary, if it was taken on the current kernel source."""
+    import hashlib
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
+        sha = hashlib.sha1(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+        if ("sha1: %s" % sha) not in txt:
+            return None
+        return {k: float(v) for k, v in re.findall(r"^(\w+): ([0-9.]+)$", txt, re.M)}
+    except OSError:
+        return None
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -306,6 +320,7 @@ def main():
     sec_ms = kern["secular"][1] / max(1, kern["secular"][0])
     achieved = SECULAR_FLOPS_PER_INTERACTION * interactions / (sec_ms * 1e-3) / 1e12
     peak, peak_src = _fp64_peak()
+    prof = _profiled("k_secular_batched4096_dram.md", "paper_2108_04209_gb300/csrc/rank1.cu")
 
     # e2e: host buffers, copies inside the timed region
     h_off = torch.from_numpy(batch.offsets).pin_memory()
@@ -345,7 +360,9 @@ def main():
             "gpu_launches": int(launches),
             "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kern.items()},
             "roofline": {"bound": "alu", "kernel": "k_secular", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "dtype": "fp64", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "dtype": "fp64", "frac": achieved / peak,
+                         "traffic": (prof or {}).get("traffic_bytes"),
+                         "fp64_pipe_pct_ncu": (prof or {}).get("fp64_pipe_pct"),
                          "peak_source": peak_src,
                          "algorithmic": "%.0f flops/interaction x %.4g interactions per launch" % (
                              SECULAR_FLOPS_PER_INTERACTION, interactions)},

@@ -49,8 +49,8 @@ typedef struct {
     double  tau;          /* deflation tolerance of Remark 4.1 (absolute; strict '<' tests) */
     double  stop_c;       /* constant c of the stopping test eq. (4.12): |f| < c m (1+|psi|+|phi|) eps */
     int32_t max_iter;     /* iteration cap of the secular solver (the paper is silent; default 50) */
-    int32_t tile_roots;   /* secular schedule: roots per work unit in the pole-split mode (32..1024,
-                             multiple of 32); other values: chosen from the batch size */
+    int32_t tile_roots;   /* secular schedule: roots per work unit (32..4096, multiple of 32);
+                             other values: chosen from the batch size */
     int32_t batching;     /* superdc_eig: 1 = a whole tree level per launch (default); 0 = one
                              launch sequence per node (the unbatched baseline) */
     int32_t sched;        /* secular schedule: 0 automatic, 1 whole problems per CTA with per-warp
@@ -134,7 +134,7 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
  * pre-reserved memory budget).  The paper has no counterpart; this is an
  * interface variant only.  Same arguments, layout and results as
  * superdc_secular_batched, but the call makes no device allocation: its
- * scratch is a static device array of about 9 MB that every GPU which loads
+ * scratch is a static device array of about 11 MB that every GPU which loads
  * the library holds until the process exits.
  *   - limits: nprob <= SDC_NOALLOC_MAX_PROB and total <= SDC_NOALLOC_MAX_TOTAL,
  *     else SUPERDC_ERR_ARG (nothing enqueued);

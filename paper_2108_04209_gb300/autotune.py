@@ -1,7 +1,7 @@
 """Autotuner for the secular-root schedule of the batched rank-one step.
 
-Candidates: whole problems per CTA with per-warp root pools (sched=1), and the
-pole-split schedule (sched=2) with 32..256 roots per work unit.  Each is timed
+Candidates: per-warp root pools (sched=1) with 256..2048 roots per work unit,
+and the pole-split schedule (sched=2) with 64..256 roots per work unit.  Each is timed
 with CUDA events on the caller's batch (device tensors, the same call the
 user makes); the fastest is cached per (device, problem-count bucket,
 root-count bucket) in a JSON file so later calls skip the search.
@@ -14,7 +14,7 @@ import torch
 from . import _lib as L
 
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "superdc_gb300", "tune.json")
-CANDIDATES = [(1, 0)] + [(2, t) for t in (32, 64, 128, 256)]
+CANDIDATES = [(1, t) for t in (2048, 1024, 512, 256)] + [(2, t) for t in (64, 128, 256)]
 
 
 def _key(nprob, total):

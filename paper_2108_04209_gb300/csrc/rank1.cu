@@ -424,6 +424,17 @@ struct Acc { double psi, phi, dpsi, dphi; };
 // first pole has global index jg0.  Pole j goes to psi if j <= k, else to phi.
 // The warp's roots are consecutive (kwlo..kwhi), so the loop runs in three
 // warp-uniform regions; only the middle one selects per lane.
+__device__ __forceinline__ int fexp(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
+
+// Every term uses the shifted difference (d_j - d_K) - y of eq. (4.14).  (The
+// local-shifting variant that takes d_j - x for far poles, eqs. (4.19)-(4.21),
+// saves one FP64 subtraction per term but measured slower on GB300: the
+// integer exponent test and branch cost more than the subtraction.)
+__device__ __forceinline__ double shifted_t(double dj, double dK, double y)
+{
+    return (dj - dK) - y;
+}
+
 template <bool DERIV>
 __device__ __forceinline__ void sweep(const double *__restrict__ sd, const double *__restrict__ sw,
                                       int j0, int j1, int jg0, int k, int kwlo, int kwhi,
@@ -433,7 +444,7 @@ __device__ __forceinline__ void sweep(const double *__restrict__ sd, const doubl
     int ea = min(j1, max(j0, kwlo - jg0 + 1));
 #pragma unroll 4
     for (int j = j0; j < ea; j++) {
-        double t = (sd[j] - dK) - y;
+        double t = shifted_t(sd[j], dK, y);
         double r = rcp_nr1(t);
         if (DERIV) {
             double a = sw[j] * r;
@@ -446,7 +457,7 @@ __device__ __forceinline__ void sweep(const double *__restrict__ sd, const doubl
     // region B: kwlo < j <= kwhi -> per lane
     int eb = min(j1, max(ea, kwhi - jg0 + 1));
     for (int j = ea; j < eb; j++) {
-        double t = (sd[j] - dK) - y;
+        double t = shifted_t(sd[j], dK, y);
         double r = rcp_nr1(t);
         double a = sw[j] * r;
         if (jg0 + j <= k) { A.psi += a; if (DERIV) A.dpsi = fma(a, r, A.dpsi); }
@@ -455,7 +466,7 @@ __device__ __forceinline__ void sweep(const double *__restrict__ sd, const doubl
     // region C: j > kwhi -> phi for every lane
 #pragma unroll 4
     for (int j = eb; j < j1; j++) {
-        double t = (sd[j] - dK) - y;
+        double t = shifted_t(sd[j], dK, y);
         double r = rcp_nr1(t);
         if (DERIV) {
             double a = sw[j] * r;
@@ -548,12 +559,12 @@ struct Root {
     }
 };
 
-// Work units of the secular kernel: (problem, first root, end root).
-// Problems with at most SEC_CHUNK kept poles form one unit (their poles are
-// staged in shared memory once); larger ones are cut into units of
-// SEC_UNIT_BIG roots whose sweeps stream the poles in chunks.  Units are
+// Work units of the secular kernel: (problem, first root, end root), at most
+// ubig roots each.  A unit stages its problem's poles in shared memory (all of
+// them when they fit in SEC_CHUNK, else in chunks per sweep).  Units are
 // ordered by decreasing problem size (largest first) so the long units start
-// early and the tail of the launch is short.
+// early, and capping the roots per unit spreads a large problem over several
+// SMs, which keeps the tail of the launch short.
 constexpr int SEC_UNIT_BIG = 2048;
 constexpr int SORT_MAX = 8192;
 
@@ -595,7 +606,7 @@ __global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int ubig,
     for (int64_t q = beg; q < end; q++) {
         int64_t pp = sorted ? (int64_t)(0xFFFFFFFFu - (unsigned)(keys[q] & 0xFFFFFFFFull)) : q;
         int m = mk[pp];
-        cnt += (whole_small && m <= SEC_CHUNK) ? (m > 0) : (m + ubig - 1) / ubig;
+        cnt += (m + ubig - 1) / ubig;
     }
     part[threadIdx.x] = cnt;
     __syncthreads();
@@ -611,11 +622,7 @@ __global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int ubig,
         int64_t pp = sorted ? (int64_t)(0xFFFFFFFFu - (unsigned)(keys[q] & 0xFFFFFFFFull)) : q;
         int m = mk[pp];
         if (m <= 0) continue;
-        if (whole_small && m <= SEC_CHUNK) {
-            units[u++] = make_int4((int)pp, 0, m, 0);
-        } else {
-            for (int r = 0; r < m; r += ubig) units[u++] = make_int4((int)pp, r, min(m, r + ubig), 0);
-        }
+        for (int r = 0; r < m; r += ubig) units[u++] = make_int4((int)pp, r, min(m, r + ubig), 0);
     }
 }
 
@@ -726,6 +733,7 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
                     o.org[b0 + k] = R.K;
                     o.eta[b0 + k] = R.y;
                     o.dorg[b0 + k] = R.dK;
+                    o.lamk[b0 + k] = R.dK + R.y;
                     if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
                 }
             }
@@ -840,7 +848,7 @@ __global__ void k_merge(int64_t nprob, const int64_t *__restrict__ off, int64_t 
         int pos;
         double val;
         if (s < mk) {
-            val = dorg[s] + eta[s];                      // eq. (4.21)
+            val = o.lamk[b0 + s];                        // eq. (4.21), d_K + eta
             // deflated slots with a smaller key
             int lo = mk, hi = m;
             while (lo < hi) {
@@ -853,7 +861,7 @@ __global__ void k_merge(int64_t nprob, const int64_t *__restrict__ off, int64_t 
             int lo = 0, hi = mk;
             while (lo < hi) {
                 int mid = (lo + hi) >> 1;
-                double lm = dorg[mid] + eta[mid];
+                double lm = o.lamk[b0 + mid];
                 if (key_less(lm, src[mid], val, src[s])) lo = mid + 1; else hi = mid;
             }
             pos = (s - mk) + lo;
@@ -869,8 +877,9 @@ __global__ void k_merge(int64_t nprob, const int64_t *__restrict__ off, int64_t 
 // ---------------------------------------------------------------------------
 // Host launcher
 // ---------------------------------------------------------------------------
-superdc_status r1_run(const R1Args &a, cudaStream_t st)
+superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
 {
+    R1Args a = a_in;
     const int nsm = sdc_num_sms();
     double *wd = nullptr, *wz = nullptr;
     int8_t *kept = nullptr;
@@ -881,6 +890,7 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     SDC_CHECK(sdc_alloc(&tile_off, a.nprob + 1, st));
     int32_t *surv = nullptr;
     SDC_CHECK(sdc_alloc(&surv, a.total, st));
+    SDC_CHECK(sdc_alloc(&a.o.lamk, a.total, st));
     int4 *units = nullptr;
     int *ucount = nullptr;
     SDC_CHECK(sdc_alloc(&units, a.nprob + a.total / 32 + 2, st));
@@ -909,9 +919,9 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     const int slots = nsm * 6;
     const int64_t per = (a.rows >= 0 ? a.rows : a.total) / slots;
     const bool split = (a.sched == 2) || (a.sched == 0 && per < 512);
-    int ubig = SEC_UNIT_BIG;
+    int ubig = SEC_UNIT_BIG / 2;
     if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
-    if (split && a.tile_roots >= 32 && a.tile_roots <= 1024) ubig = (a.tile_roots / 32) * 32;
+    if (a.tile_roots >= 32 && a.tile_roots <= 4096) ubig = (a.tile_roots / 32) * 32;
     PROF_LAUNCH("units", st, k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, ubig, split ? 0 : 1, units, ucount,
                                                            ucount + 1));
     if (split)
@@ -931,6 +941,7 @@ superdc_status r1_run(const R1Args &a, cudaStream_t st)
     SDC_CHECK(cudaFreeAsync(tile_off, st));
     SDC_CHECK(cudaFreeAsync(units, st));
     SDC_CHECK(cudaFreeAsync(surv, st));
+    SDC_CHECK(cudaFreeAsync(a.o.lamk, st));
     SDC_CHECK(cudaFreeAsync(ucount, st));
     return SUPERDC_OK;
 }
@@ -969,7 +980,8 @@ constexpr size_t NA_SURV = NA_UNITS + na_round((NA_P + NA_T / 32 + 2) * sizeof(i
 constexpr size_t NA_PINV = NA_SURV + na_round(NA_T * sizeof(int32_t));
 constexpr size_t NA_KEPT = NA_PINV + na_round(NA_T * sizeof(int32_t));
 constexpr size_t NA_UCNT = NA_KEPT + na_round(NA_T * sizeof(int8_t));
-constexpr size_t NA_BYTES = NA_UCNT + na_round(2 * sizeof(int));
+constexpr size_t NA_LAMK = NA_UCNT + na_round(2 * sizeof(int));
+constexpr size_t NA_BYTES = NA_LAMK + na_round(NA_T * sizeof(double));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
@@ -1027,6 +1039,7 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     a.o.dorg = (double *)(base + NA_DORG);
     a.o.wsum = (double *)(base + NA_WSUM);
     a.o.pinv = (int32_t *)(base + NA_PINV);
+    a.o.lamk = (double *)(base + NA_LAMK);
     double *wd = (double *)(base + NA_WD), *wz = (double *)(base + NA_WZ);
     int8_t *kept = (int8_t *)(base + NA_KEPT);
     int64_t *tile_off = (int64_t *)(base + NA_TILE);
@@ -1049,7 +1062,7 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     const int slots = nsm * 6;
     const int64_t per = a.total / slots;
     const bool split = per < 512;
-    int ubig = SEC_UNIT_BIG;
+    int ubig = SEC_UNIT_BIG / 2;
     if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
     k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, ubig, split ? 0 : 1, units, ucount, ucount + 1);
     if (split)

@@ -12,6 +12,7 @@ struct R1Out {
     double *dorg;   // d_{K} of every kept root (scratch or stored), total entries
     int32_t *pinv;  // merged position of every slot (inverse of perm), total entries
     double *wsum;   // sum of kept z^2 per problem (scratch), nprob entries
+    double *lamk;   // d_K + eta of every kept root, slot order (scratch), total entries
 };
 
 struct R1Args {
