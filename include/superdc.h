@@ -126,6 +126,36 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
                                        const superdc_opts *opts, superdc_rank1_out *out,
                                        cudaStream_t stream);
 
+/* Y = Qhat^T X (trans = 1) or Y = Qhat X (trans = 0) for every problem of a
+ * superdc_secular_batched result `fwd` (the structured eigenvector matrices of
+ * eq. (4.26) with the rotations and the sort), applied to caller columns:
+ * X, Y total x ncols column-major (ld ldx, ldy >= total), problem p owning rows
+ * [offsets[p], offsets[p+1]).  X is read only; X and Y must not overlap. */
+superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offsets, int64_t total,
+                                   const superdc_rank1_out *fwd, int32_t trans, int64_t ncols,
+                                   const double *X, int64_t ldx, double *Y, int64_t ldy,
+                                   cudaStream_t stream);
+
+/* Adjoint of superdc_secular_batched (reverse mode through the secular roots
+ * by the implicit-function theorem; the row-12 building block).
+ * fwd: the forward outputs of the same call (unchanged since); rho, offsets,
+ * total as in the forward.  Cotangents (DEVICE, may be NULL / ncols = 0):
+ *   lam_bar[total] of the new eigenvalues (merged order, as fwd->lam);
+ *   Ybar (total x ncols, column-major, ld ldy) of Y = Qhat^T X for the caller
+ *   columns X (total x ncols, ld ldx, input order).
+ * Outputs: d_bar[total], z_bar[total] (input order), X_bar = Qhat Ybar
+ * (total x ncols, ld ldxb; written only when ncols > 0).
+ * Kept block: eigen-adjoint of diag(d_k) + z_k z_k^T through the Cauchy-like
+ * factor (eq. (4.26)) with zhat recomputed from the stored factor vectors and
+ * every difference in shifted form (eq. (4.28)); deflation rotations are
+ * treated as fixed linear maps (their dependence on z is of order tau). */
+superdc_status superdc_secular_batched_backward(int64_t nprob, const int64_t *offsets, int64_t total,
+                                                double rho, const superdc_rank1_out *fwd,
+                                                const double *lam_bar, int64_t ncols, const double *X,
+                                                int64_t ldx, const double *Ybar, int64_t ldy,
+                                                double *d_bar, double *z_bar, double *X_bar, int64_t ldxb,
+                                                cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * superdc_secular_batched_noalloc: the batched rank-one step of
  * superdc_secular_batched for callers that cannot allocate device memory

@@ -182,3 +182,75 @@ class EigFactor:
                 self._f = ctypes.c_void_p()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the batched rank-one step and its autograd wrapper
+# ---------------------------------------------------------------------------
+def secular_batched_backward(offsets, out, rho, lam_bar=None, X=None, Ybar=None):
+    """Reverse mode of ``secular_batched`` (superdc_secular_batched_backward).
+
+    ``out`` is the dict returned by the forward call.  Returns (d_bar, z_bar,
+    X_bar); X_bar is None when no columns are given."""
+    total = out["lam"].numel() if offsets.numel() > 1 else 0
+    total = int(offsets[-1].item()) if total else 0
+    nprob = offsets.numel() - 1
+    dev = out["lam"].device
+    d_bar = torch.empty(max(total, 1), dtype=torch.float64, device=dev)
+    z_bar = torch.empty(max(total, 1), dtype=torch.float64, device=dev)
+    ncols = 0
+    Xf = Yf = Xb = None
+    if X is not None:
+        ncols = X.shape[1]
+        Xf = X.t().contiguous().t()
+        Yf = Ybar.t().contiguous().t()
+        Xb = torch.empty((ncols, total), dtype=torch.float64, device=dev).t()
+    ro = L.Rank1Out(**{k: (_ptr(v).value or None) for k, v in out.items()})
+    code = L.lib().superdc_secular_batched_backward(
+        nprob, _ptr(offsets), total, float(rho), ctypes.byref(ro), _ptr(lam_bar), ncols,
+        _ptr(Xf), total, _ptr(Yf), total, _ptr(d_bar), _ptr(z_bar), _ptr(Xb), total, _stream())
+    L.check(code, "superdc_secular_batched_backward")
+    return d_bar[:total], z_bar[:total], Xb
+
+
+class SecularEig(torch.autograd.Function):
+    """(d, z, X) -> (lambda, Y = Qhat^T X) for a batch of rank-one problems,
+    differentiable in d, z and X.  offsets (int64, device) and rho are
+    constants.  The backward runs superdc_secular_batched_backward."""
+
+    @staticmethod
+    def forward(ctx, offsets, d, z, X, rho=1.0, tau=1e-12):
+        out = secular_batched(offsets, d.detach(), z.detach(), rho, default_opts(tau=tau))
+        Y = None
+        if X is not None and X.numel():
+            Y = _apply_rank1_T(offsets, out, X.detach())
+        ctx.save_for_backward(offsets, X if X is not None else torch.empty(0, device=d.device))
+        ctx.out, ctx.rho = out, rho
+        lam = out["lam"][:d.numel()].clone()
+        return (lam, Y) if Y is not None else (lam, torch.empty(0, device=d.device, dtype=torch.float64))
+
+    @staticmethod
+    def backward(ctx, lam_bar, Y_bar):
+        offsets, X = ctx.saved_tensors
+        has_x = X.numel() > 0
+        d_bar, z_bar, X_bar = secular_batched_backward(
+            offsets, ctx.out, ctx.rho, lam_bar.contiguous(),
+            X if has_x else None, Y_bar if has_x else None)
+        return None, d_bar, z_bar, (X_bar if has_x else None), None, None
+
+
+def _apply_rank1_T(offsets, out, X):
+    return apply_rank1(offsets, out, X, trans=True)
+
+
+def apply_rank1(offsets, out, X, trans=True):
+    """Qhat^T X (trans) or Qhat X for the factors of a secular_batched result."""
+    total = int(offsets[-1].item())
+    ncols = X.shape[1]
+    Xf = X.t().contiguous().t()
+    Y = torch.empty((ncols, total), dtype=torch.float64, device=X.device).t()
+    ro = L.Rank1Out(**{k: (_ptr(v).value or None) for k, v in out.items()})
+    code = L.lib().superdc_rank1_apply(offsets.numel() - 1, _ptr(offsets), total, ctypes.byref(ro),
+                                       1 if trans else 0, ncols, _ptr(Xf), total, _ptr(Y), total, _stream())
+    L.check(code, "superdc_rank1_apply")
+    return Y

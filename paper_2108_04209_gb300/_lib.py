@@ -77,6 +77,14 @@ def lib():
         L.superdc_eigfact_shape.argtypes = [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
                                             ctypes.POINTER(c_int64)]
         L.superdc_eigfact_shape.restype = c_int32
+        L.superdc_secular_batched_backward.argtypes = [c_int64, c_void_p, c_int64, c_double,
+                                                       ctypes.POINTER(Rank1Out), c_void_p, c_int64, c_void_p,
+                                                       c_int64, c_void_p, c_int64, c_void_p, c_void_p,
+                                                       c_void_p, c_int64, c_void_p]
+        L.superdc_secular_batched_backward.restype = c_int32
+        L.superdc_rank1_apply.argtypes = [c_int64, c_void_p, c_int64, ctypes.POINTER(Rank1Out), c_int32, c_int64,
+                                          c_void_p, c_int64, c_void_p, c_int64, c_void_p]
+        L.superdc_rank1_apply.restype = c_int32
         L.superdc_profile_enable.argtypes = [c_int32]
         L.superdc_profile_enable.restype = c_int32
         L.superdc_profile_reset.argtypes = []
