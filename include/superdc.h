@@ -55,10 +55,13 @@ typedef struct {
                              launch sequence per node (the unbatched baseline) */
     int32_t sched;        /* secular schedule: 0 automatic, 1 whole problems per CTA with per-warp
                              root pools, 2 CTA warps split the poles of one 32-root group */
+    int32_t tape;         /* superdc_eig: 1 = keep the forward intermediates that
+                             superdc_eig_backward needs (O(r^2 n log n) doubles) */
+    int32_t pad;
 } superdc_opts;
 
 /* Fills *opts with the defaults: tau = 1e-10, stop_c = 8, max_iter = 50,
- * tile_roots = 0 (automatic), batching = 1, sched = 0. */
+ * tile_roots = 0 (automatic), batching = 1, sched = 0, tape = 0. */
 superdc_status superdc_opts_default(superdc_opts *opts);
 
 /* Human-readable name of a status code (static string). */
@@ -242,6 +245,25 @@ void superdc_eigfact_free(superdc_eigfact *f);
 superdc_status superdc_apply_Q(const superdc_eigfact *f, int32_t trans, int64_t ncols,
                                const double *X, int64_t ldx, double *Y, int64_t ldy,
                                cudaStream_t stream);
+
+/* Reverse mode of superdc_eig (Algorithms 1-3 differentiated; no counterpart
+ * in the paper): gradients of a loss L(lambda, Y = Q^T V) with respect to the
+ * generators and V, given the cotangents lambda_bar (n, may be NULL) and Ybar
+ * (n x k, ld ldy; k = 0 for eigenvalue-only losses).  The factor must come
+ * from superdc_eig with opts.tape = 1 on the same handle (else
+ * SUPERDC_ERR_STATE).  Each rank-one step is reversed through its secular
+ * roots (the adjoint of superdc_secular_batched_backward); the level build,
+ * the leaf eigendecompositions and the dividing stage (H, B~, beta = ||B~||_2)
+ * are reversed exactly.  Outputs (DEVICE, caller-allocated, packing of
+ * superdc_build_hss): gD (gradient for symmetric perturbations of the leaf
+ * blocks), gU, gR, gB (zero where a generator is not used), gV (n x k, ld
+ * ldgv).  Deflation rotations are treated as fixed (their dependence is of
+ * the order of tau); degenerate eigenvalues make eigenvector losses
+ * non-differentiable. */
+superdc_status superdc_eig_backward(const superdc_hss *h, const superdc_eigfact *f,
+                                    const double *lambda_bar, int64_t k, const double *V, int64_t ldv,
+                                    const double *Ybar, int64_t ldy, double *gD, double *gU, double *gR,
+                                    double *gB, double *gV, int64_t ldgv, cudaStream_t stream);
 
 /* Latched device status of a handle (synchronises the handle's last work):
  * SUPERDC_OK, SUPERDC_ERR_NONFINITE or SUPERDC_ERR_NOCONV. */

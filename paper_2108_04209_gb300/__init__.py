@@ -97,17 +97,22 @@ class HSSMatrix:
     ``h`` is an ``inputs.HSS`` (tree + generators); the generators are copied
     to the GPU and then into the library handle."""
 
-    def __init__(self, h, device=None):
+    def __init__(self, h, device=None, tensors=None):
         import numpy as np
         dev = torch.device(device or "cuda")
-        t = h.tree
+        t = h.tree if hasattr(h, "tree") else h
         self.n, self.rank = int(t.n), int(t.rank)
+        self.tree = t
         self._lch = np.ascontiguousarray(t.lchild, np.int32)
         self._rch = np.ascontiguousarray(t.rchild, np.int32)
         self._sz = np.ascontiguousarray(t.leaf_size, np.int64)
         tree = L.Tree(self.n, int(t.nnodes), self._lch.ctypes.data, self._rch.ctypes.data,
                       self._sz.ctypes.data, self.rank)
-        D, U, R, B = (torch.from_numpy(x).to(dev) for x in h.packed())
+        if tensors is not None:
+            D, U, R, B = (x.detach().contiguous() for x in tensors)
+        else:
+            D, U, R, B = (torch.from_numpy(x).to(dev) for x in h.packed())
+        self.sizes = (D.numel(), U.numel(), R.numel(), B.numel())
         self._h = ctypes.c_void_p()
         code = L.lib().superdc_build_hss(ctypes.byref(tree), _ptr(D), _ptr(U), _ptr(R), _ptr(B), _stream(),
                                          ctypes.byref(self._h))
@@ -254,3 +259,38 @@ def apply_rank1(offsets, out, X, trans=True):
                                        1 if trans else 0, ncols, _ptr(Xf), total, _ptr(Y), total, _stream())
     L.check(code, "superdc_rank1_apply")
     return Y
+
+
+class HSSEig(torch.autograd.Function):
+    """(D, U, R, B, V) -> (lambda, Y = Q^T V) for a symmetric HSS matrix given
+    by its packed generators (layout of superdc_build_hss; ``tree`` is an
+    ``inputs.Tree``).  Differentiable in D (symmetric perturbations), U, R, B
+    and V; the backward runs superdc_eig_backward on the forward's tape."""
+
+    @staticmethod
+    def forward(ctx, tree, D, U, R, B, V, opts=None):
+        H = HSSMatrix(tree, tensors=(D, U, R, B))
+        o = opts if opts is not None else default_opts()
+        o.tape = 1
+        lam, F = H.eig(o)
+        Vc = V.detach().reshape(H.n, -1)
+        Y = F.apply_Q(Vc, trans=True)
+        ctx.H, ctx.F = H, F
+        ctx.save_for_backward(Vc)
+        return lam, Y
+
+    @staticmethod
+    def backward(ctx, lam_bar, Y_bar):
+        (V,) = ctx.saved_tensors
+        H, F = ctx.H, ctx.F
+        n, k = V.shape
+        dev = V.device
+        gD, gU, gR, gB = (torch.empty(sz, dtype=torch.float64, device=dev) for sz in H.sizes)
+        gV = torch.empty((k, n), dtype=torch.float64, device=dev).t()
+        Vf = V.t().contiguous().t()
+        Yb = (Y_bar if Y_bar is not None else torch.zeros_like(V)).t().contiguous().t()
+        lb = lam_bar.contiguous() if lam_bar is not None else None
+        code = L.lib().superdc_eig_backward(H._h, F._f, _ptr(lb), k, _ptr(Vf), n, _ptr(Yb), n, _ptr(gD), _ptr(gU),
+                                            _ptr(gR), _ptr(gB), _ptr(gV), n, _stream())
+        L.check(code, "superdc_eig_backward")
+        return None, gD, gU, gR, gB, gV.reshape(V.shape), None

@@ -25,7 +25,8 @@ class SuperDCError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("tau", c_double), ("stop_c", c_double), ("max_iter", c_int32),
-                ("tile_roots", c_int32), ("batching", c_int32), ("sched", c_int32)]
+                ("tile_roots", c_int32), ("batching", c_int32), ("sched", c_int32), ("tape", c_int32),
+                ("pad", c_int32)]
 
 
 class Tree(ctypes.Structure):
@@ -85,6 +86,10 @@ def lib():
         L.superdc_rank1_apply.argtypes = [c_int64, c_void_p, c_int64, ctypes.POINTER(Rank1Out), c_int32, c_int64,
                                           c_void_p, c_int64, c_void_p, c_int64, c_void_p]
         L.superdc_rank1_apply.restype = c_int32
+        L.superdc_eig_backward.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p,
+                                           c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,
+                                           c_void_p]
+        L.superdc_eig_backward.restype = c_int32
         L.superdc_profile_enable.argtypes = [c_int32]
         L.superdc_profile_enable.restype = c_int32
         L.superdc_profile_reset.argtypes = []

@@ -27,6 +27,8 @@ superdc_status superdc_opts_default(superdc_opts *opts)
     opts->tile_roots = 0;
     opts->batching = 1;
     opts->sched = 0;
+    opts->tape = 0;
+    opts->pad = 0;
     return SUPERDC_OK;
 }
 

@@ -24,6 +24,9 @@
 // (eq. (4.28)) and lambda_k - lambda_l = (d_{K_k} - d_{K_l}) + (eta_k - eta_l).
 // Deflation: the rotations are treated as fixed linear maps (their dependence
 // on z is of the order of tau); deflated eigenvalues are the rotated poles.
+// Eigenvalue pairs with |lambda_k - lambda_l| <= 1e-10 max(|lambda_k|, |lambda_l|)
+// are treated as one eigenspace (no coupling term): eigenvector losses are not
+// differentiable there, and losses invariant within the eigenspace are exact.
 #include <algorithm>
 #include <cuda_runtime.h>
 #include "common.cuh"
@@ -92,6 +95,8 @@ k_bw_lamlam(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__res
                 for (int ll = 0; ll < cn; ll++) {
                     if (l0 + ll == k) continue;
                     const double dl = (dKk - sK[ll]) + (ek - sE[ll]);     // lambda_k - lambda_l
+                    // numerically degenerate pairs form one eigenspace: no coupling
+                    if (fabs(dl) <= 1e-10 * fmax(fabs(dKk + ek), fabs(sK[ll] + sE[ll]))) continue;
                     const double r = rcp_full(dl);
                     const double r2 = r * r;
 #pragma unroll
@@ -226,6 +231,53 @@ __global__ void k_tiles_b(int64_t nprob, const int32_t *__restrict__ mk, int tr,
 
 }  // namespace
 
+// Adjoint of one batched rank-one step given its factor view (pinv and d_K
+// available).  X: the columns the step transformed (input order, read only),
+// Ybar: cotangent of Qhat^T X (merged order); lam_bar may be NULL.
+superdc_status r1_backward_fv(const FactorView &f, int64_t total, const double *lam_bar, int ncols,
+                              const double *X, int64_t ldx, const double *Ybar, int64_t ldy, double *d_bar,
+                              double *z_bar, double *X_bar, int64_t ldxb, double sqrt_rho, cudaStream_t st)
+{
+    const int nsm = sdc_num_sms();
+    double *u = nullptr, *g = nullptr, *dbs = nullptr, *zbs = nullptr, *Y = nullptr, *Xw = nullptr;
+    int64_t *tile_off = nullptr;
+    SDC_CHECK(sdc_alloc(&u, total, st));
+    SDC_CHECK(sdc_alloc(&g, total, st));
+    SDC_CHECK(sdc_alloc(&dbs, total, st));
+    SDC_CHECK(sdc_alloc(&zbs, total, st));
+    SDC_CHECK(sdc_alloc(&tile_off, f.nprob + 1, st));
+    SDC_CHECK(cudaMemsetAsync(u, 0, total * sizeof(double), st));
+    SDC_CHECK(cudaMemsetAsync(g, 0, total * sizeof(double), st));
+    k_tiles_b<<<1, 1024, 0, st>>>(f.nprob, f.mk, TB, tile_off);
+    superdc_status s = SUPERDC_OK;
+    if (ncols > 0) {
+        // Y = Qhat^T X is recomputed (the rotations act on a copy of X)
+        SDC_CHECK(sdc_alloc(&Y, (size_t)total * ncols, st));
+        SDC_CHECK(sdc_alloc(&Xw, (size_t)total * ncols, st));
+        SDC_CHECK(cudaMemcpy2DAsync(Xw, total * sizeof(double), X, ldx * sizeof(double), total * sizeof(double),
+                                    ncols, cudaMemcpyDeviceToDevice, st));
+        s = cauchy_apply_T(f, total, Xw, total, Y, total, ncols, st);
+        if (s == SUPERDC_OK) s = cauchy_apply_N(f, total, Ybar, ldy, X_bar, ldxb, ncols, st);
+        for (int c0 = 0; c0 < ncols && s == SUPERDC_OK; c0 += BW_C) {
+            PROF_LAUNCH("bw_lamlam", st, k_bw_lamlam<<<(unsigned)(nsm * 4), TB, 0, st>>>(
+                f.nprob, f.off, tile_off, f.mk, f.dorg, f.eta, f.bnorm, f.pinv, Y, total, Ybar, ldy, c0,
+                std::min(BW_C, ncols - c0), u, g));
+        }
+    }
+    PROF_LAUNCH("bw_dz", st, k_bw_dz<<<(unsigned)(nsm * 4), TB, 0, st>>>(
+        f.nprob, f.off, tile_off, f.mk, f.dk, f.dorg, f.eta, f.vhat, f.bnorm, f.pinv, lam_bar, u, g, dbs, zbs));
+    k_bw_deflate<<<(unsigned)((f.nprob + 127) / 128), 128, 0, st>>>(f.nprob, f.off, f.mk, f.ngiv, f.src, f.pinv,
+                                                                    f.giv_ab, f.giv_cs, lam_bar, dbs, zbs, sqrt_rho,
+                                                                    d_bar, z_bar);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(u, st); cudaFreeAsync(g, st);
+    cudaFreeAsync(dbs, st); cudaFreeAsync(zbs, st); cudaFreeAsync(tile_off, st);
+    if (Y) cudaFreeAsync(Y, st);
+    if (Xw) cudaFreeAsync(Xw, st);
+    if (s != SUPERDC_OK) return s;
+    return e == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+}
+
 extern "C" superdc_status superdc_secular_batched_backward(
     int64_t nprob, const int64_t *offsets, int64_t total, double rho, const superdc_rank1_out *fwd,
     const double *lam_bar, int64_t ncols, const double *X, int64_t ldx, const double *Ybar, int64_t ldy,
@@ -239,52 +291,20 @@ extern "C" superdc_status superdc_secular_batched_backward(
     if (ncols > 0 && (!X || !Ybar || !X_bar || ldx < total || ldy < total || ldxb < total)) return SUPERDC_ERR_ARG;
     const int nsm = sdc_num_sms();
     int32_t *pinv = nullptr;
-    double *dorg = nullptr, *u = nullptr, *g = nullptr, *dbs = nullptr, *zbs = nullptr, *Y = nullptr, *Xw = nullptr;
-    int64_t *tile_off = nullptr;
+    double *dorg = nullptr;
     SDC_CHECK(sdc_alloc(&pinv, total, st));
     SDC_CHECK(sdc_alloc(&dorg, total, st));
-    SDC_CHECK(sdc_alloc(&u, total, st));
-    SDC_CHECK(sdc_alloc(&g, total, st));
-    SDC_CHECK(sdc_alloc(&dbs, total, st));
-    SDC_CHECK(sdc_alloc(&zbs, total, st));
-    SDC_CHECK(sdc_alloc(&tile_off, nprob + 1, st));
-    SDC_CHECK(cudaMemsetAsync(u, 0, total * sizeof(double), st));
-    SDC_CHECK(cudaMemsetAsync(g, 0, total * sizeof(double), st));
     k_prep<<<(unsigned)(nsm * 8), 256, 0, st>>>(nprob, offsets, total, fwd->mk, fwd->perm, fwd->org, fwd->dk, pinv,
                                                  dorg);
-    k_tiles_b<<<1, 1024, 0, st>>>(nprob, fwd->mk, TB, tile_off);
     FactorView f;
     f.nprob = nprob; f.off = offsets; f.mk = fwd->mk; f.ngiv = fwd->ngiv; f.dk = fwd->dk; f.eta = fwd->eta;
     f.dorg = dorg; f.vhat = fwd->vhat; f.bnorm = fwd->bnorm; f.src = fwd->src; f.perm = fwd->perm; f.pinv = pinv;
     f.giv_ab = fwd->giv_ab; f.giv_cs = fwd->giv_cs;
-    superdc_status s = SUPERDC_OK;
-    if (ncols > 0) {
-        // Y = Qhat^T X is recomputed (the rotations act on a copy of X)
-        SDC_CHECK(sdc_alloc(&Y, (size_t)total * ncols, st));
-        SDC_CHECK(sdc_alloc(&Xw, (size_t)total * ncols, st));
-        SDC_CHECK(cudaMemcpy2DAsync(Xw, total * sizeof(double), X, ldx * sizeof(double), total * sizeof(double),
-                                    ncols, cudaMemcpyDeviceToDevice, st));
-        s = cauchy_apply_T(f, total, Xw, total, Y, total, (int)ncols, st);
-        if (s == SUPERDC_OK) s = cauchy_apply_N(f, total, Ybar, ldy, X_bar, ldxb, (int)ncols, st);
-        for (int c0 = 0; c0 < ncols && s == SUPERDC_OK; c0 += BW_C) {
-            PROF_LAUNCH("bw_lamlam", st, k_bw_lamlam<<<(unsigned)(nsm * 4), TB, 0, st>>>(
-                nprob, offsets, tile_off, fwd->mk, dorg, fwd->eta, fwd->bnorm, pinv, Y, total, Ybar, ldy, c0,
-                (int)std::min<int64_t>(BW_C, ncols - c0), u, g));
-        }
-    }
-    PROF_LAUNCH("bw_dz", st, k_bw_dz<<<(unsigned)(nsm * 4), TB, 0, st>>>(
-        nprob, offsets, tile_off, fwd->mk, fwd->dk, dorg, fwd->eta, fwd->vhat, fwd->bnorm, pinv, lam_bar, u, g,
-        dbs, zbs));
-    k_bw_deflate<<<(unsigned)((nprob + 127) / 128), 128, 0, st>>>(nprob, offsets, fwd->mk, fwd->ngiv, fwd->src, pinv,
-                                                                  fwd->giv_ab, fwd->giv_cs, lam_bar, dbs, zbs,
-                                                                  sqrt(rho), d_bar, z_bar);
-    cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(pinv, st); cudaFreeAsync(dorg, st); cudaFreeAsync(u, st); cudaFreeAsync(g, st);
-    cudaFreeAsync(dbs, st); cudaFreeAsync(zbs, st); cudaFreeAsync(tile_off, st);
-    if (Y) cudaFreeAsync(Y, st);
-    if (Xw) cudaFreeAsync(Xw, st);
-    if (s != SUPERDC_OK) return s;
-    return e == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+    superdc_status s = r1_backward_fv(f, total, lam_bar, (int)ncols, X, ldx, Ybar, ldy, d_bar, z_bar, X_bar, ldxb,
+                                      sqrt(rho), st);
+    cudaFreeAsync(pinv, st);
+    cudaFreeAsync(dorg, st);
+    return s;
 }
 
 extern "C" superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offsets, int64_t total,

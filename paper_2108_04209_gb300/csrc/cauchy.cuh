@@ -25,3 +25,10 @@ superdc_status cauchy_apply_T(const FactorView &f, int64_t total, double *X, int
 // Y = Qhat X.  X rows in merged order (read only); Y rows in input order.
 superdc_status cauchy_apply_N(const FactorView &f, int64_t total, const double *X, int64_t ldx,
                               double *Y, int64_t ldy, int ncols, cudaStream_t st);
+
+// Adjoint of one batched rank-one step (backward.cu): d_bar, z_bar (input
+// order), X_bar = Qhat Ybar, from lam_bar (merged order, may be NULL) and the
+// cotangent Ybar of Qhat^T X.
+superdc_status r1_backward_fv(const FactorView &f, int64_t total, const double *lam_bar, int ncols,
+                              const double *X, int64_t ldx, const double *Ybar, int64_t ldy, double *d_bar,
+                              double *z_bar, double *X_bar, int64_t ldxb, double sqrt_rho, cudaStream_t st);

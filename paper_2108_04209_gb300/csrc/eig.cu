@@ -25,40 +25,7 @@
 #include "cauchy.cuh"
 #include "prof.cuh"
 
-struct superdc_hss {
-    int64_t n = 0;
-    int nnodes = 0, r = 0, lmax = 0, nleaves = 0, mmax = 0;
-    std::vector<int> lch, rch, level;
-    std::vector<int64_t> size, off;
-    std::vector<std::vector<int>> lev_nodes;       // nodes of each level, left to right
-    std::vector<int> leaves;                       // left to right
-    // device
-    double *D = nullptr, *U = nullptr, *R = nullptr, *B = nullptr;
-    int32_t *d_lch = nullptr, *d_rch = nullptr;
-    int64_t *d_size = nullptr;
-    int64_t *d_leaf_off = nullptr, *d_leaf_m = nullptr, *d_leaf_doff = nullptr, *d_leaf_uoff = nullptr;
-    int32_t *d_leaf_id = nullptr;
-    std::vector<int64_t *> d_lev_off;              // per level: node row offsets (nodes+1)
-    std::vector<int32_t *> d_lev_nodes;            // per level: node ids
-};
-
-struct StepF {   // stored factor of one rank-one step of one level
-    double *dk, *eta, *dorg, *vhat, *bnorm, *giv_cs;
-    int32_t *src, *pinv, *giv_ab, *mk, *ngiv, *sweeps;
-};
-
-struct superdc_eigfact {
-    const superdc_hss *h = nullptr;
-    int64_t n = 0;
-    int r = 0, lmax = 0;
-    std::vector<char *> slabs;             // device allocations owned by the handle
-    double *Qleaf = nullptr;               // concatenated leaf eigenvector blocks (column-major)
-    int64_t *d_qoff = nullptr;             // offset of each leaf's block
-    std::vector<int32_t *> P;              // per non-leaf level: merge order (node-local old position)
-    std::vector<std::vector<StepF>> F;     // [level][step]
-    int32_t *status = nullptr;             // device status word
-    cudaStream_t last_stream = nullptr;
-};
+#include "handles.cuh"
 
 namespace {
 
@@ -79,12 +46,15 @@ cudaError_t dalloc(T **p, size_t n, std::vector<char *> *own)
 //   Zhat scale: Bts = Bt / sqrt(beta), sqb = sqrt(beta)
 // H_root = 0 (the R generators of the root's children are never read).
 // ---------------------------------------------------------------------------
-__device__ void jacobi_small_maxeig(double *G, int r, double *out)
+__device__ void jacobi_small_maxeig(double *G, int r, double *out, double *V)
 {
-    // cyclic Jacobi on the r x r symmetric matrix G (column-major), one thread
+    // cyclic Jacobi on the r x r symmetric matrix G (column-major), one thread;
+    // V (r x r, may be NULL) accumulates the rotations; *out = largest eigenvalue,
+    // V's first column is overwritten with its eigenvector
     double fro = 0;
     for (int i = 0; i < r * r; i++) fro += G[i] * G[i];
     fro = sqrt(fro);
+    if (V) for (int i = 0; i < r * r; i++) V[i] = ((i % r) == (i / r)) ? 1.0 : 0.0;
     for (int sw = 0; sw < 60; sw++) {
         double off = 0;
         for (int j = 0; j < r; j++)
@@ -110,22 +80,32 @@ __device__ void jacobi_small_maxeig(double *G, int r, double *out)
                     G[k + r * p] = c * gp - s * gq;
                     G[k + r * q] = s * gp + c * gq;
                 }
+                if (V)
+                    for (int k = 0; k < r; k++) {
+                        double vp = V[k + r * p], vq = V[k + r * q];
+                        V[k + r * p] = c * vp - s * vq;
+                        V[k + r * q] = s * vp + c * vq;
+                    }
             }
     }
-    double mx = 0;
-    for (int i = 0; i < r; i++) mx = fmax(mx, G[i + r * i]);
-    *out = mx;
+    double mx = G[0];
+    int im = 0;
+    for (int i = 1; i < r; i++) if (G[i + r * i] > mx) { mx = G[i + r * i]; im = i; }
+    *out = fmax(mx, 0.0);
+    if (V && im != 0)
+        for (int k = 0; k < r; k++) V[k] = V[k + r * im];
 }
 
 __global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, const int32_t *__restrict__ lch,
                          const int32_t *__restrict__ rch, const double *__restrict__ R,
                          const double *__restrict__ B, double *__restrict__ H, double *__restrict__ Bts,
-                         double *__restrict__ sqb, int32_t *status)
+                         double *__restrict__ sqb, int32_t *status, double *__restrict__ tBt,
+                         double *__restrict__ tbeta, double *__restrict__ tu1, double *__restrict__ tv1)
 {
     extern __shared__ double sm[];
     const int rr = r * r;
     double *Hi = sm, *R1 = sm + rr, *R2 = sm + 2 * rr, *Bt = sm + 3 * rr, *T1 = sm + 4 * rr, *T2 = sm + 5 * rr,
-           *G = sm + 6 * rr;
+           *G = sm + 6 * rr, *Vg = sm + 7 * rr;
     __shared__ double s_beta;
     const int i = nodes[blockIdx.x];
     const int c1 = lch[i], c2 = rch[i];
@@ -163,12 +143,22 @@ __global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, con
     __syncthreads();
     if (threadIdx.x == 0) {
         double mx;
-        jacobi_small_maxeig(G, r, &mx);
+        jacobi_small_maxeig(G, r, &mx, Vg);
         s_beta = sqrt(fmax(mx, 0.0));
         if (!isfinite(s_beta)) sdc_latch(status, SUPERDC_DEV_NONFINITE);
     }
     __syncthreads();
     const double beta = s_beta;
+    if (tBt) {      // forward tape for the adjoint: Bt, beta, top singular pair u1 = Bt v1 / beta, v1
+        for (int e = threadIdx.x; e < rr; e += blockDim.x) tBt[(int64_t)i * rr + e] = Bt[e];
+        for (int a = threadIdx.x; a < r; a += blockDim.x) {
+            double sv = 0;
+            for (int k = 0; k < r; k++) sv += Bt[a + r * k] * Vg[k];
+            tu1[(int64_t)i * r + a] = (beta > 0) ? sv / beta : 0.0;
+            tv1[(int64_t)i * r + a] = Vg[a];
+        }
+        if (threadIdx.x == 0) tbeta[i] = beta;
+    }
     const double sb = sqrt(beta);
     for (int e = threadIdx.x; e < rr; e += blockDim.x) {
         int a = e % r, b = e / r;
@@ -681,9 +671,33 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
     auto free_tmp = [&]() { for (auto p : tmp) cudaFree(p); tmp.clear(); };
 #undef EIG_CHECK
 #define EIG_CHECK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { free_tmp(); return fail(e_); } } while (0)
-    EIG_CHECK(talloc(&H, (size_t)nn * rr));
-    EIG_CHECK(talloc(&Bts, (size_t)nn * rr));
-    EIG_CHECK(talloc(&sqb, nn));
+    Tape &T = f->tape;
+    T.on = opts->tape != 0;
+    if (T.on) {
+        EIG_CHECK(dalloc(&H, (size_t)nn * rr, &f->slabs));
+        EIG_CHECK(dalloc(&Bts, (size_t)nn * rr, &f->slabs));
+        EIG_CHECK(dalloc(&sqb, nn, &f->slabs));
+        EIG_CHECK(dalloc(&T.Bt, (size_t)nn * rr, &f->slabs));
+        EIG_CHECK(dalloc(&T.beta, nn, &f->slabs));
+        EIG_CHECK(dalloc(&T.u1, (size_t)nn * r, &f->slabs));
+        EIG_CHECK(dalloc(&T.v1, (size_t)nn * r, &f->slabs));
+        T.H = H; T.Bts = Bts; T.sqb = sqb;
+        T.lam_prev.assign(lmax, nullptr);
+        T.Wprev.assign(lmax, nullptr);
+        T.WKb.assign(lmax, std::vector<double *>(r, nullptr));
+        for (int l = 0; l < lmax; l++) {
+            const int ctot = (l == 0) ? r : 2 * r;
+            EIG_CHECK(dalloc(&T.lam_prev[l], n, &f->slabs));
+            EIG_CHECK(dalloc(&T.Wprev[l], (size_t)n * r, &f->slabs));
+            for (int j = 0; j < r; j++) EIG_CHECK(dalloc(&T.WKb[l][j], (size_t)n * (ctot - j), &f->slabs));
+        }
+        EIG_CHECK(cudaMemsetAsync(T.Bt, 0, (size_t)nn * rr * sizeof(double), st));
+        EIG_CHECK(cudaMemsetAsync(T.beta, 0, nn * sizeof(double), st));
+    } else {
+        EIG_CHECK(talloc(&H, (size_t)nn * rr));
+        EIG_CHECK(talloc(&Bts, (size_t)nn * rr));
+        EIG_CHECK(talloc(&sqb, nn));
+    }
     EIG_CHECK(talloc(&lamA, n));
     EIG_CHECK(talloc(&lamB, n));
     EIG_CHECK(talloc(&Wp, (size_t)n * r));
@@ -701,8 +715,9 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
         std::vector<int> nodes;
         for (int i : h->lev_nodes[l]) if (h->lch[i] >= 0) nodes.push_back(i);
         if (nodes.empty()) continue;
-        PROF_LAUNCH("divide", st, k_divide<<<(unsigned)nodes.size(), 128, 7 * rr * sizeof(double), st>>>(
-            h->d_lev_nodes[l], nn - 1, r, h->d_lch, h->d_rch, h->R, h->B, H, Bts, sqb, f->status));
+        PROF_LAUNCH("divide", st, k_divide<<<(unsigned)nodes.size(), 128, 8 * rr * sizeof(double), st>>>(
+            h->d_lev_nodes[l], nn - 1, r, h->d_lch, h->d_rch, h->R, h->B, H, Bts, sqb, f->status,
+            T.on ? T.Bt : nullptr, T.beta, T.u1, T.v1));
     }
     // ---- 2. leaves
     {
@@ -718,12 +733,19 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
         const int nl = (int)h->lev_nodes[l].size();
         const bool root = (l == 0);
         const int ctot = root ? r : 2 * r;
+        if (T.on) {
+            EIG_CHECK(cudaMemcpyAsync(T.lam_prev[l], dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            EIG_CHECK(cudaMemcpyAsync(T.Wprev[l], Wp, (size_t)n * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
         PROF_LAUNCH("build", st, k_build<<<(unsigned)(nsm * 4), 256, 0, st>>>(
             n, r, nl, h->d_lev_off[l], h->d_lev_nodes[l], nn - 1, h->d_lch, h->d_rch, h->d_size, h->R, Bts, sqb,
             dcur, Wp, dnxt, f->P[l], WK));
         std::swap(dcur, dnxt);
         for (int j = 0; j < r; j++) {
             StepF &S = f->F[l][j];
+            if (T.on)
+                EIG_CHECK(cudaMemcpyAsync(T.WKb[l][j], WK + (int64_t)j * n, (size_t)n * (ctot - j) * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, st));
             // level-batched (default): every node of the level is one problem of
             // one launch sequence; unbatched baseline: one sequence per node
             const int nseg = opts->batching ? 1 : nl;
@@ -882,3 +904,14 @@ superdc_status superdc_eigfact_shape(const superdc_eigfact *f, int32_t *lmax, in
 }
 
 }  // extern "C"
+
+FactorView factor_view(const superdc_eigfact *f, int l, int j) { return view(f, l, j); }
+
+superdc_status leaves_apply(const superdc_eigfact *f, int trans, int ncols, const double *X, int64_t ldx, double *Y,
+                            int64_t ldy, cudaStream_t st)
+{
+    const superdc_hss *h = f->h;
+    k_leaf_apply<<<(unsigned)h->nleaves, 256, 0, st>>>(f->n, h->d_leaf_off, h->d_leaf_m, f->Qleaf, f->d_qoff, X, ldx,
+                                                       Y, ldy, ncols, trans);
+    return cudaGetLastError() == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+}

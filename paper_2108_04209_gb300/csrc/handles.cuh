@@ -1,0 +1,58 @@
+// Internal layout of the library handles (shared by the forward and the adjoint).
+#pragma once
+#include <vector>
+#include <cuda_runtime.h>
+#include "common.cuh"
+#include "cauchy.cuh"
+
+struct superdc_hss {
+    int64_t n = 0;
+    int nnodes = 0, r = 0, lmax = 0, nleaves = 0, mmax = 0;
+    std::vector<int> lch, rch, level;
+    std::vector<int64_t> size, off;
+    std::vector<std::vector<int>> lev_nodes;       // nodes of each level, left to right
+    std::vector<int> leaves;                       // left to right
+    // device
+    double *D = nullptr, *U = nullptr, *R = nullptr, *B = nullptr;
+    int32_t *d_lch = nullptr, *d_rch = nullptr;
+    int64_t *d_size = nullptr;
+    int64_t *d_leaf_off = nullptr, *d_leaf_m = nullptr, *d_leaf_doff = nullptr, *d_leaf_uoff = nullptr;
+    int32_t *d_leaf_id = nullptr;
+    std::vector<int64_t *> d_lev_off;              // per level: node row offsets (nodes+1)
+    std::vector<int32_t *> d_lev_nodes;            // per level: node ids
+};
+
+struct StepF {   // stored factor of one rank-one step of one level
+    double *dk, *eta, *dorg, *vhat, *bnorm, *giv_cs;
+    int32_t *src, *pinv, *giv_ab, *mk, *ngiv, *sweeps;
+};
+
+// Forward intermediates kept for superdc_eig_backward (opts.tape = 1).
+struct Tape {
+    bool on = false;
+    std::vector<double *> lam_prev;             // [level] children's eigenvalues (n), input of the level build
+    std::vector<double *> Wprev;                // [level] children's W = Q_c^T U_c (n x r)
+    std::vector<std::vector<double *>> WKb;     // [level][step] columns step..ctot-1 before the step (n x (ctot-step))
+    double *H = nullptr, *Bt = nullptr, *Bts = nullptr, *beta = nullptr, *sqb = nullptr, *u1 = nullptr, *v1 = nullptr;
+};
+
+struct superdc_eigfact {
+    const superdc_hss *h = nullptr;
+    Tape tape;
+    int64_t n = 0;
+    int r = 0, lmax = 0;
+    std::vector<char *> slabs;             // device allocations owned by the handle
+    double *Qleaf = nullptr;               // concatenated leaf eigenvector blocks (column-major)
+    int64_t *d_qoff = nullptr;             // offset of each leaf's block
+    std::vector<int32_t *> P;              // per non-leaf level: merge order (node-local old position)
+    std::vector<std::vector<StepF>> F;     // [level][step]
+    int32_t *status = nullptr;             // device status word
+    cudaStream_t last_stream = nullptr;
+};
+
+
+// the stored factor of rank-one step j of level l, as a batched view
+FactorView factor_view(const superdc_eigfact *f, int l, int j);
+// dense leaf blocks: Y = Q_leaf^T X (trans) or Q_leaf X, all leaves
+superdc_status leaves_apply(const superdc_eigfact *f, int trans, int ncols, const double *X, int64_t ldx, double *Y,
+                            int64_t ldy, cudaStream_t st);
