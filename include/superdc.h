@@ -57,11 +57,15 @@ typedef struct {
                              root pools, 2 CTA warps split the poles of one 32-root group */
     int32_t tape;         /* superdc_eig: 1 = keep the forward intermediates that
                              superdc_eig_backward needs (O(r^2 n log n) doubles) */
-    int32_t pad;
+    int32_t fmm_min_m;    /* rank-one problems whose kept size is at least this use the triangular
+                             FMM with local shifting (Sections 4.1.2, 4.2.2, 4.3) for the secular
+                             sweeps, zhat, b and the Cauchy-like applications; smaller ones the
+                             direct tiled evaluator.  0 = the library default (the crossover
+                             measured on GB300), < 0 = direct evaluator only */
 } superdc_opts;
 
 /* Fills *opts with the defaults: tau = 1e-10, stop_c = 8, max_iter = 50,
- * tile_roots = 0 (automatic), batching = 1, sched = 0, tape = 0. */
+ * tile_roots = 0 (automatic), batching = 1, sched = 0, tape = 0, fmm_min_m = 0 (default crossover). */
 superdc_status superdc_opts_default(superdc_opts *opts);
 
 /* Human-readable name of a status code (static string). */
@@ -102,7 +106,9 @@ const char *superdc_status_string(superdc_status s);
  *                [x_a; x_b] <- [c x_a - s x_b; s x_a + c x_b];
  *   mk[p], ngiv[p] (int32, length nprob);
  *   sweeps[slot] (may be NULL) secular sweeps used per root;
- *   status (int32, length 1): SUPERDC_DEV_* bits, OR-ed (caller zeroes it).
+ *   status (int32, length 1): SUPERDC_DEV_* bits, OR-ed (caller zeroes it);
+ *   fmm[p] (may be NULL; int32, length nprob): 1 if problem p took the
+ *                triangular FMM path (opts.fmm_min_m), else 0.
  * Scratch is taken from the stream-ordered allocator and released on the
  * same stream.
  * -------------------------------------------------------------------- */
@@ -122,6 +128,7 @@ typedef struct {
     int32_t *ngiv;
     int32_t *sweeps;
     int32_t *status;
+    int32_t *fmm;
 } superdc_rank1_out;
 
 superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, int64_t total,
@@ -265,6 +272,11 @@ superdc_status superdc_eig_backward(const superdc_hss *h, const superdc_eigfact 
                                     const double *Ybar, int64_t ldy, double *gD, double *gU, double *gR,
                                     double *gB, double *gV, int64_t ldgv, cudaStream_t stream);
 
+/* FMM threshold of later superdc_apply_Q calls on this factor (same meaning
+ * as superdc_opts.fmm_min_m; superdc_eig sets it from its options).  The
+ * factor itself does not depend on it. */
+superdc_status superdc_eigfact_set_fmm_min_m(superdc_eigfact *f, int32_t fmm_min_m);
+
 /* Latched device status of a handle (synchronises the handle's last work):
  * SUPERDC_OK, SUPERDC_ERR_NONFINITE or SUPERDC_ERR_NOCONV. */
 superdc_status superdc_sync_status(const superdc_eigfact *f);
@@ -281,7 +293,8 @@ superdc_status superdc_eigfact_stats(const superdc_eigfact *f, int64_t *deflated
  *   "dk", "eta", "dorg", "vhat", "bnorm"  (double), "src", "pinv" (int32),
  *   "P" (int32, the merge order of eq. (4.31); step ignored),
  *   "giv_cs" (double, 2n), "giv_ab" (int32, 2n);
- * per node of the level: "mk", "ngiv" (int32).  Synchronous. */
+ * per node of the level: "mk", "ngiv", "fmm" (int32; fmm = 1 where the
+ * node's step took the triangular FMM path).  Synchronous. */
 superdc_status superdc_eigfact_get(const superdc_eigfact *f, int32_t level, int32_t step,
                                    const char *field, void *dst);
 /* Tree depth lmax (levels of non-leaf nodes are 0 .. lmax-1), rank r, order n. */

@@ -43,7 +43,7 @@ def alloc_rank1_out(nprob, total, device, sweeps=True):
                giv_ab=torch.empty(2 * n, **i32), giv_cs=torch.empty(2 * n, **f64),
                mk=torch.empty(max(nprob, 1), **i32), ngiv=torch.empty(max(nprob, 1), **i32),
                sweeps=torch.empty(n, **i32) if sweeps else None,
-               status=torch.zeros(1, **i32))
+               status=torch.zeros(1, **i32), fmm=torch.zeros(max(nprob, 1), **i32))
     return out
 
 
@@ -161,6 +161,10 @@ class EigFactor:
         L.check(code, "superdc_apply_Q")
         return Y.reshape(-1) if vec else Y
 
+    def set_fmm_min_m(self, fmm_min_m):
+        """FMM threshold of later apply_Q calls (opts.fmm_min_m meaning)."""
+        L.check(L.lib().superdc_eigfact_set_fmm_min_m(self._f, int(fmm_min_m)), "superdc_eigfact_set_fmm_min_m")
+
     def stats(self):
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         L.check(L.lib().superdc_eigfact_stats(self._f, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
@@ -173,7 +177,7 @@ class EigFactor:
         spec = {"dk": (n, np.float64), "eta": (n, np.float64), "dorg": (n, np.float64), "vhat": (n, np.float64),
                 "bnorm": (n, np.float64), "src": (n, np.int32), "pinv": (n, np.int32), "P": (n, np.int32),
                 "giv_cs": (2 * n, np.float64), "giv_ab": (2 * n, np.int32), "mk": (nn, np.int32),
-                "ngiv": (nn, np.int32)}
+                "ngiv": (nn, np.int32), "fmm": (nn, np.int32)}
         cnt, dt = spec[field]
         out = np.empty(cnt, dt)
         L.check(L.lib().superdc_eigfact_get(self._f, level, step, field.encode(), out.ctypes.data),

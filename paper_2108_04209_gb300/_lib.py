@@ -26,7 +26,7 @@ class SuperDCError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("tau", c_double), ("stop_c", c_double), ("max_iter", c_int32),
                 ("tile_roots", c_int32), ("batching", c_int32), ("sched", c_int32), ("tape", c_int32),
-                ("pad", c_int32)]
+                ("fmm_min_m", c_int32)]
 
 
 class Tree(ctypes.Structure):
@@ -36,7 +36,7 @@ class Tree(ctypes.Structure):
 
 class Rank1Out(ctypes.Structure):
     _fields_ = [(n, c_void_p) for n in ("lam", "dk", "zk", "eta", "vhat", "bnorm", "org", "src", "perm",
-                                         "giv_ab", "giv_cs", "mk", "ngiv", "sweeps", "status")]
+                                         "giv_ab", "giv_cs", "mk", "ngiv", "sweeps", "status", "fmm")]
 
 
 _lib = None
@@ -68,6 +68,8 @@ def lib():
         L.superdc_eigfact_free.restype = None
         L.superdc_apply_Q.argtypes = [c_void_p, c_int32, c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p]
         L.superdc_apply_Q.restype = c_int32
+        L.superdc_eigfact_set_fmm_min_m.argtypes = [c_void_p, c_int32]
+        L.superdc_eigfact_set_fmm_min_m.restype = c_int32
         L.superdc_sync_status.argtypes = [c_void_p]
         L.superdc_sync_status.restype = c_int32
         L.superdc_eigfact_stats.argtypes = [c_void_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_int64),

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "rank1.cuh"
+#include "fmm.cuh"
 
 int sdc_num_sms()
 {
@@ -28,7 +29,7 @@ superdc_status superdc_opts_default(superdc_opts *opts)
     opts->batching = 1;
     opts->sched = 0;
     opts->tape = 0;
-    opts->pad = 0;
+    opts->fmm_min_m = 0;
     return SUPERDC_OK;
 }
 
@@ -78,10 +79,11 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
     a.max_iter = opts->max_iter;
     a.tile_roots = opts->tile_roots;
     a.sched = opts->sched;
+    a.fmm_min_m = fmm_resolve(opts->fmm_min_m);
     a.o.lam = out->lam; a.o.dk = out->dk; a.o.zk = out->zk; a.o.eta = out->eta;
     a.o.vhat = out->vhat; a.o.bnorm = out->bnorm; a.o.org = out->org; a.o.src = out->src;
     a.o.perm = out->perm; a.o.giv_ab = out->giv_ab; a.o.giv_cs = out->giv_cs; a.o.mk = out->mk;
-    a.o.ngiv = out->ngiv; a.o.sweeps = out->sweeps; a.o.status = out->status;
+    a.o.ngiv = out->ngiv; a.o.sweeps = out->sweeps; a.o.status = out->status; a.o.fmm_used = out->fmm;
     SDC_CHECK(sdc_alloc(&a.o.dorg, total, stream));
     SDC_CHECK(sdc_alloc(&a.o.wsum, nprob, stream));
     SDC_CHECK(sdc_alloc(&a.o.pinv, total, stream));

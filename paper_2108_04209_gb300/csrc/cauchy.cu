@@ -9,7 +9,9 @@
 // FP64 FMAs in registers, the operands of the other side are staged in shared
 // memory in chunks of TI rows.
 #include "common.cuh"
+#include <algorithm>
 #include "cauchy.cuh"
+#include "fmm.cuh"
 #include "prof.cuh"
 
 namespace {
@@ -93,7 +95,7 @@ __global__ void k_givens(FactorView f, double *X, int64_t ldx, int ncols, int in
 template <int NC>
 __global__ void __launch_bounds__(TJ)
 k_cauchy_T(FactorView f, const int64_t *__restrict__ tile_off, const double *__restrict__ X, int64_t ldx,
-           double *__restrict__ Y, int64_t ldy, int col0, int ncols)
+           double *__restrict__ Y, int64_t ldy, int col0, int ncols, const int32_t *__restrict__ fslot)
 {
     __shared__ double sd[TI];
     __shared__ double sx[NC][TI];
@@ -101,6 +103,7 @@ k_cauchy_T(FactorView f, const int64_t *__restrict__ tile_off, const double *__r
     const int nc = min(NC, ncols - col0);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t p = sdc_upper_index(tile_off, f.nprob, tile);
+        if (fslot && fslot[p] >= 0) continue;   // FMM problem (uniform per CTA)
         const int64_t b0 = f.off[p];
         const int m = f.mk[p];
         const int j = (int)(tile - tile_off[p]) * TJ + threadIdx.x;
@@ -144,7 +147,7 @@ k_cauchy_T(FactorView f, const int64_t *__restrict__ tile_off, const double *__r
 template <int NC>
 __global__ void __launch_bounds__(TJ)
 k_cauchy_N(FactorView f, const int64_t *__restrict__ tile_off, const double *__restrict__ X, int64_t ldx,
-           double *__restrict__ Y, int64_t ldy, int col0, int ncols)
+           double *__restrict__ Y, int64_t ldy, int col0, int ncols, const int32_t *__restrict__ fslot)
 {
     __shared__ double sk[TI], se[TI];
     __shared__ double sx[NC][TI];
@@ -152,6 +155,7 @@ k_cauchy_N(FactorView f, const int64_t *__restrict__ tile_off, const double *__r
     const int nc = min(NC, ncols - col0);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t p = sdc_upper_index(tile_off, f.nprob, tile);
+        if (fslot && fslot[p] >= 0) continue;   // FMM problem (uniform per CTA)
         const int64_t b0 = f.off[p];
         const int m = f.mk[p];
         const int i = (int)(tile - tile_off[p]) * TJ + threadIdx.x;
@@ -225,20 +229,20 @@ int pick_nc(int c)
 
 template <int NC>
 void launch_T(const FactorView &f, const int64_t *tile_off, const double *X, int64_t ldx, double *Y, int64_t ldy,
-              int col0, int ncols, unsigned grid, cudaStream_t st)
+              int col0, int ncols, unsigned grid, const int32_t *fslot, cudaStream_t st)
 {
-    k_cauchy_T<NC><<<grid, TJ, 0, st>>>(f, tile_off, X, ldx, Y, ldy, col0, ncols);
+    k_cauchy_T<NC><<<grid, TJ, 0, st>>>(f, tile_off, X, ldx, Y, ldy, col0, ncols, fslot);
 }
 
 template <int NC>
 void launch_N(const FactorView &f, const int64_t *tile_off, const double *X, int64_t ldx, double *Y, int64_t ldy,
-              int col0, int ncols, unsigned grid, cudaStream_t st)
+              int col0, int ncols, unsigned grid, const int32_t *fslot, cudaStream_t st)
 {
-    k_cauchy_N<NC><<<grid, TJ, 0, st>>>(f, tile_off, X, ldx, Y, ldy, col0, ncols);
+    k_cauchy_N<NC><<<grid, TJ, 0, st>>>(f, tile_off, X, ldx, Y, ldy, col0, ncols, fslot);
 }
 
 typedef void (*LaunchFn)(const FactorView &, const int64_t *, const double *, int64_t, double *, int64_t, int, int,
-                         unsigned, cudaStream_t);
+                         unsigned, const int32_t *, cudaStream_t);
 
 LaunchFn pick(bool trans, int nc)
 {
@@ -267,11 +271,22 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
         PROF_LAUNCH("givens", st, k_givens<<<(unsigned)((nt + gthreads - 1) / gthreads), gthreads, 0, st>>>(
             f, Xmut, ldx, ncols, 0));
     }
+    // problems whose kept size reaches the threshold: triangular FMM
+    FmmPlan fp;
+    {
+        const int w = std::min(32, ncols);
+        superdc_status fs = fmm_plan(fp, f.nprob, f.off, total, f.max_m, f.mk, f.dk, f.fmm_min_m, w, w, nullptr,
+                                     st);
+        if (fs != SUPERDC_OK) { fmm_free(fp, st); cudaFreeAsync(tile_off, st); return fs; }
+    }
+    const int32_t *fslot = fp.on ? fp.dv.fslot : nullptr;
+    superdc_status fs = SUPERDC_OK;
     const unsigned grid = (unsigned)(nsm * 4);
     for (int c0 = 0; c0 < ncols; c0 += 32) {
         const int c = min(32, ncols - c0);
         LaunchFn fn = pick(trans, pick_nc(c));
-        PROF_LAUNCH("cauchy", st, fn(f, tile_off, X, ldx, Y, ldy, c0, ncols, grid, st));
+        PROF_LAUNCH("cauchy", st, fn(f, tile_off, X, ldx, Y, ldy, c0, ncols, grid, fslot, st));
+        if (fs == SUPERDC_OK) fs = fmm_cauchy(fp, f, X, ldx, Y, ldy, c0, c, trans, st);
     }
     PROF_LAUNCH("deflcopy", st, k_defl_copy<<<(unsigned)(nsm * 8), 256, 0, st>>>(f, total, X, ldx, Y, ldy, ncols,
                                                                                   trans ? 1 : 0));
@@ -282,7 +297,8 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
     }
     SDC_CHECK(cudaGetLastError());
     SDC_CHECK(cudaFreeAsync(tile_off, st));
-    return SUPERDC_OK;
+    fmm_free(fp, st);
+    return fs;
 }
 
 }  // namespace

@@ -14,6 +14,8 @@ struct FactorView {
     const double *dk, *eta, *dorg, *vhat, *bnorm;   // device, per slot
     const int32_t *src, *perm, *pinv, *giv_ab;      // device
     const double *giv_cs;
+    int32_t fmm_min_m = 0;   // kept size from which a problem takes the FMM path (0: direct only)
+    int64_t max_m = -1;      // upper bound on the problem sizes (-1: unknown)
 };
 
 // Y = Qhat^T X.  X (rows in the step's input order) is overwritten by the

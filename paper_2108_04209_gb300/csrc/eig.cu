@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "rank1.cuh"
 #include "cauchy.cuh"
+#include "fmm.cuh"
 #include "prof.cuh"
 
 #include "handles.cuh"
@@ -473,6 +474,10 @@ FactorView view(const superdc_eigfact *f, int l, int j)
     v.mk = S.mk; v.ngiv = S.ngiv;
     v.dk = S.dk; v.eta = S.eta; v.dorg = S.dorg; v.vhat = S.vhat; v.bnorm = S.bnorm;
     v.src = S.src; v.perm = nullptr; v.pinv = S.pinv; v.giv_ab = S.giv_ab; v.giv_cs = S.giv_cs;
+    v.fmm_min_m = f->fmm_min_m;
+    int64_t mx = 0;
+    for (int i : h->lev_nodes[l]) mx = std::max<int64_t>(mx, h->size[i]);
+    v.max_m = mx;
     return v;
 }
 
@@ -632,6 +637,7 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
     const int r = h->r, lmax = h->lmax, rr = r * r, nn = h->nnodes;
     superdc_eigfact *f = new superdc_eigfact();
     f->h = h; f->n = n; f->r = r; f->lmax = lmax;
+    f->fmm_min_m = fmm_resolve(opts->fmm_min_m);
     auto fail = [&](cudaError_t e) {
         superdc_eigfact_free(f);
         return e == cudaErrorMemoryAllocation ? SUPERDC_ERR_OOM : SUPERDC_ERR_CUDA;
@@ -658,9 +664,9 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
             S.dk = dslab; S.eta = dslab + n; S.dorg = dslab + 2 * n; S.vhat = dslab + 3 * n;
             S.bnorm = dslab + 4 * n; S.giv_cs = dslab + 5 * n;
             int32_t *islab;
-            EIG_CHECK(dalloc(&islab, 5 * n + 2 * np, &f->slabs));
+            EIG_CHECK(dalloc(&islab, 5 * n + 3 * np, &f->slabs));
             S.src = islab; S.pinv = islab + n; S.giv_ab = islab + 2 * n; S.sweeps = islab + 4 * n;
-            S.mk = islab + 5 * n; S.ngiv = islab + 5 * n + np;
+            S.mk = islab + 5 * n; S.ngiv = islab + 5 * n + np; S.fmm = islab + 5 * n + 2 * np;
         }
     }
     // ---- work buffers (released at the end of the call)
@@ -733,6 +739,8 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
         const int nl = (int)h->lev_nodes[l].size();
         const bool root = (l == 0);
         const int ctot = root ? r : 2 * r;
+        int64_t lev_max = 0;
+        for (int i : h->lev_nodes[l]) lev_max = std::max<int64_t>(lev_max, h->size[i]);
         if (T.on) {
             EIG_CHECK(cudaMemcpyAsync(T.lam_prev[l], dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
             EIG_CHECK(cudaMemcpyAsync(T.Wprev[l], Wp, (size_t)n * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -757,16 +765,22 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
                 a.d = dcur; a.z = WK + (int64_t)j * n;
                 a.sqrt_rho = 1.0; a.tau = opts->tau; a.stop_c = opts->stop_c; a.max_iter = opts->max_iter;
                 a.tile_roots = opts->tile_roots; a.sched = opts->sched;
+                a.fmm_min_m = f->fmm_min_m;
+                a.max_m = opts->batching ? lev_max : a.rows;
                 a.o.lam = dnxt; a.o.dk = S.dk; a.o.zk = zk; a.o.eta = S.eta; a.o.vhat = S.vhat;
                 a.o.bnorm = S.bnorm; a.o.org = org; a.o.src = S.src; a.o.perm = perm; a.o.giv_ab = S.giv_ab;
                 a.o.giv_cs = S.giv_cs; a.o.mk = S.mk + q; a.o.ngiv = S.ngiv + q; a.o.sweeps = S.sweeps;
                 a.o.status = f->status; a.o.dorg = S.dorg; a.o.pinv = S.pinv; a.o.wsum = wsum + q;
+                a.o.fmm_used = S.fmm + q;
                 superdc_status s1 = r1_run(a, st);
                 if (s1 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s1; }
                 const int c = ctot - (j + 1);
                 if (c > 0) {
                     FactorView v = view(f, l, j);
-                    if (!opts->batching) { v.nprob = 1; v.off += q; v.mk += q; v.ngiv += q; }
+                    if (!opts->batching) {
+                        v.nprob = 1; v.off += q; v.mk += q; v.ngiv += q;
+                        v.max_m = h->size[h->lev_nodes[l][q]];
+                    }
                     superdc_status s2 = cauchy_apply_T(v, n, WK + (int64_t)(j + 1) * n, n,
                                                        WK2 + (int64_t)(j + 1) * n, n, c, st);
                     if (s2 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s2; }
@@ -841,6 +855,13 @@ superdc_status superdc_apply_Q(const superdc_eigfact *f, int32_t trans, int64_t 
     return e == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
 }
 
+superdc_status superdc_eigfact_set_fmm_min_m(superdc_eigfact *f, int32_t fmm_min_m)
+{
+    if (!f) return SUPERDC_ERR_ARG;
+    f->fmm_min_m = fmm_resolve(fmm_min_m);
+    return SUPERDC_OK;
+}
+
 superdc_status superdc_sync_status(const superdc_eigfact *f)
 {
     if (!f) return SUPERDC_ERR_ARG;
@@ -890,6 +911,7 @@ superdc_status superdc_eigfact_get(const superdc_eigfact *f, int32_t level, int3
     else if (fld == "giv_ab") { src = S.giv_ab; bytes = 2 * n * 4; }
     else if (fld == "mk") { src = S.mk; bytes = np * 4; }
     else if (fld == "ngiv") { src = S.ngiv; bytes = np * 4; }
+    else if (fld == "fmm") { src = S.fmm; bytes = np * 4; }
     else return SUPERDC_ERR_ARG;
     return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
 }

@@ -1,0 +1,65 @@
+// Triangular FMM with local shifting for the large problems of a batched
+// rank-one step (Sections 4.1.2, 4.2.2 and 4.3): the secular sweeps (the lower
+// and upper triangular sums psi, phi and their derivatives, eq. (4.10)), the
+// Loewner zhat in logarithmic form (eq. (4.25)), the normalisation b
+// (eq. (4.27)) and the Cauchy-like applications of eq. (4.29).
+//
+// Problems whose kept size is at least min_m take this path; the direct
+// evaluators skip them (each direct kernel reads the plan's fslot array).
+#pragma once
+#include <vector>
+#include "common.cuh"
+#include "rank1.cuh"
+#include "cauchy.cuh"
+
+constexpr int FMM_B = 64;      // indices per leaf box
+constexpr int FMM_P = 24;      // Chebyshev nodes (expansion order) per box
+constexpr int FMM_NCAP = 32;   // near-list capacity per box (a box whose list would be longer, and
+                               // its subtree, sums its targets directly over all sources)
+
+// Device view of a plan: which problems of the batch use the FMM and their
+// box trees (index-based binary tree over the kept poles, near lists from the
+// geometric admissibility test).
+struct FmmDev {
+    int64_t nprob;
+    const int64_t *box_base, *leaf_base;   // nprob+1: boxes / leaf boxes per problem (prefix)
+    int32_t *fslot;                        // nprob: >= 0 FMM problem, -1 direct
+    const int32_t *fprob, *nfmm;           // FMM problem -> batch problem; count
+    const double *blo, *bhi;               // per box: interval [lo, hi] of its points
+    const int32_t *nnear, *near;           // per box: near list (same level); nnear < 0: every source direct
+    double *M, *W, *coef;                  // workspace: moments, node weights, leaf coefficients
+    int ncol, nfield;                      // workspace widths
+};
+
+struct FmmPlan {
+    FmmDev dv{};
+    int64_t cap_boxes = 0, cap_leaves = 0, cap_f = 0;
+    int lmax = 0;                          // upper bound on tree levels
+    bool on = false;                       // some problem may take the FMM path
+    std::vector<void *> bufs;
+};
+
+// Decide per problem (kept size mk >= min_m) and build the box trees from the
+// kept poles dk.  max_m: an upper bound on the problem sizes (-1 unknown).
+// ncol / nfield: widths of the moment and coefficient workspaces.
+// used (may be NULL): per problem 1 if it takes the FMM path, else 0.
+superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
+                        const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,
+                        cudaStream_t st);
+void fmm_free(FmmPlan &pl, cudaStream_t st);
+
+// Roots of the FMM problems (same outputs as the direct secular kernel).
+superdc_status fmm_secular(const FmmPlan &pl, const int64_t *off, const R1Out &o, double stop_c, int max_iter,
+                           cudaStream_t st);
+// zhat (eq. (4.23) via eq. (4.25)) and b (eq. (4.27)) of the FMM problems.
+superdc_status fmm_lowner(const FmmPlan &pl, const int64_t *off, const R1Out &o, cudaStream_t st);
+superdc_status fmm_bnorm(const FmmPlan &pl, const int64_t *off, const R1Out &o, cudaStream_t st);
+// Columns [col0, col0 + nc) of Y = Qhat^T X (trans) or Y = Qhat X for the FMM
+// problems (layouts as cauchy_apply_T / cauchy_apply_N; X already rotated for trans).
+superdc_status fmm_cauchy(const FmmPlan &pl, const FactorView &f, const double *X, int64_t ldx, double *Y,
+                          int64_t ldy, int col0, int nc, bool trans, cudaStream_t st);
+
+// Library default of the FMM threshold (kept problem size), and the
+// threshold an option value selects (> 0 itself, 0 the default, < 0 off).
+int fmm_default_min_m();
+inline int fmm_resolve(int32_t opt) { return opt > 0 ? opt : (opt == 0 ? fmm_default_min_m() : 0); }

@@ -25,6 +25,7 @@ struct superdc_hss {
 struct StepF {   // stored factor of one rank-one step of one level
     double *dk, *eta, *dorg, *vhat, *bnorm, *giv_cs;
     int32_t *src, *pinv, *giv_ab, *mk, *ngiv, *sweeps;
+    int32_t *fmm;   // per node: 1 if the step took the FMM path
 };
 
 // Forward intermediates kept for superdc_eig_backward (opts.tape = 1).
@@ -47,6 +48,7 @@ struct superdc_eigfact {
     std::vector<int32_t *> P;              // per non-leaf level: merge order (node-local old position)
     std::vector<std::vector<StepF>> F;     // [level][step]
     int32_t *status = nullptr;             // device status word
+    int fmm_min_m = 0;                     // resolved FMM threshold of the factorisation (0: direct)
     cudaStream_t last_stream = nullptr;
 };
 

@@ -25,6 +25,8 @@
 #include "common.cuh"
 #include "rank1.cuh"
 #include "prof.cuh"
+#include "secular.cuh"
+#include "fmm.cuh"
 #include <algorithm>
 #include <mutex>
 
@@ -33,76 +35,6 @@ namespace {
 constexpr int SEC_CHUNK = 2048;   // poles staged per shared-memory chunk
 constexpr int DEFL_BIG = 128;     // problems larger than this deflate with a whole CTA
 
-// ---------------------------------------------------------------------------
-// FP64 reciprocal without the FP64 divide sequence.  The GB300 FP64 pipe
-// retires ~2 DFMA per clock per SM, so every FP64 instruction of the inner
-// loops counts, while integer and MUFU pipes are nearly free.  Seed: the
-// leading 23 mantissa bits of |t| as a float in [1,2), reciprocal on the MUFU
-// (rcp.approx.f32, relative error < 2^-22 after the truncation), exponent and
-// sign rebuilt with integer arithmetic (valid for every normal double).  Then
-// Newton-Raphson r <- r + r (1 - t r), which squares the relative error:
-// one step -> < 2^-44, two steps -> correctly rounded up to ~1 ulp.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float mufu_rcp(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ double rcp_seed(double t)
-{
-    const int hi = __double2hiint(t);
-    const unsigned lo = (unsigned)__double2loint(t);
-    const unsigned sign = (unsigned)hi & 0x80000000u;
-    const int e = (hi >> 20) & 0x7FF;
-    const unsigned mb = (((unsigned)hi & 0xFFFFFu) << 3) | (lo >> 29);
-    const float rm = mufu_rcp(__uint_as_float(0x3F800000u | mb));   // in (0.5, 1]
-    const unsigned rb = __float_as_uint(rm);
-    const int E = (int)(rb >> 23) - 127 - (e - 1023) + 1023;
-    const unsigned rmant = rb & 0x7FFFFFu;
-    return __hiloint2double((int)(sign | ((unsigned)E << 20) | (rmant >> 3)), (int)(rmant << 29));
-}
-
-// one Newton step: relative error < 2^-44 (secular sweeps: every term of psi
-// (phi) has the same sign, so the sum inherits the per-term bound, which is
-// below the stopping tolerance of eq. (4.12) for m >= 32)
-__device__ __forceinline__ double rcp_nr1(double t)
-{
-    double r = rcp_seed(t);
-    double e = fma(-t, r, 1.0);
-    return fma(r, e, r);
-}
-
-// two Newton steps: full FP64 accuracy (b, Cauchy-like applications)
-__device__ __forceinline__ double rcp_nr2(double t)
-{
-    double r = rcp_seed(t);
-    double e = fma(-t, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-t, r, 1.0);
-    return fma(r, e, r);
-}
-
-// root of a*y^2 + b*y + c = 0 strictly inside (lo, hi), else the bracket middle
-__device__ double quad_in(double a, double b, double c, double lo, double hi)
-{
-    double mid = 0.5 * (lo + hi);
-    if (a == 0.0) {
-        if (b == 0.0) return mid;
-        double y = -c / b;
-        return (y > lo && y < hi) ? y : mid;
-    }
-    double disc = b * b - 4.0 * a * c;
-    if (!(disc >= 0.0)) return mid;
-    double sq = sqrt(disc);
-    double q = -0.5 * (b + (b >= 0 ? sq : -sq));
-    double y1 = q / a;
-    double y2 = (q != 0.0) ? c / q : y1;
-    if (y1 > lo && y1 < hi) return y1;
-    if (y2 > lo && y2 < hi) return y2;
-    return mid;
-}
 
 // ---------------------------------------------------------------------------
 // Deflation (Remark 4.1), one thread per problem.
@@ -415,149 +347,6 @@ __global__ void k_tiles(int64_t nprob, const int32_t *__restrict__ mk, int tr, i
     for (int64_t p = beg; p < end; p++) { tile_off[p] = acc; acc += (mk[p] + tr - 1) / tr; }
 }
 
-// ---------------------------------------------------------------------------
-// Secular roots.
-// ---------------------------------------------------------------------------
-struct Acc { double psi, phi, dpsi, dphi; };
-
-// Accumulate the triangular parts over poles [j0, j1) of a staged chunk whose
-// first pole has global index jg0.  Pole j goes to psi if j <= k, else to phi.
-// The warp's roots are consecutive (kwlo..kwhi), so the loop runs in three
-// warp-uniform regions; only the middle one selects per lane.
-__device__ __forceinline__ int fexp(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
-
-// Every term uses the shifted difference (d_j - d_K) - y of eq. (4.14).  (The
-// local-shifting variant that takes d_j - x for far poles, eqs. (4.19)-(4.21),
-// saves one FP64 subtraction per term but measured slower on GB300: the
-// integer exponent test and branch cost more than the subtraction.)
-__device__ __forceinline__ double shifted_t(double dj, double dK, double y)
-{
-    return (dj - dK) - y;
-}
-
-template <bool DERIV>
-__device__ __forceinline__ void sweep(const double *__restrict__ sd, const double *__restrict__ sw,
-                                      int j0, int j1, int jg0, int k, int kwlo, int kwhi,
-                                      double dK, double y, Acc &A)
-{
-    // region A: global j <= kwlo -> psi for every lane
-    int ea = min(j1, max(j0, kwlo - jg0 + 1));
-#pragma unroll 4
-    for (int j = j0; j < ea; j++) {
-        double t = shifted_t(sd[j], dK, y);
-        double r = rcp_nr1(t);
-        if (DERIV) {
-            double a = sw[j] * r;
-            A.psi += a;
-            A.dpsi = fma(a, r, A.dpsi);
-        } else {
-            A.psi = fma(sw[j], r, A.psi);
-        }
-    }
-    // region B: kwlo < j <= kwhi -> per lane
-    int eb = min(j1, max(ea, kwhi - jg0 + 1));
-    for (int j = ea; j < eb; j++) {
-        double t = shifted_t(sd[j], dK, y);
-        double r = rcp_nr1(t);
-        double a = sw[j] * r;
-        if (jg0 + j <= k) { A.psi += a; if (DERIV) A.dpsi = fma(a, r, A.dpsi); }
-        else              { A.phi += a; if (DERIV) A.dphi = fma(a, r, A.dphi); }
-    }
-    // region C: j > kwhi -> phi for every lane
-#pragma unroll 4
-    for (int j = eb; j < j1; j++) {
-        double t = shifted_t(sd[j], dK, y);
-        double r = rcp_nr1(t);
-        if (DERIV) {
-            double a = sw[j] * r;
-            A.phi += a;
-            A.dphi = fma(a, r, A.dphi);
-        } else {
-            A.phi = fma(sw[j], r, A.phi);
-        }
-    }
-}
-
-struct Root {
-    int k, m, K, phase, nsw;
-    bool last;
-    double dK, y, lo, hi;
-    double d0, d1, w0, w1, W;   // d_k, d_{k+1}, w_k, w_{k+1}, sum w
-
-    __device__ void init(const double *__restrict__ dk, const double *__restrict__ zk, int k_, int m_, double W_)
-    {
-        k = k_; m = m_; W = W_;
-        last = (k == m - 1);
-        d0 = dk[k];
-        double z0 = zk[k];
-        w0 = z0 * z0;
-        if (!last) { d1 = dk[k + 1]; double z1 = zk[k + 1]; w1 = z1 * z1; }
-        else       { d1 = d0; w1 = 0.0; }
-        phase = 0; nsw = 0;
-        K = k; dK = d0;
-        y = last ? 0.5 * W : 0.5 * (d1 - d0);     // midpoint sweep
-        lo = hi = 0.0;
-    }
-
-    // returns true when the root is final
-    __device__ bool update(const Acc &A, double tol, int max_iter, int32_t *status)
-    {
-        nsw++;
-        double f = 1.0 + A.psi + A.phi;
-        if (!isfinite(f)) { sdc_latch(status, SUPERDC_DEV_NONFINITE); return true; }
-        if (phase == 0) {
-            // origin choice (Section 4.2.1) and initial guess: freeze the
-            // non-adjacent terms at the midpoint, solve the two-pole model
-            if (!last) {
-                double D = d1 - d0, h = 0.5 * D;
-                double rest = f + w0 / h - w1 / (D - h);
-                if (f >= 0.0) { K = k;     lo = 0.0; hi = h;   dK = d0; }
-                else          { K = k + 1; lo = -h;  hi = 0.0; dK = d1; }
-                double a = d0 - dK, b = d1 - dK;
-                y = quad_in(rest, -(rest * (a + b) + w0 + w1), w0 * b + w1 * a, lo, hi);
-            } else {
-                double ym = 0.5 * W;
-                if (f >= 0.0) { lo = 0.0; hi = ym; } else { lo = ym; hi = W; }
-                double rest = f + w0 / ym;
-                y = (rest > 0.0) ? w0 / rest : 0.5 * (lo + hi);
-                if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
-            }
-            phase = 1;
-            return false;
-        }
-        if (fabs(f) < tol * (1.0 + fabs(A.psi) + fabs(A.phi))) return true;   // eq. (4.12)
-        if (f < 0.0) lo = y; else hi = y;
-        double ynew;
-        if (!last) {
-            // middle-way step: psi ~ a1 + b1/(d_k - x), phi ~ a2 + b2/(d_{k+1} - x)
-            double Dk = (d0 - dK) - y, Dk1 = (d1 - dK) - y;
-            double c = f - Dk * A.dpsi - Dk1 * A.dphi;
-            double Aq = (Dk + Dk1) * f - Dk * Dk1 * (A.dpsi + A.dphi);
-            double Bq = Dk * Dk1 * f;
-            double corr;
-            if (c == 0.0) {
-                corr = (Aq != 0.0) ? Bq / Aq : 0.0;
-            } else {
-                double disc = Aq * Aq - 4.0 * Bq * c;
-                if (disc < 0.0) disc = 0.0;
-                double s = sqrt(disc);
-                double den = Aq + (Aq >= 0 ? s : -s);
-                corr = (den != 0.0) ? 2.0 * Bq / den : 0.0;
-            }
-            ynew = y + corr;
-        } else {
-            double Dl = (d0 - dK) - y;
-            double den = f - Dl * A.dpsi;
-            double corr = (den != 0.0) ? Dl + Dl * Dl * A.dpsi / den : 0.0;
-            ynew = y + corr;
-        }
-        if (!(ynew > lo && ynew < hi)) ynew = lo + 0.5 * (hi - lo);
-        if (ynew == y || !(ynew > lo && ynew < hi)) return true;   // bracket at double resolution
-        y = ynew;
-        if (nsw - 1 >= max_iter) { sdc_latch(status, SUPERDC_DEV_NOCONV); return true; }
-        return false;
-    }
-};
 
 // Work units of the secular kernel: (problem, first root, end root), at most
 // ubig roots each.  A unit stages its problem's poles in shared memory (all of
@@ -568,8 +357,9 @@ struct Root {
 constexpr int SEC_UNIT_BIG = 2048;
 constexpr int SORT_MAX = 8192;
 
-__global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int ubig, int whole_small,
-                        int4 *__restrict__ units, int *__restrict__ nunits, int *__restrict__ counter)
+__global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, const int32_t *__restrict__ fslot, int ubig,
+                        int whole_small, int4 *__restrict__ units, int *__restrict__ nunits,
+                        int *__restrict__ counter)
 {
     extern __shared__ unsigned long long keys[];   // SORT_MAX entries when sorting
     __shared__ int part[1024];
@@ -580,7 +370,8 @@ __global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int ubig,
         while (n2 < nprob) n2 <<= 1;
         for (int64_t i = threadIdx.x; i < n2; i += T) {
             // descending by size: key = (size << 32) | (~p) so that equal sizes keep index order
-            keys[i] = (i < nprob) ? (((unsigned long long)(unsigned)mk[i] << 32) |
+            const int mi = (i < nprob && !(fslot && fslot[i] >= 0)) ? mk[i] : 0;
+            keys[i] = (i < nprob) ? (((unsigned long long)(unsigned)mi << 32) |
                                      (unsigned long long)(0xFFFFFFFFu - (unsigned)i))
                                   : 0ull;
         }
@@ -605,7 +396,7 @@ __global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int ubig,
     int cnt = 0;
     for (int64_t q = beg; q < end; q++) {
         int64_t pp = sorted ? (int64_t)(0xFFFFFFFFu - (unsigned)(keys[q] & 0xFFFFFFFFull)) : q;
-        int m = mk[pp];
+        int m = (fslot && fslot[pp] >= 0) ? 0 : mk[pp];   // FMM problems: not here
         cnt += (m + ubig - 1) / ubig;
     }
     part[threadIdx.x] = cnt;
@@ -620,7 +411,7 @@ __global__ void k_units(int64_t nprob, const int32_t *__restrict__ mk, int ubig,
     int u = part[threadIdx.x];
     for (int64_t q = beg; q < end; q++) {
         int64_t pp = sorted ? (int64_t)(0xFFFFFFFFu - (unsigned)(keys[q] & 0xFFFFFFFFull)) : q;
-        int m = mk[pp];
+        int m = (fslot && fslot[pp] >= 0) ? 0 : mk[pp];
         if (m <= 0) continue;
         for (int r = 0; r < m; r += ubig) units[u++] = make_int4((int)pp, r, min(m, r + ubig), 0);
     }
@@ -756,11 +547,13 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
 // ---------------------------------------------------------------------------
 template <int TR>
 __global__ void __launch_bounds__(TR)
-k_lowner(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restrict__ tile_off, R1Out o)
+k_lowner(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restrict__ tile_off, R1Out o,
+         const int32_t *__restrict__ fslot)
 {
     const int64_t ntiles = tile_off[nprob];
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t p = sdc_upper_index(tile_off, nprob, tile);
+        if (fslot && fslot[p] >= 0) continue;   // FMM problem
         const int64_t b0 = off[p];
         const int m = o.mk[p];
         const int i = (int)(tile - tile_off[p]) * TR + threadIdx.x;
@@ -803,11 +596,13 @@ k_lowner(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restri
 // ---------------------------------------------------------------------------
 template <int TR>
 __global__ void __launch_bounds__(TR)
-k_bnorm(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restrict__ tile_off, R1Out o)
+k_bnorm(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restrict__ tile_off, R1Out o,
+         const int32_t *__restrict__ fslot)
 {
     const int64_t ntiles = tile_off[nprob];
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t p = sdc_upper_index(tile_off, nprob, tile);
+        if (fslot && fslot[p] >= 0) continue;   // FMM problem
         const int64_t b0 = off[p];
         const int m = o.mk[p];
         const int j = (int)(tile - tile_off[p]) * TR + threadIdx.x;
@@ -908,6 +703,15 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     if (a.total > DEFL_BIG)
         PROF_LAUNCH("deflate", st, k_deflate_big<<<(unsigned)a.nprob, DB_T, 0, st>>>(
             a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau, wd, wz, kept, surv, a.o));
+    // problems whose kept size reaches the threshold take the triangular FMM
+    // path; the direct kernels below skip them
+    FmmPlan fp;
+    {
+        superdc_status fs = fmm_plan(fp, a.nprob, a.off, a.total, a.max_m, a.o.mk, a.o.dk, a.fmm_min_m, 1, 4,
+                                     a.o.fmm_used, st);
+        if (fs != SUPERDC_OK) { fmm_free(fp, st); return fs; }
+    }
+    const int32_t *fslot = fp.on ? fp.dv.fslot : nullptr;
     const int TR = 128;
     PROF_LAUNCH("tiles", st, k_tiles<<<1, 1024, 0, st>>>(a.nprob, a.o.mk, TR, tile_off));
     const unsigned grid = (unsigned)(nsm * 8);
@@ -922,16 +726,19 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     int ubig = SEC_UNIT_BIG / 2;
     if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
     if (a.tile_roots >= 32 && a.tile_roots <= 4096) ubig = (a.tile_roots / 32) * 32;
-    PROF_LAUNCH("units", st, k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, ubig, split ? 0 : 1, units, ucount,
-                                                           ucount + 1));
+    PROF_LAUNCH("units", st, k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, fslot, ubig, split ? 0 : 1, units,
+                                                           ucount, ucount + 1));
     if (split)
         PROF_LAUNCH("secular", st, (k_secular<4, true><<<(unsigned)slots, 128, 0, st>>>(
                                        a.off, units, ucount, ucount + 1, a.o, a.stop_c, a.max_iter)));
     else
         PROF_LAUNCH("secular", st, (k_secular<4, false><<<(unsigned)slots, 128, 0, st>>>(
                                        a.off, units, ucount, ucount + 1, a.o, a.stop_c, a.max_iter)));
-    PROF_LAUNCH("lowner", st, k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o));
-    PROF_LAUNCH("bnorm", st, k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o));
+    superdc_status fs = fmm_secular(fp, a.off, a.o, a.stop_c, a.max_iter, st);
+    PROF_LAUNCH("lowner", st, k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, fslot));
+    if (fs == SUPERDC_OK) fs = fmm_lowner(fp, a.off, a.o, st);
+    PROF_LAUNCH("bnorm", st, k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, fslot));
+    if (fs == SUPERDC_OK) fs = fmm_bnorm(fp, a.off, a.o, st);
     PROF_LAUNCH("merge", st, k_merge<<<(unsigned)(nsm * 8), 256, 0, st>>>(a.nprob, a.off, a.total, a.o));
     SDC_CHECK(cudaGetLastError());
 
@@ -943,7 +750,8 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     SDC_CHECK(cudaFreeAsync(surv, st));
     SDC_CHECK(cudaFreeAsync(a.o.lamk, st));
     SDC_CHECK(cudaFreeAsync(ucount, st));
-    return SUPERDC_OK;
+    fmm_free(fp, st);
+    return fs;
 }
 
 // ---------------------------------------------------------------------------
@@ -1040,6 +848,7 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     a.o.wsum = (double *)(base + NA_WSUM);
     a.o.pinv = (int32_t *)(base + NA_PINV);
     a.o.lamk = (double *)(base + NA_LAMK);
+    if (out->fmm) SDC_CHECK(cudaMemsetAsync(out->fmm, 0, (size_t)nprob * sizeof(int32_t), st));   // direct only
     double *wd = (double *)(base + NA_WD), *wz = (double *)(base + NA_WZ);
     int8_t *kept = (int8_t *)(base + NA_KEPT);
     int64_t *tile_off = (int64_t *)(base + NA_TILE);
@@ -1064,15 +873,15 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     const bool split = per < 512;
     int ubig = SEC_UNIT_BIG / 2;
     if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
-    k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, ubig, split ? 0 : 1, units, ucount, ucount + 1);
+    k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, nullptr, ubig, split ? 0 : 1, units, ucount, ucount + 1);
     if (split)
         k_secular<4, true><<<(unsigned)slots, 128, 0, st>>>(a.off, units, ucount, ucount + 1, a.o, a.stop_c,
                                                              a.max_iter);
     else
         k_secular<4, false><<<(unsigned)slots, 128, 0, st>>>(a.off, units, ucount, ucount + 1, a.o, a.stop_c,
                                                               a.max_iter);
-    k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o);
-    k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o);
+    k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, nullptr);
+    k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, nullptr);
     k_merge<<<(unsigned)(nsm * 8), 256, 0, st>>>(a.nprob, a.off, a.total, a.o);
     SDC_CHECK(cudaGetLastError());
     return SUPERDC_OK;

@@ -13,6 +13,7 @@ struct R1Out {
     int32_t *pinv;  // merged position of every slot (inverse of perm), total entries
     double *wsum;   // sum of kept z^2 per problem (scratch), nprob entries
     double *lamk;   // d_K + eta of every kept root, slot order (scratch), total entries
+    int32_t *fmm_used = nullptr;   // per problem: 1 if it took the FMM path (may be NULL)
 };
 
 struct R1Args {
@@ -23,6 +24,8 @@ struct R1Args {
     double sqrt_rho, tau, stop_c;
     int max_iter, tile_roots;
     int sched = 0;          // 0 automatic, 1 whole problems per CTA (root pools per warp), 2 pole split
+    int fmm_min_m = 0;      // kept size from which a problem takes the FMM path (0: direct only)
+    int64_t max_m = -1;     // upper bound on the problem sizes (-1: unknown)
     R1Out o;
 };
 
