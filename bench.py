@@ -37,6 +37,8 @@ WORKLOAD = ("batched secular solve: 4096 independent rank-one problems, m~U{32..
             "deflation + shifted roots + Loewner zhat + b + sorted eigenvalues")
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 (no measured figure in the peaks file)
 SECULAR_FLOPS_PER_INTERACTION = 7.0   # 2 sub, 1 recip, 1 mul, 1 add, 1 fma (2)
+FMM_P = 24                              # Chebyshev order of the FMM expansions
+FMM_FAR_FLOPS = 4 * (FMM_P - 1) * 3     # per root and sweep: four Clenshaw sums (fma + sub per step)
 
 
 def _profiled(name, src):
@@ -260,7 +262,9 @@ def main():
     sdc.check_status(out["status"], "timed")
     kern = {}
     import ctypes
-    for name in ("deflate", "tiles", "units", "secular", "lowner", "bnorm", "merge"):
+    for name in ("deflate", "tiles", "units", "secular", "lowner", "bnorm", "merge", "fmm_plan", "fmm_tree",
+                 "fmm_mom", "fmm_m2m", "fmm_m2l", "fmm_l2l", "fmm_secular", "fmm_secular_last", "fmm_lowner",
+                 "fmm_bnorm"):
         n_ = ctypes.c_int64(0)
         t_ = ctypes.c_double(0.0)
         lib.superdc_profile_read(name.encode(), ctypes.byref(n_), ctypes.byref(t_))
@@ -312,15 +316,39 @@ def main():
     unb_roots = int(batch.offsets[nsample])
     unbatched_rps = unb_roots / (e0.elapsed_time(e1) * 1e-3)
 
-    # algorithmic work of the secular kernel (from the run's own sweep counts)
+    # algorithmic work of the secular kernels, from the run's own counts: the
+    # direct kernel evaluates every (root, pole) pair of a sweep, the FMM
+    # kernels the near-field pairs (counted on the device) plus four Clenshaw
+    # sums per root and sweep
     mk = out["mk"].cpu().numpy().astype(np.float64)
     sw = out["sweeps"].cpu().numpy().astype(np.float64)
+    fm = out["fmm"].cpu().numpy()[:batch.nprob] != 0
     per_prob_sweeps = np.add.reduceat(sw, batch.offsets[:-1]) if total else np.zeros(0)
-    interactions = float(np.sum(mk * per_prob_sweeps))
-    sec_ms = kern["secular"][1] / max(1, kern["secular"][0])
-    achieved = SECULAR_FLOPS_PER_INTERACTION * interactions / (sec_ms * 1e-3) / 1e12
+    interactions = float(np.sum((mk * per_prob_sweeps)[~fm]))
+    last_sweeps = np.array([sw[int(batch.offsets[p]) + int(mk[p]) - 1] if fm[p] else 0.0
+                            for p in range(batch.nprob)])
+    fmm_root_sweeps = float(np.sum(per_prob_sweeps[fm]) - last_sweeps.sum())   # tree roots only
+    terms = ctypes.c_int64(0)
+    lib.superdc_profile_counter(b"fmm_secular_terms", ctypes.byref(terms))
+    fmm_terms = float(terms.value) / max(1, args.steps)
     peak, peak_src = _fp64_peak()
-    prof = _profiled("k_secular_batched4096_dram.md", "paper_2108_04209_gb300/csrc/rank1.cu")
+    sec_ms = kern["secular"][1] / max(1, kern["secular"][0])
+    fsec_ms = kern["fmm_secular"][1] / max(1, args.steps)
+    rl = {}
+    if interactions > 0:
+        a_ = SECULAR_FLOPS_PER_INTERACTION * interactions / (sec_ms * 1e-3) / 1e12
+        rl["k_secular"] = {"achieved": a_, "ms": sec_ms, "flops": SECULAR_FLOPS_PER_INTERACTION * interactions,
+                           "algorithmic": "%.0f flops/interaction x %.4g (root, pole) interactions per launch" % (
+                               SECULAR_FLOPS_PER_INTERACTION, interactions)}
+    if fmm_root_sweeps > 0 and fsec_ms > 0:
+        fl = SECULAR_FLOPS_PER_INTERACTION * fmm_terms + FMM_FAR_FLOPS * fmm_root_sweeps
+        rl["fmm_secular"] = {"achieved": fl / (fsec_ms * 1e-3) / 1e12, "ms": fsec_ms, "flops": fl,
+                             "algorithmic": "%.0f flops x %.4g near-field terms + %d flops x %.4g root sweeps" % (
+                                 SECULAR_FLOPS_PER_INTERACTION, fmm_terms, FMM_FAR_FLOPS, fmm_root_sweeps)}
+    dom = max(rl, key=lambda k: rl[k]["ms"]) if rl else "k_secular"
+    prof = _profiled("k_secular_batched4096_dram.md", "paper_2108_04209_gb300/csrc/rank1.cu") \
+        if dom == "k_secular" else _profiled("fmm_secular_batched4096_dram.md", "paper_2108_04209_gb300/csrc/fmm.cu")
+    achieved = rl[dom]["achieved"] if rl else 0.0
 
     # e2e: host buffers, copies inside the timed region
     h_off = torch.from_numpy(batch.offsets).pin_memory()
@@ -359,13 +387,17 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "gpu_launches": int(launches),
             "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kern.items()},
-            "roofline": {"bound": "alu", "kernel": "k_secular", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "dtype": "fp64", "frac": achieved / peak,
                          "traffic": (prof or {}).get("traffic_bytes"),
                          "fp64_pipe_pct_ncu": (prof or {}).get("fp64_pipe_pct"),
                          "peak_source": peak_src,
-                         "algorithmic": "%.0f flops/interaction x %.4g interactions per launch" % (
-                             SECULAR_FLOPS_PER_INTERACTION, interactions)},
+                         "algorithmic": rl.get(dom, {}).get("algorithmic"),
+                         "other": {k: {"achieved": v["achieved"], "frac": v["achieved"] / peak, "ms": v["ms"]}
+                                   for k, v in rl.items() if k != dom}},
+            "fmm": {"threshold": "opts.fmm_min_m=%d (0 = library default)" % opts.fmm_min_m,
+                    "problems": int(fm.sum()), "roots": int(mk[fm].sum()),
+                    "direct_problems": int((~fm).sum()), "direct_roots": int(mk[~fm].sum())},
             "secular_sweeps_mean": float(sw[sw > 0].mean()) if np.any(sw > 0) else 0.0,
             "schedule": {"autotuned": "sched=%d tile_roots=%d" % (opts.sched, opts.tile_roots),
                          "candidates_ms": tune_ms},

@@ -312,6 +312,11 @@ superdc_status superdc_eigfact_shape(const superdc_eigfact *f, int32_t *lmax, in
 superdc_status superdc_profile_enable(int32_t on);
 superdc_status superdc_profile_reset(void);
 superdc_status superdc_profile_read(const char *name, int64_t *launches, double *ms);
+/* Work counters recorded while profiling (synchronous read; zeroed by
+ * superdc_profile_reset): "fmm_secular_terms" = pole terms summed directly by
+ * the FMM secular kernel (near fields), "fmm_secular_last_terms" = terms of
+ * the last roots (summed over every pole), both over all sweeps. */
+superdc_status superdc_profile_counter(const char *name, int64_t *value);
 
 #ifdef __cplusplus
 }

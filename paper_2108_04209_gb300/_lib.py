@@ -98,6 +98,8 @@ def lib():
         L.superdc_profile_reset.restype = c_int32
         L.superdc_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(c_int64), ctypes.POINTER(c_double)]
         L.superdc_profile_read.restype = c_int32
+        L.superdc_profile_counter.argtypes = [ctypes.c_char_p, ctypes.POINTER(c_int64)]
+        L.superdc_profile_counter.restype = c_int32
         _lib = L
     return _lib
 

@@ -10,21 +10,22 @@
 // two boxes interact through expansions is decided geometrically: boxes S, T
 // of one level are admissible when their gap is at least FMM_KAPPA times the
 // larger width.  Near lists are built top-down (children of the parent's near
-// list that are not admissible).  A box whose list would exceed FMM_NCAP (a
-// box straddling a wide gap of the spectrum is close to everything) is marked
-// "all near", and so is its subtree: the targets of such leaves are summed
-// directly over every source, the other leaves keep the expansions.  Only the last eigenvalue
+// list that are not admissible) and have any length (a wide box, e.g. in a
+// tail of the spectrum, is close to many boxes; its narrow children are not).
+// Only when the list pool is exhausted is a box marked "all near", with its
+// subtree: the targets of such leaves are summed directly over every source.  Only the last eigenvalue
 // lambda_{m-1} lies outside the tree (to the right of d_{m-1}): as a target it
 // is summed directly, as a source it is added directly to every target.
 //
 // Expansions.  Chebyshev interpolation with FMM_P first-kind nodes per box:
-// source moments M_n = sum_j w_j T_n(u_j) of the leaf boxes, translated
-// exactly to the parents (T_n(alpha u + beta) expands in T_0..T_n), node
-// weights W_q = sum_j w_j L_q(u_j) from the moments; every leaf box receives
-// the kernel sums of all boxes admissible to it or to one of its ancestors
-// (while the ancestor's parent was not) at its own Chebyshev nodes, converted
-// to Chebyshev coefficients and evaluated at the targets by Clenshaw.  Work is
-// O(m P^2 log m / FMM_B) for the far field plus O(m FMM_B) for the near field.
+// source moments M_n = sum_j w_j T_n(u_j) of the leaf boxes, node weights
+// W_q = sum_j w_j L_q(u_j) from the moments, parents' moments exactly from
+// the children's weights (T_n(alpha u + beta) has degree n < P; upward pass); every box
+// receives the kernel sums of its interaction list (children of its parent's
+// near list that are admissible to it) at its own Chebyshev nodes (M2L), the
+// parents' fields are interpolated down the tree (L2L), and on the leaves the
+// field becomes Chebyshev coefficients evaluated at the targets by Clenshaw.
+// Work is O(m P^2 / FMM_B) for the far field plus O(m FMM_B) for the near field.
 //
 // Triangularity.  A far box lies entirely to the left or right of the target
 // box in index order, so its sums go to the lower (psi, C_L w, S_L w) or the
@@ -51,6 +52,7 @@ namespace {
 constexpr int P = FMM_P;
 constexpr int B = FMM_B;
 constexpr double FMM_KAPPA = 1.0;
+constexpr int SPLIT_NEAR = 8;     // leaf boxes with this many near boxes or more: CTA-split secular sweeps
 constexpr int WMAX = 32;          // widest moment / coefficient block (columns)
 
 // ---------------------------------------------------------------------------
@@ -102,19 +104,28 @@ __device__ __forceinline__ bool adm(double loS, double hiS, double loT, double h
 
 // near list of a leaf box: nn >= 0 entries, or (nn < 0) every leaf box
 __device__ __forceinline__ int near_len(int nn, int nb0) { return nn < 0 ? nb0 : nn; }
-__device__ __forceinline__ int near_box(const int32_t *__restrict__ near, int64_t g, int nn, int i)
+__device__ __forceinline__ int near_box(const FmmDev &pl, int64_t g, int nn, int i)
 {
-    return nn < 0 ? i : near[g * FMM_NCAP + i];
+    return nn < 0 ? i : pl.near[pl.nstart[g] + i];
 }
 
-// Chebyshev nodes x_q = cos((2q+1) pi / 2P) and T_n(x_q) (Tx[q * P + n])
-__device__ void cheb_tables(double *xq, double *Tx)
+// Chebyshev nodes x_q = cos((2q+1) pi / 2P) and T_n(x_q) (Tx[q * P + n], by
+// the three-term recurrence, one row per thread); the caller synchronises
+// before the first use
+__device__ __forceinline__ void cheb_tables(double *xq, double *Tx)
 {
-    for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
-        const int q = t / P, n = t % P;
-        Tx[t] = cospi((double)(n * (2 * q + 1)) / (2.0 * P));
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+        const double x = cospi((double)(2 * q + 1) / (2.0 * P));
+        xq[q] = x;
+        double t0 = 1.0, t1 = x;
+        Tx[q * P] = 1.0;
+        Tx[q * P + 1] = x;
+        for (int n = 2; n < P; n++) {
+            const double t2 = 2.0 * x * t1 - t0;
+            Tx[q * P + n] = t2;
+            t0 = t1; t1 = t2;
+        }
     }
-    for (int q = threadIdx.x; q < P; q += blockDim.x) xq[q] = cospi((double)(2 * q + 1) / (2.0 * P));
 }
 
 // Clenshaw evaluation of sum_n a_n T_n(u)
@@ -194,55 +205,108 @@ __global__ void k_fmm_plan(int64_t nprob, const int32_t *__restrict__ mk, int mi
     }
 }
 
-// Box intervals and near lists, one CTA per problem, top level first.
+// Box intervals and near lists, one CTA per problem, top level first.  Near
+// lists have any length; they are stored back to back in the problem's share
+// of the pool (FMM_NPOOL entries per box on average).  A box whose list no
+// longer fits, and its subtree, is marked "all near" (nnear = -1).
+__device__ __forceinline__ int near_count(const double *__restrict__ blo, const double *__restrict__ bhi,
+                                          const int32_t *__restrict__ near, int64_t gb, int nb, int b,
+                                          int64_t pst, int npn)
+{
+    const double loT = blo[gb + b], hiT = bhi[gb + b];
+    int cnt = 0;
+    for (int i = 0; i < npn; i++) {
+        const int s = near[pst + i];
+        for (int S = 2 * s; S <= 2 * s + 1 && S < nb; S++)
+            if (S == b || !adm(blo[gb + S], bhi[gb + S], loT, hiT)) cnt++;
+    }
+    return cnt;
+}
+
 __global__ void __launch_bounds__(256)
 k_fmm_tree(int64_t nprob, const int64_t *__restrict__ off, const int32_t *__restrict__ mk,
            const double *__restrict__ dk, const int64_t *__restrict__ box_base, int32_t *__restrict__ fslot,
            double *__restrict__ blo, double *__restrict__ bhi, int32_t *__restrict__ nnear,
-           int32_t *__restrict__ near, int32_t *__restrict__ used)
+           int64_t *__restrict__ nstart, int32_t *__restrict__ near, int32_t *__restrict__ used)
 {
+    __shared__ int64_t part[256];
+    __shared__ int64_t s_pos;
+    const int T = blockDim.x;
     for (int64_t p = blockIdx.x; p < nprob; p += gridDim.x) {
         if (fslot[p] < 0) continue;
         const int m = mk[p];
         const double *d = dk + off[p];
         const int64_t g0 = box_base[p];
+        const int64_t pool_end = box_base[p + 1] * FMM_NPOOL;
         const int nb0 = (m + B - 1) / B;
         const int L = lev_count(nb0);
+        if (threadIdx.x == 0) s_pos = g0 * FMM_NPOOL;
+        __syncthreads();
         for (int l = L - 1; l >= 0; l--) {
             const int nb = lev_nb(nb0, l);
             const int64_t gb = g0 + lev_base(nb0, l);
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const int64_t gp0 = (l < L - 1) ? g0 + lev_base(nb0, l + 1) : 0;
+            for (int b = threadIdx.x; b < nb; b += T) {
                 int i0, i1;
                 box_range(m, l, b, i0, i1);
                 blo[gb + b] = d[i0];
                 bhi[gb + b] = (i1 < m) ? d[i1] : d[m - 1];
             }
             __syncthreads();
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-                int cnt = 0;
+            // each thread a contiguous range of boxes: count, block prefix, fill
+            const int per = (nb + T - 1) / T;
+            const int bb = min(nb, (int)threadIdx.x * per), be = min(nb, bb + per);
+            int64_t sum = 0;
+            for (int b = bb; b < be; b++) {
+                if (l == L - 1) { sum += 1; continue; }
+                const int64_t gp = gp0 + (b >> 1);
+                const int npn = nnear[gp];
+                if (npn >= 0) sum += near_count(blo, bhi, near, gb, nb, b, nstart[gp], npn);
+            }
+            part[threadIdx.x] = sum;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int64_t acc = 0;
+                for (int i = 0; i < T; i++) { const int64_t v = part[i]; part[i] = acc; acc += v; }
+            }
+            __syncthreads();
+            int64_t pos = s_pos + part[threadIdx.x];
+            for (int b = bb; b < be; b++) {
+                int cnt;
                 if (l == L - 1) {
-                    near[(gb + b) * FMM_NCAP] = b;
                     cnt = 1;
+                    if (pos + 1 <= pool_end) near[pos] = b; else cnt = -1;
+                    nstart[gb + b] = pos;
+                    pos += 1;
                 } else {
-                    const int64_t gp = g0 + lev_base(nb0, l + 1) + (b >> 1);
+                    const int64_t gp = gp0 + (b >> 1);
                     const int npn = nnear[gp];
                     if (npn < 0) {
-                        cnt = -1;                                  // parent: all near
+                        cnt = -1;                                           // parent all near
+                        nstart[gb + b] = pos;
                     } else {
-                        const double loT = blo[gb + b], hiT = bhi[gb + b];
-                        for (int i = 0; i < npn && cnt >= 0; i++) {
-                            const int s = near[gp * FMM_NCAP + i];
-                            for (int S = 2 * s; S <= 2 * s + 1 && S < nb; S++) {
-                                if (S != b && adm(blo[gb + S], bhi[gb + S], loT, hiT)) continue;
-                                if (cnt == FMM_NCAP) { cnt = -1; break; }   // overflow: all near
-                                near[(gb + b) * FMM_NCAP + cnt] = S;
-                                cnt++;
+                        const int64_t pst = nstart[gp];
+                        const int c = near_count(blo, bhi, near, gb, nb, b, pst, npn);
+                        nstart[gb + b] = pos;
+                        if (pos + c <= pool_end) {
+                            const double loT = blo[gb + b], hiT = bhi[gb + b];
+                            int w = 0;
+                            for (int i = 0; i < npn; i++) {
+                                const int s2 = near[pst + i];
+                                for (int S = 2 * s2; S <= 2 * s2 + 1 && S < nb; S++)
+                                    if (S == b || !adm(blo[gb + S], bhi[gb + S], loT, hiT)) near[pos + w++] = S;
                             }
+                            cnt = c;
+                        } else {
+                            cnt = -1;                                       // pool exhausted: all near
                         }
+                        pos += c;
                     }
                 }
                 nnear[gb + b] = cnt;
             }
+            __syncthreads();
+            if (threadIdx.x == T - 1) s_pos = pos;
             __syncthreads();
         }
         if (threadIdx.x == 0 && used) used[p] = 1;
@@ -360,68 +424,111 @@ __global__ void __launch_bounds__(B) k_fmm_leafmom(FmmDev pl, SrcArgs a)
     }
 }
 
-// moments of the boxes of level l from their children (exact translation)
+// Boxes of level l of the FMM problems, enumerated as (FMM problem f, box b)
+// with b below the widest level-l box count nbl_max (host bound); returns
+// false for slots without a box.
+// Box u of level l over all FMM problems (per-level prefix lev_off[l][f]).
+__device__ __forceinline__ bool level_box(const FmmDev &pl, const int32_t *__restrict__ mk, int l, int64_t u,
+                                          int64_t &p, int &nb0, int &b, int64_t &g)
+{
+    const int nf = *pl.nfmm;
+    const int64_t *lo = pl.lev_off + (int64_t)l * (pl.cap_f + 1);
+    const int64_t f = sdc_upper_index(lo, (int64_t)nf, u);
+    b = (int)(u - lo[f]);
+    p = pl.fprob[f];
+    if (pl.fslot[p] < 0) return false;
+    nb0 = (mk[p] + B - 1) / B;
+    if (l >= lev_count(nb0) || b >= lev_nb(nb0, l)) return false;
+    g = pl.box_base[p] + lev_base(nb0, l) + b;
+    return true;
+}
+
+// per-level prefix of the box counts of the FMM problems (one CTA per level)
+__global__ void k_fmm_levoff(const int32_t *__restrict__ mk, const int32_t *__restrict__ fprob,
+                             const int32_t *__restrict__ nfmm, int64_t cap_f, int64_t *__restrict__ lev_off)
+{
+    __shared__ int64_t part[1024];
+    const int l = blockIdx.x;
+    const int nf = *nfmm;
+    const int T = blockDim.x;
+    const int per = (nf + T - 1) / T;
+    const int beg = min(nf, (int)threadIdx.x * per), end = min(nf, beg + per);
+    int64_t sum = 0;
+    for (int f = beg; f < end; f++) {
+        const int nb0 = (mk[fprob[f]] + B - 1) / B;
+        if (l < lev_count(nb0)) sum += lev_nb(nb0, l);
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < T; i++) { const int64_t v = part[i]; part[i] = acc; acc += v; }
+        lev_off[(int64_t)l * (cap_f + 1) + nf] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int f = beg; f < end; f++) {
+        lev_off[(int64_t)l * (cap_f + 1) + f] = acc;
+        const int nb0 = (mk[fprob[f]] + B - 1) / B;
+        if (l < lev_count(nb0)) acc += lev_nb(nb0, l);
+    }
+}
+
+// moments of the boxes of level l from their children's node weights:
+// M_n(parent) = sum_children sum_q W_q(child) T_n(alpha x_q + beta), exact
+// because T_n(alpha u + beta) has degree n < P and the children's weights
+// reproduce every moment of degree < P
 __global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__restrict__ mk, int l, int nw)
 {
-    __shared__ double A[P][P + 1];
-    __shared__ double Mc[P][WMAX + 1];
+    __shared__ double Tv[2][P][P + 1];
+    __shared__ double Wc[2][P][WMAX + 1];
     __shared__ double Ms[P][WMAX + 1];
     __shared__ double Tx[P * P], xq[P];
     cheb_tables(xq, Tx);
     const int tid = threadIdx.x;
-    const int64_t nbox = pl.box_base[pl.nprob];
-    for (int64_t g = blockIdx.x; g < nbox; g += gridDim.x) {
-        const int64_t p = sdc_upper_index(pl.box_base, pl.nprob, g);
-        if (pl.fslot[p] < 0) continue;
-        const int m = mk[p];
-        const int nb0 = (m + B - 1) / B;
-        if (l >= lev_count(nb0)) continue;
-        const int64_t local = g - pl.box_base[p];
-        const int lb = lev_base(nb0, l), nbl = lev_nb(nb0, l);
-        if (local < lb || local >= lb + nbl) continue;
-        const int b = (int)(local - lb);
+    const int64_t nu = pl.lev_off[(int64_t)l * (pl.cap_f + 1) + *pl.nfmm];
+    for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
+        int64_t p, g;
+        int nb0, b;
+        if (!level_box(pl, mk, l, u, p, nb0, b, g)) continue;
         double cP, hP;
         box_ch(pl.blo[g], pl.bhi[g], cP, hP);
-        __syncthreads();
-        for (int t = tid; t < P * nw; t += blockDim.x) Ms[t / nw][t % nw] = 0.0;
         const int nbc = lev_nb(nb0, l - 1);
         const int64_t gcb = pl.box_base[p] + lev_base(nb0, l - 1);
-        for (int ci = 0; ci < 2; ci++) {
-            const int cb = 2 * b + ci;
-            if (cb >= nbc) break;
-            const int64_t gc = gcb + cb;
+        const int nch = (2 * b + 1 < nbc) ? 2 : 1;
+        __syncthreads();
+        for (int t = tid; t < 2 * P; t += blockDim.x) {
+            const int ci = t / P, q = t % P;
+            if (ci >= nch) continue;
+            const int64_t gc = gcb + 2 * b + ci;
             double cc, hc;
             box_ch(pl.blo[gc], pl.bhi[gc], cc, hc);
-            const double al = hc / hP, be = (cc - cP) / hP;
-            __syncthreads();
-            for (int t = tid; t < P * nw; t += blockDim.x)
-                Mc[t / nw][t % nw] = pl.M[(gc * P + t / nw) * pl.ncol + t % nw];
-            if (tid < P) {
-                A[0][tid] = (tid == 0) ? 1.0 : 0.0;
-                A[1][tid] = (tid == 0) ? be : ((tid == 1) ? al : 0.0);
-            }
-            __syncthreads();
-            // T_{n+1}(v) = 2 v T_n(v) - T_{n-1}(v), v = al u + be, in coefficient space
-            for (int n = 1; n < P - 1; n++) {
-                if (tid < P) {
-                    const int k = tid;
-                    double U;
-                    if (k == 0) U = 0.5 * A[n][1];
-                    else if (k == 1) U = A[n][0] + 0.5 * A[n][2];
-                    else U = 0.5 * (A[n][k - 1] + ((k + 1 < P) ? A[n][k + 1] : 0.0));
-                    A[n + 1][k] = 2.0 * (al * U + be * A[n][k]) - A[n - 1][k];
-                }
-                __syncthreads();
-            }
-            for (int t = tid; t < P * nw; t += blockDim.x) {
-                const int n = t / nw, q = t % nw;
-                double s = 0.0;
-                for (int k = 0; k <= n; k++) s = fma(A[n][k], Mc[k][q], s);
-                Ms[n][q] += s;
+            const double v = (cc + hc * xq[q] - cP) / hP;
+            double t0 = 1.0, t1 = v;
+            Tv[ci][q][0] = 1.0;
+            Tv[ci][q][1] = v;
+            for (int n = 2; n < P; n++) {
+                const double t2 = 2.0 * v * t1 - t0;
+                Tv[ci][q][n] = t2;
+                t0 = t1; t1 = t2;
             }
         }
+        for (int t = tid; t < 2 * P * nw; t += blockDim.x) {
+            const int ci = t / (P * nw), r = t % (P * nw);
+            if (ci >= nch) continue;
+            const int64_t gc = gcb + 2 * b + ci;
+            Wc[ci][r / nw][r % nw] = pl.W[(gc * P + r / nw) * pl.ncol + r % nw];
+        }
         __syncthreads();
-        for (int t = tid; t < P * nw; t += blockDim.x) pl.M[(g * P + t / nw) * pl.ncol + t % nw] = Ms[t / nw][t % nw];
+        for (int t = tid; t < P * nw; t += blockDim.x) {
+            const int n = t / nw, q = t % nw;
+            double s = 0.0;
+            for (int ci = 0; ci < nch; ci++)
+                for (int k = 0; k < P; k++) s = fma(Tv[ci][k][n], Wc[ci][k][q], s);
+            Ms[n][q] = s;
+            pl.M[(g * P + n) * pl.ncol + q] = s;
+        }
+        __syncthreads();
         for (int t = tid; t < P * nw; t += blockDim.x) {
             const int qn = t / nw, q = t % nw;
             double s = Ms[0][q];
@@ -431,8 +538,10 @@ __global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__res
     }
 }
 
-// far-field sums at the Chebyshev nodes of every leaf box, converted to
-// Chebyshev coefficients.  Kernels (s source, t target):
+// Multipole-to-local: for every box T below the top, the kernel sums of the
+// boxes of its interaction list (children of its parent's near list that are
+// admissible to T) at T's Chebyshev nodes.  "All near" boxes and the top box
+// get no far field.  Kernels (s source, t target):
 //   K_SEC: 1/(s-t) and 1/(s-t)^2 into four fields (psi, phi, psi', phi' by side)
 //   K_1: 1/(s-t)   K_2: 1/(s-t)^2   K_1N: 1/(t-s)   K_LOG: log|s-t|
 enum { K_SEC = 0, K_1 = 1, K_2 = 2, K_1N = 3, K_LOG = 4 };
@@ -442,47 +551,45 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
 {
     constexpr int NT = 128;
     constexpr int RMAX = (P * WMAX + NT - 1) / NT;
-    __shared__ double Tx[P * P], xq[P], tq[P];
+    __shared__ double xq[P], tq[P];
+    __shared__ double Tx[P * P];
     __shared__ double Ws[P][WMAX + 1];
     __shared__ double K1[P][P + 1];
     __shared__ double K2[(KER == K_SEC) ? P : 1][P + 1];
-    __shared__ double Fs[P][WMAX + 1];
     cheb_tables(xq, Tx);
     const int nf = (KER == K_SEC) ? 4 : nw;
     const int tid = threadIdx.x;
-    const int64_t nleaf = pl.leaf_base[pl.nprob];
-    for (int64_t gl = blockIdx.x; gl < nleaf; gl += gridDim.x) {
-        const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
+    const int64_t nbox = pl.box_base[pl.nprob];
+    for (int64_t g = blockIdx.x; g < nbox; g += gridDim.x) {
+        const int64_t p = sdc_upper_index(pl.box_base, pl.nprob, g);
         if (pl.fslot[p] < 0) continue;
         const int m = mk[p];
         const int nb0 = (m + B - 1) / B;
         const int L = lev_count(nb0);
-        const int Tb = (int)(gl - pl.leaf_base[p]);
-        const int64_t gp0 = pl.box_base[p];
-        double cT, hT;
-        box_ch(pl.blo[gp0 + Tb], pl.bhi[gp0 + Tb], cT, hT);
-        __syncthreads();
-        if (tid < P) tq[tid] = cT + hT * xq[tid];
+        int local = (int)(g - pl.box_base[p]), l = 0;
+        while (local >= lev_nb(nb0, l)) { local -= lev_nb(nb0, l); l++; }
+        const int Tb = local;
         double acc[RMAX];
 #pragma unroll
         for (int r = 0; r < RMAX; r++) acc[r] = 0.0;
-        // an all-near leaf sums every source directly: no far field
-        const int Lf = (pl.nnear[gp0 + Tb] < 0) ? 1 : L;
-        for (int l = 0; l < Lf - 1; l++) {
-            const int Ab = Tb >> l;
-            const int64_t gbl = gp0 + lev_base(nb0, l);
-            const int64_t gPA = gp0 + lev_base(nb0, l + 1) + (Ab >> 1);
-            const double loA = pl.blo[gbl + Ab], hiA = pl.bhi[gbl + Ab];
+        if (l < L - 1 && pl.nnear[g] >= 0) {
+            double cT, hT;
+            box_ch(pl.blo[g], pl.bhi[g], cT, hT);
+            __syncthreads();
+            if (tid < P) tq[tid] = cT + hT * xq[tid];
+            const int64_t gbl = pl.box_base[p] + lev_base(nb0, l);
+            const int64_t gPT = pl.box_base[p] + lev_base(nb0, l + 1) + (Tb >> 1);
+            const double loT = pl.blo[g], hiT = pl.bhi[g];
             const int nbl = lev_nb(nb0, l);
-            const int npn = pl.nnear[gPA];
+            const int npn = pl.nnear[gPT];
             for (int i = 0; i < npn; i++) {
-                const int s = pl.near[gPA * FMM_NCAP + i];
+                const int s = pl.near[pl.nstart[gPT] + i];
                 for (int S = 2 * s; S <= 2 * s + 1 && S < nbl; S++) {
-                    if (S == Ab) continue;
+                    if (S == Tb) continue;
                     const int64_t gS = gbl + S;
                     const double loS = pl.blo[gS], hiS = pl.bhi[gS];
-                    if (!adm(loS, hiS, loA, hiA)) continue;
-                    const bool left = S < Ab;
+                    if (!adm(loS, hiS, loT, hiT)) continue;
+                    const bool left = S < Tb;
                     double cS, hS;
                     box_ch(loS, hiS, cS, hS);
                     __syncthreads();
@@ -493,7 +600,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                         if (KER == K_LOG) {
                             K1[q][q2] = log(fabs(diff));
                         } else {
-                            const double r = 1.0 / diff;
+                            const double r = rcp_nr2(diff);
                             if (KER == K_SEC) { K1[q][q2] = r; K2[q][q2] = r * r; }
                             else if (KER == K_1) K1[q][q2] = r;
                             else if (KER == K_1N) K1[q][q2] = -r;
@@ -521,92 +628,110 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                 }
             }
         }
-        __syncthreads();
 #pragma unroll
         for (int r = 0; r < RMAX; r++) {
             const int t = tid + r * NT;
-            if (t < P * nf) Fs[t / nf][t % nf] = acc[r];
+            if (t < P * nf) pl.F[(g * P + t / nf) * pl.nfield + t % nf] = acc[r];
+        }
+    }
+}
+
+// Local-to-local for the boxes of level l: add the parent's far field,
+// interpolated at the box's Chebyshev nodes (Chebyshev coefficients of the
+// parent's node values, evaluated at alpha x_q + beta).  On the leaf level
+// the field is converted to Chebyshev coefficients for the targets.
+__global__ void __launch_bounds__(128) k_fmm_l2l(FmmDev pl, const int32_t *__restrict__ mk, int l, int nf)
+{
+    __shared__ double xq[P];
+    __shared__ double Tx[P * P];
+    __shared__ double Fs[P][WMAX + 1];
+    __shared__ double Ac[P][WMAX + 1];
+    __shared__ double Tv[P][P + 1];
+    cheb_tables(xq, Tx);
+    const int tid = threadIdx.x;
+    const int64_t nu = pl.lev_off[(int64_t)l * (pl.cap_f + 1) + *pl.nfmm];
+    for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
+        int64_t p, g;
+        int nb0, b;
+        if (!level_box(pl, mk, l, u, p, nb0, b, g)) continue;
+        const int L = lev_count(nb0);
+        if (l >= L - 1) continue;                      // the top box has no far field
+        const bool alln = pl.nnear[g] < 0;
+        const int64_t gP = pl.box_base[p] + lev_base(nb0, l + 1) + (b >> 1);
+        __syncthreads();
+        if (!alln) {
+            // parent's Chebyshev coefficients
+            for (int t = tid; t < P * nf; t += blockDim.x) Fs[t / nf][t % nf] = pl.F[(gP * P + t / nf) * pl.nfield + t % nf];
+            double cP, hP, cT, hT;
+            box_ch(pl.blo[gP], pl.bhi[gP], cP, hP);
+            box_ch(pl.blo[g], pl.bhi[g], cT, hT);
+            if (tid < P) {
+                const double v = (cT + hT * xq[tid] - cP) / hP;
+                double t0 = 1.0, t1 = v;
+                Tv[tid][0] = 1.0;
+                Tv[tid][1] = v;
+                for (int n = 2; n < P; n++) {
+                    const double t2 = 2.0 * v * t1 - t0;
+                    Tv[tid][n] = t2;
+                    t0 = t1; t1 = t2;
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < P * nf; t += blockDim.x) {
+                const int n = t / nf, f = t % nf;
+                double s = 0.0;
+                for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
+                Ac[n][f] = s * ((n == 0) ? 1.0 : 2.0) / P;
+            }
+            __syncthreads();
+            for (int t = tid; t < P * nf; t += blockDim.x) {
+                const int q = t / nf, f = t % nf;
+                double s = pl.F[(g * P + q) * pl.nfield + f];
+                for (int n = 0; n < P; n++) s = fma(Tv[q][n], Ac[n][f], s);
+                Fs[q][f] = s;     // own row (q, f) only
+            }
+        } else {
+            for (int t = tid; t < P * nf; t += blockDim.x) Fs[t / nf][t % nf] = 0.0;
         }
         __syncthreads();
-        for (int t = tid; t < P * nf; t += NT) {
-            const int n = t / nf, f = t % nf;
-            double s = 0.0;
-            for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
-            pl.coef[(gl * pl.nfield + f) * P + n] = s * ((n == 0) ? 1.0 : 2.0) / P;
+        if (l > 0) {
+            for (int t = tid; t < P * nf; t += blockDim.x) pl.F[(g * P + t / nf) * pl.nfield + t % nf] = Fs[t / nf][t % nf];
+        } else {
+            const int64_t gl = pl.leaf_base[p] + b;
+            for (int t = tid; t < P * nf; t += blockDim.x) {
+                const int n = t / nf, f = t % nf;
+                double s = 0.0;
+                for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
+                pl.coef[(gl * pl.nfield + f) * P + n] = s * ((n == 0) ? 1.0 : 2.0) / P;
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Secular roots of the FMM problems.  Units: first one per problem for its
-// last root (outside the tree; every pole direct, the warp splits the poles),
-// then one per 32 roots of a leaf box.  One root per lane; each sweep sums
-// the near boxes with shifted differences (staged per warp) and evaluates the
-// four far-field expansions at x = d_K + y.
+// Secular roots of the FMM problems, one warp per leaf box: a lane takes the
+// next root of the box when its root has converged (the box's roots share
+// the near list).  Each sweep sums the near boxes with shifted differences
+// (staged per warp) and evaluates the four far-field expansions at
+// x = d_K + y.  The last root of each problem (outside the tree) is solved
+// by k_secular_last.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(64)
-k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter)
+k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
+              unsigned long long *terms)
 {
     __shared__ double sd[2][B], sw[2][B];
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nf = *pl.nfmm;
     const int64_t nleaf = pl.leaf_base[pl.nprob];
-    const int64_t nunits = nf + nleaf * (B / 32);
-    for (int64_t u = (int64_t)blockIdx.x * 2 + warp; u < nunits; u += (int64_t)gridDim.x * 2) {
-        if (u < nf) {
-            const int64_t p = pl.fprob[u];
-            if (pl.fslot[p] < 0) continue;
-            const int64_t b0 = off[p];
-            const int m = o.mk[p];
-            const double *dk = o.dk + b0, *zk = o.zk + b0;
-            const double W = o.wsum[p];
-            const double tol = stop_c * (double)m * SDC_EPS;
-            Root R;
-            R.init(dk, zk, m - 1, m, W);
-            bool fin = false;
-            while (!fin) {
-                const bool p0 = (R.phase == 0);
-                double ps = 0.0, dps = 0.0;
-                for (int j = lane; j < m; j += 32) {
-                    const double t = shifted_t(dk[j], R.dK, R.y);
-                    const double r = rcp_nr1(t);
-                    const double z = zk[j];
-                    const double a = (z * z) * r;
-                    ps += a;
-                    if (!p0) dps = fma(a, r, dps);
-                }
-                for (int sh = 16; sh > 0; sh >>= 1) {
-                    ps += __shfl_down_sync(FULL, ps, sh);
-                    dps += __shfl_down_sync(FULL, dps, sh);
-                }
-                Acc A;
-                A.psi = __shfl_sync(FULL, ps, 0);
-                A.dpsi = __shfl_sync(FULL, dps, 0);
-                A.phi = 0.0;
-                A.dphi = 0.0;
-                fin = R.update(A, tol, max_iter, lane == 0 ? o.status : nullptr);
-            }
-            if (lane == 0) {
-                const int k = m - 1;
-                o.org[b0 + k] = R.K;
-                o.eta[b0 + k] = R.y;
-                o.dorg[b0 + k] = R.dK;
-                o.lamk[b0 + k] = R.dK + R.y;
-                if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
-            }
-            continue;
-        }
-        const int64_t lu = u - nf;
-        const int64_t gl = lu / (B / 32);
-        const int half = (int)(lu % (B / 32));
+    for (int64_t gl = (int64_t)blockIdx.x * 2 + warp; gl < nleaf; gl += (int64_t)gridDim.x * 2) {
         const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
         if (pl.fslot[p] < 0) continue;
         const int64_t b0 = off[p];
         const int m = o.mk[p];
         const int Tb = (int)(gl - pl.leaf_base[p]);
-        const int k0 = Tb * B + half * 32;
-        const int kend = min(k0 + 32, m - 1);
+        const int k0 = Tb * B;
+        const int kend = min(k0 + B, m - 1);
         if (k0 >= kend) continue;
         const double *dk = o.dk + b0, *zk = o.zk + b0;
         const double W = o.wsum[p];
@@ -618,8 +743,13 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
         const double *cf = pl.coef + gl * pl.nfield * P;
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
+        if (nnr < 0 || nnr >= SPLIT_NEAR) continue;     // long near list: k_secular_fmm_split
+        int near_terms = 0;
+        if (terms)
+            for (int i = 0; i < nn; i++) near_terms += min(B, m - near_box(pl, g, nnr, i) * B);
         int k = k0 + lane;
         bool act = k < kend;
+        int next = k0 + 32;
         Root R;
         R.dK = 0.0; R.y = 1.0; R.phase = 1;
         if (act) R.init(dk, zk, k, m, W);
@@ -628,6 +758,8 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
             const int kwhi = __reduce_max_sync(FULL, act ? k : -1);
             const int kk = act ? k : kwlo;
             const bool p0 = __all_sync(FULL, !act || R.phase == 0);
+            const unsigned amask = __ballot_sync(FULL, act);
+            if (terms && lane == 0) atomicAdd(terms, (unsigned long long)__popc(amask) * (unsigned long long)near_terms);
             Acc A = {0.0, 0.0, 0.0, 0.0};
             if (act) {
                 // far field at the plain position x = d_K + y (local shifting)
@@ -647,7 +779,7 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
                 A.dphi = fma(uu, e1, cf[3 * P] - e2);
             }
             for (int i = 0; i < nn; i++) {
-                const int S = near_box(pl.near, g, nnr, i);
+                const int S = near_box(pl, g, nnr, i);
                 const int j0 = S * B;
                 const int cnt = min(B, m - j0);
                 __syncwarp();
@@ -660,14 +792,190 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
                 if (p0) sweep<false>(sd[warp], sw[warp], 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
                 else    sweep<true>(sd[warp], sw[warp], 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
             }
+            bool fin = false;
             if (act && R.update(A, tol, max_iter, o.status)) {
                 o.org[b0 + k] = R.K;
                 o.eta[b0 + k] = R.y;
                 o.dorg[b0 + k] = R.dK;
                 o.lamk[b0 + k] = R.dK + R.y;
                 if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
-                act = false;
+                fin = true;
             }
+            const unsigned mask = __ballot_sync(FULL, fin);
+            if (fin) {
+                k = next + __popc(mask & ((1u << lane) - 1u));
+                act = k < kend;
+                if (act) R.init(dk, zk, k, m, W);
+            }
+            next += __popc(mask);
+        }
+    }
+}
+
+// Leaf boxes with long near lists (SPLIT_NEAR boxes or more, or "all near"),
+// one CTA of SPW warps per box: the warps hold the same 32 roots (replicated
+// state), split the near boxes between them and reduce the partial sums
+// through shared memory in a fixed order after every sweep; the box's roots
+// run in groups of 32.
+template <int SPW>
+__global__ void __launch_bounds__(SPW * 32)
+k_secular_fmm_split(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
+                    unsigned long long *terms)
+{
+    __shared__ double sd[SPW][B], sw[SPW][B];
+    __shared__ double red[SPW][4][32];
+    const unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nleaf = pl.leaf_base[pl.nprob];
+    for (int64_t gl = blockIdx.x; gl < nleaf; gl += gridDim.x) {
+        const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
+        if (pl.fslot[p] < 0) continue;
+        const int64_t b0 = off[p];
+        const int m = o.mk[p];
+        const int Tb = (int)(gl - pl.leaf_base[p]);
+        const int64_t g = pl.box_base[p] + Tb;
+        const int nnr = pl.nnear[g];
+        if (nnr >= 0 && nnr < SPLIT_NEAR) continue;     // short list: k_secular_fmm
+        const int nn = near_len(nnr, (m + B - 1) / B);
+        const int k0b = Tb * B;
+        const int kendb = min(k0b + B, m - 1);
+        const double *dk = o.dk + b0, *zk = o.zk + b0;
+        const double W = o.wsum[p];
+        const double tol = stop_c * (double)m * SDC_EPS;
+        double cT, hT;
+        box_ch(pl.blo[g], pl.bhi[g], cT, hT);
+        const double ihT = 1.0 / hT;
+        const double *cf = pl.coef + gl * pl.nfield * P;
+        int near_terms = 0;
+        if (terms)
+            for (int i = 0; i < nn; i++) near_terms += min(B, m - near_box(pl, g, nnr, i) * B);
+        for (int k0 = k0b; k0 < kendb; k0 += 32) {
+            const int k = k0 + lane;
+            bool act = k < kendb;
+            Root R;
+            R.dK = 0.0; R.y = 1.0; R.phase = 1;
+            if (act) R.init(dk, zk, k, m, W);
+            while (__syncthreads_or(act)) {
+                const int kwlo = __reduce_min_sync(FULL, act ? k : 0x7fffffff);
+                const int kwhi = __reduce_max_sync(FULL, act ? k : -1);
+                const int kk = act ? k : kwlo;
+                const bool p0 = __all_sync(FULL, !act || R.phase == 0);
+                const unsigned amask = __ballot_sync(FULL, act);
+                if (terms && warp == 0 && lane == 0)
+                    atomicAdd(terms, (unsigned long long)__popc(amask) * (unsigned long long)near_terms);
+                Acc A = {0.0, 0.0, 0.0, 0.0};
+                if (warp == 0 && act) {
+                    const double uu = ((R.dK + R.y) - cT) * ihT;
+                    A.psi = clenshaw(cf, uu);
+                    A.phi = clenshaw(cf + P, uu);
+                    A.dpsi = clenshaw(cf + 2 * P, uu);
+                    A.dphi = clenshaw(cf + 3 * P, uu);
+                }
+                for (int i = warp; i < nn; i += SPW) {
+                    const int S = near_box(pl, g, nnr, i);
+                    const int j0 = S * B;
+                    const int cnt = min(B, m - j0);
+                    __syncwarp();
+                    for (int jj = lane; jj < cnt; jj += 32) {
+                        sd[warp][jj] = dk[j0 + jj];
+                        const double z = zk[j0 + jj];
+                        sw[warp][jj] = z * z;
+                    }
+                    __syncwarp();
+                    if (p0) sweep<false>(sd[warp], sw[warp], 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
+                    else    sweep<true>(sd[warp], sw[warp], 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
+                }
+                red[warp][0][lane] = A.psi;
+                red[warp][1][lane] = A.phi;
+                red[warp][2][lane] = A.dpsi;
+                red[warp][3][lane] = A.dphi;
+                __syncthreads();
+                Acc T = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+                for (int w = 0; w < SPW; w++) {      // same order in every warp
+                    T.psi += red[w][0][lane];
+                    T.phi += red[w][1][lane];
+                    T.dpsi += red[w][2][lane];
+                    T.dphi += red[w][3][lane];
+                }
+                __syncthreads();
+                if (act && R.update(T, tol, max_iter, warp == 0 ? o.status : nullptr)) {
+                    if (warp == 0) {
+                        o.org[b0 + k] = R.K;
+                        o.eta[b0 + k] = R.y;
+                        o.dorg[b0 + k] = R.dK;
+                        o.lamk[b0 + k] = R.dK + R.y;
+                        if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
+                    }
+                    act = false;
+                }
+            }
+        }
+    }
+}
+
+// The last root of every FMM problem (in (d_{m-1}, d_{m-1} + sum w]): every
+// pole direct, split over a CTA; thread 0 holds the root state, the partial
+// sums are reduced in a fixed order.
+constexpr int SL_T = 256;
+
+__global__ void __launch_bounds__(SL_T)
+k_secular_last(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
+               unsigned long long *terms)
+{
+    __shared__ double red[2][SL_T / 32];
+    __shared__ double s_dK, s_y;
+    __shared__ int s_done, s_p0;
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nf = *pl.nfmm;
+    for (int f = blockIdx.x; f < nf; f += gridDim.x) {
+        const int64_t p = pl.fprob[f];
+        if (pl.fslot[p] < 0) continue;
+        const int64_t b0 = off[p];
+        const int m = o.mk[p];
+        const double *dk = o.dk + b0, *zk = o.zk + b0;
+        const double tol = stop_c * (double)m * SDC_EPS;
+        Root R;
+        __syncthreads();
+        if (tid == 0) {
+            R.init(dk, zk, m - 1, m, o.wsum[p]);
+            s_dK = R.dK; s_y = R.y; s_done = 0; s_p0 = 1;
+        }
+        __syncthreads();
+        while (!s_done) {
+            const double dK = s_dK, y = s_y;
+            const bool p0 = s_p0 != 0;
+            double ps = 0.0, dps = 0.0;
+            for (int j = tid; j < m; j += SL_T) {
+                const double r = rcp_nr1(shifted_t(dk[j], dK, y));
+                const double z = zk[j];
+                const double a = (z * z) * r;
+                ps += a;
+                if (!p0) dps = fma(a, r, dps);
+            }
+            for (int sh = 16; sh > 0; sh >>= 1) {
+                ps += __shfl_down_sync(FULL, ps, sh);
+                dps += __shfl_down_sync(FULL, dps, sh);
+            }
+            if (lane == 0) { red[0][warp] = ps; red[1][warp] = dps; }
+            __syncthreads();
+            if (tid == 0) {
+                Acc A = {0.0, 0.0, 0.0, 0.0};
+                for (int w = 0; w < SL_T / 32; w++) { A.psi += red[0][w]; A.dpsi += red[1][w]; }
+                const bool fin = R.update(A, tol, max_iter, o.status);
+                if (terms) atomicAdd(terms, (unsigned long long)m);
+                s_dK = R.dK; s_y = R.y; s_p0 = (R.phase == 0); s_done = fin;
+                if (fin) {
+                    const int k = m - 1;
+                    o.org[b0 + k] = R.K;
+                    o.eta[b0 + k] = R.y;
+                    o.dorg[b0 + k] = R.dK;
+                    o.lamk[b0 + k] = R.dK + R.y;
+                    if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
+                }
+            }
+            __syncthreads();
         }
     }
 }
@@ -722,7 +1030,7 @@ __global__ void __launch_bounds__(B) k_lowner_fmm(FmmDev pl, const int64_t *__re
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
         for (int s = 0; s < nn; s++) {
-            const int S = near_box(pl.near, g, nnr, s);
+            const int S = near_box(pl, g, nnr, s);
             const int j0 = S * B;
             const int cnt = min(B, (m - 1) - j0);
             __syncthreads();
@@ -802,7 +1110,7 @@ __global__ void __launch_bounds__(B) k_bnorm_fmm(FmmDev pl, const int64_t *__res
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
         for (int q = 0; q < nn; q++) {
-            const int S = near_box(pl.near, g, nnr, q);
+            const int S = near_box(pl, g, nnr, q);
             const int i0 = S * B;
             const int cnt = min(B, m - i0);
             __syncthreads();
@@ -884,7 +1192,7 @@ k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
         for (int s = 0; s < nn; s++) {
-            const int S = near_box(pl.near, g, nnr, s);
+            const int S = near_box(pl, g, nnr, s);
             const int i0 = S * B;
             const int cnt = min(B, m - i0);
             __syncthreads();
@@ -959,7 +1267,7 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
         for (int s = 0; s < nn; s++) {
-            const int S = near_box(pl.near, g, nnr, s);
+            const int S = near_box(pl, g, nnr, s);
             const int j0 = S * B;
             const int cnt = min(B, (m - 1) - j0);
             __syncthreads();
@@ -993,6 +1301,13 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
 
 unsigned fmm_grid() { return (unsigned)(sdc_num_sms() * 8); }
 
+// grid of a level launch: at most one CTA per box the level can hold
+unsigned lev_grid(const FmmPlan &pl, int l)
+{
+    const int64_t nb = (int64_t)lev_nb(pl.nb0max, l) * std::max<int64_t>(1, pl.cap_f);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sdc_num_sms() * 8));
+}
+
 SrcArgs src_from_r1(const int64_t *off, const R1Out &o)
 {
     SrcArgs a{};
@@ -1005,10 +1320,13 @@ template <int MODE, int KER>
 superdc_status far_field(const FmmPlan &pl, const SrcArgs &a, int nw, cudaStream_t st)
 {
     const unsigned g = fmm_grid();
+    const int nf = (KER == K_SEC) ? 4 : nw;
     PROF_LAUNCH("fmm_mom", st, k_fmm_leafmom<MODE><<<g, B, 0, st>>>(pl.dv, a));
     for (int l = 1; l < pl.lmax; l++)
-        PROF_LAUNCH("fmm_m2m", st, k_fmm_m2m<<<g, 128, 0, st>>>(pl.dv, a.mk, l, nw));
+        PROF_LAUNCH("fmm_m2m", st, k_fmm_m2m<<<lev_grid(pl, l), 128, 0, st>>>(pl.dv, a.mk, l, nw));
     PROF_LAUNCH("fmm_m2l", st, k_fmm_m2l<KER><<<g, 128, 0, st>>>(pl.dv, a.mk, nw));
+    for (int l = pl.lmax - 2; l >= 0; l--)
+        PROF_LAUNCH("fmm_l2l", st, k_fmm_l2l<<<lev_grid(pl, l), 128, 0, st>>>(pl.dv, a.mk, l, nf));
     return SUPERDC_OK;
 }
 
@@ -1028,7 +1346,9 @@ void launch_cn(const FmmPlan &pl, const FactorView &f, const double *X, int64_t 
 
 }  // namespace
 
-int fmm_default_min_m() { return 4096; }
+// measured on GB300 (batched rank-one steps of equal size m, direct vs FMM):
+// the FMM is 2x slower at m = 512, 1.2x faster at 1024, 3.6x at 2048, 52x at 32768
+int fmm_default_min_m() { return 1024; }
 
 superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
                         const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,
@@ -1046,6 +1366,7 @@ superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t 
     pl.cap_leaves = total / B + nf_cap + 1;
     pl.cap_boxes = 2 * pl.cap_leaves + nf_cap * 40;
     const int nb0max = (int)((mm + B - 1) / B);
+    pl.nb0max = nb0max;
     pl.lmax = lev_count(nb0max);
     ncol = std::max(1, std::min(ncol, WMAX));
     nfield = std::max(1, std::min(nfield, WMAX));
@@ -1060,6 +1381,7 @@ superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t 
     };
     int64_t *box_base, *leaf_base;
     int32_t *fslot, *fprob, *nfmm, *nnear, *near;
+    int64_t *nstart;
     double *blo, *bhi;
     SDC_CHECK(al(&box_base, nprob + 1));
     SDC_CHECK(al(&leaf_base, nprob + 1));
@@ -1069,17 +1391,25 @@ superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t 
     SDC_CHECK(al(&blo, pl.cap_boxes));
     SDC_CHECK(al(&bhi, pl.cap_boxes));
     SDC_CHECK(al(&nnear, pl.cap_boxes));
-    SDC_CHECK(al(&near, pl.cap_boxes * FMM_NCAP));
+    SDC_CHECK(al(&near, pl.cap_boxes * FMM_NPOOL));
+    SDC_CHECK(al(&nstart, pl.cap_boxes));
     SDC_CHECK(al(&d.M, (size_t)pl.cap_boxes * P * ncol));
     SDC_CHECK(al(&d.W, (size_t)pl.cap_boxes * P * ncol));
     SDC_CHECK(al(&d.coef, (size_t)pl.cap_leaves * nfield * P));
+    SDC_CHECK(al(&d.F, (size_t)pl.cap_boxes * P * nfield));
+    int64_t *lev_off;
+    SDC_CHECK(al(&lev_off, (size_t)pl.lmax * (nf_cap + 1)));
+    d.lev_off = lev_off;
+    d.cap_f = nf_cap;
+
     d.box_base = box_base; d.leaf_base = leaf_base; d.fslot = fslot; d.fprob = fprob; d.nfmm = nfmm;
-    d.blo = blo; d.bhi = bhi; d.nnear = nnear; d.near = near;
+    d.blo = blo; d.bhi = bhi; d.nnear = nnear; d.near = near; d.nstart = nstart;
     PROF_LAUNCH("fmm_plan", st, k_fmm_plan<<<1, 1024, 0, st>>>(nprob, mk, min_m, pl.cap_boxes, pl.cap_leaves,
                                                                pl.cap_f, box_base, leaf_base, fslot, fprob, nfmm));
     const unsigned gt = (unsigned)std::min<int64_t>(nprob, (int64_t)sdc_num_sms() * 4);
     PROF_LAUNCH("fmm_tree", st, k_fmm_tree<<<gt, 256, 0, st>>>(nprob, off, mk, dk, box_base, fslot, blo, bhi,
-                                                               nnear, near, used));
+                                                               nnear, nstart, near, used));
+    PROF_LAUNCH("fmm_plan", st, k_fmm_levoff<<<pl.lmax, 1024, 0, st>>>(mk, fprob, nfmm, nf_cap, lev_off));
     SDC_CHECK(cudaGetLastError());
     pl.on = true;
     return SUPERDC_OK;
@@ -1097,7 +1427,15 @@ superdc_status fmm_secular(const FmmPlan &pl, const int64_t *off, const R1Out &o
 {
     if (!pl.on) return SUPERDC_OK;
     far_field<M_SEC, K_SEC>(pl, src_from_r1(off, o), 1, st);
-    PROF_LAUNCH("fmm_secular", st, k_secular_fmm<<<fmm_grid(), 64, 0, st>>>(pl.dv, off, o, stop_c, max_iter));
+    const unsigned gl = (unsigned)std::max<int64_t>(1, std::min<int64_t>(pl.cap_f, (int64_t)sdc_num_sms() * 2));
+    unsigned long long *terms = prof_counter("fmm_secular_terms");
+    unsigned long long *lterms = prof_counter("fmm_secular_last_terms");
+    PROF_LAUNCH("fmm_secular_last", st, k_secular_last<<<gl, SL_T, 0, st>>>(pl.dv, off, o, stop_c, max_iter,
+                                                                             lterms));
+    PROF_LAUNCH("fmm_secular", st, k_secular_fmm<<<fmm_grid(), 64, 0, st>>>(pl.dv, off, o, stop_c, max_iter,
+                                                                             terms));
+    PROF_LAUNCH("fmm_secular", st, (k_secular_fmm_split<8><<<fmm_grid(), 256, 0, st>>>(pl.dv, off, o, stop_c,
+                                                                                      max_iter, terms)));
     SDC_CHECK(cudaGetLastError());
     return SUPERDC_OK;
 }

@@ -14,8 +14,7 @@
 
 constexpr int FMM_B = 64;      // indices per leaf box
 constexpr int FMM_P = 24;      // Chebyshev nodes (expansion order) per box
-constexpr int FMM_NCAP = 32;   // near-list capacity per box (a box whose list would be longer, and
-                               // its subtree, sums its targets directly over all sources)
+constexpr int FMM_NPOOL = 24;  // near-list pool entries per box (average; lists have any length)
 
 // Device view of a plan: which problems of the batch use the FMM and their
 // box trees (index-based binary tree over the kept poles, near lists from the
@@ -26,8 +25,12 @@ struct FmmDev {
     int32_t *fslot;                        // nprob: >= 0 FMM problem, -1 direct
     const int32_t *fprob, *nfmm;           // FMM problem -> batch problem; count
     const double *blo, *bhi;               // per box: interval [lo, hi] of its points
-    const int32_t *nnear, *near;           // per box: near list (same level); nnear < 0: every source direct
+    const int32_t *nnear, *near;           // per box: near-list length (< 0: every source direct); list pool
+    const int64_t *nstart;                 // per box: start of its near list in the pool
     double *M, *W, *coef;                  // workspace: moments, node weights, leaf coefficients
+    double *F;                             // workspace: far field at every box's nodes
+    const int64_t *lev_off;                // per level: prefix of the FMM problems' box counts
+    int64_t cap_f;                         // capacity of the FMM problem list
     int ncol, nfield;                      // workspace widths
 };
 
@@ -35,6 +38,7 @@ struct FmmPlan {
     FmmDev dv{};
     int64_t cap_boxes = 0, cap_leaves = 0, cap_f = 0;
     int lmax = 0;                          // upper bound on tree levels
+    int nb0max = 0;                        // upper bound on leaf boxes per problem
     bool on = false;                       // some problem may take the FMM path
     std::vector<void *> bufs;
 };

@@ -14,6 +14,7 @@ struct Slot {
 };
 bool g_on = false;
 std::vector<Slot> g_slots;
+std::vector<std::pair<const char *, unsigned long long *>> g_ctr;
 cudaEvent_t g_open = nullptr;
 
 Slot *find(const char *name, bool create)
@@ -43,6 +44,18 @@ void drain(Slot &s)
 }  // namespace
 
 bool prof_on() { return g_on; }
+
+unsigned long long *prof_counter(const char *name)
+{
+    if (!g_on) return nullptr;
+    for (auto &c : g_ctr)
+        if (strcmp(c.first, name) == 0) return c.second;
+    unsigned long long *p = nullptr;
+    if (cudaMalloc(&p, sizeof(unsigned long long)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(unsigned long long)) != cudaSuccess) { cudaFree(p); return nullptr; }
+    g_ctr.push_back({name, p});
+    return p;
+}
 
 void prof_begin(cudaStream_t st)
 {
@@ -76,7 +89,22 @@ superdc_status superdc_profile_reset(void)
         s.launches = 0;
         s.ms = 0.0;
     }
+    for (auto &c : g_ctr) cudaMemset(c.second, 0, sizeof(unsigned long long));
     return SUPERDC_OK;
+}
+
+superdc_status superdc_profile_counter(const char *name, int64_t *value)
+{
+    if (!name || !value) return SUPERDC_ERR_ARG;
+    for (auto &c : g_ctr) {
+        if (strcmp(c.first, name) != 0) continue;
+        unsigned long long v = 0;
+        if (cudaMemcpy(&v, c.second, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SUPERDC_ERR_CUDA;
+        *value = (int64_t)v;
+        return SUPERDC_OK;
+    }
+    *value = 0;
+    return SUPERDC_ERR_ARG;
 }
 
 superdc_status superdc_profile_read(const char *name, int64_t *launches, double *ms)

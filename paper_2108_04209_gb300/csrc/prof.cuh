@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 
 bool prof_on();
+// Device work counter of a named kernel (events it counts are algorithmic
+// operations), or nullptr when profiling is off.
+unsigned long long *prof_counter(const char *name);
 void prof_begin(cudaStream_t st);
 void prof_end(const char *name, cudaStream_t st);
 

@@ -136,11 +136,10 @@ __global__ void k_deflate(int64_t nprob, const int64_t *__restrict__ off,
 
 // ---------------------------------------------------------------------------
 // Deflation of large problems, one CTA (DB_T threads) per problem: the
-// |z| < tau mask and the compactions run in parallel; the Givens scan, whose
-// every test depends on the previous rotation, runs in warp 0 over the
-// survivors, 32 at a time broadcast from registers.  The arithmetic is the
-// same explicitly rounded sequence as k_deflate, so decisions and rotated
-// values agree bit for bit.
+// |z| < tau mask, the adjacent Givens tests and the compactions run in
+// parallel; only chains of consecutive rotations are walked sequentially.
+// The arithmetic is the same explicitly rounded sequence as k_deflate, so
+// decisions and rotated values agree bit for bit.
 // ---------------------------------------------------------------------------
 constexpr int DB_T = 512;
 
@@ -206,53 +205,69 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     }
     __syncthreads();
     if (tid == 0 && s_bad) sdc_latch(o.status, SUPERDC_DEV_NONFINITE);
-    // B: Givens scan over the survivors (warp 0)
+    // B: Givens scan over the survivors.  The candidate of every test is the
+    // previous survivor, so a test can differ from its value on the original
+    // data only right after a rotation.  B1 evaluates every adjacent test on
+    // the original values in parallel and marks the survivors whose test
+    // passes (kept = 2, "chain heads"); B2 walks the chains in order in one
+    // lane: from each head not already inside the previous chain, rotate and
+    // re-test the next pair with the rotated values until a test fails.  The
+    // tests and rotations are the same explicitly rounded operations in the
+    // same order as the plain sequential scan (k_deflate), so the decisions
+    // and rotated values agree bit for bit.
+    for (int t = 1 + tid; t < S; t += DB_T) {
+        const int ia = surv[b0 + t - 1], ib = surv[b0 + t];
+        const double da = wd[b0 + ia], za = wz[b0 + ia], db = wd[b0 + ib], zb = wz[b0 + ib];
+        const double lhs = fabs(__dmul_rn(__dmul_rn(__dsub_rn(da, db), za), zb));
+        const double rhs = __dmul_rn(__dadd_rn(__dmul_rn(za, za), __dmul_rn(zb, zb)), tau);
+        if (lhs < rhs) kept[b0 + ib] = 2;
+    }
+    __syncthreads();
     if (tid < 32) {
         const int lane = tid;
-        int ng = 0;
-        bool has_a = false;
-        int ia = 0;
-        double da = 0.0, za = 0.0;
-        for (int c = 0; c < S; c += 32) {
-            int idx = 0;
-            double dv = 0.0, zv = 0.0;
-            if (c + lane < S) {
-                idx = surv[b0 + c + lane];
-                dv = wd[b0 + idx];
-                zv = wz[b0 + idx];
-            }
-            const int cnt = min(32, S - c);
-            for (int t = 0; t < cnt; t++) {
-                const int ib = __shfl_sync(0xffffffffu, idx, t);
-                double db = __shfl_sync(0xffffffffu, dv, t);
-                double zb = __shfl_sync(0xffffffffu, zv, t);
-                if (has_a) {
-                    double lhs = fabs(__dmul_rn(__dmul_rn(__dsub_rn(da, db), za), zb));
-                    double nrm2 = __dadd_rn(__dmul_rn(za, za), __dmul_rn(zb, zb));
-                    double rhs = __dmul_rn(nrm2, tau);
-                    if (lhs < rhs) {
-                        double r = __dsqrt_rn(nrm2);
-                        double cc0 = __ddiv_rn(zb, r), ss0 = __ddiv_rn(za, r);
-                        double cc = __dmul_rn(cc0, cc0), ss = __dmul_rn(ss0, ss0);
-                        double na = __dadd_rn(__dmul_rn(cc, da), __dmul_rn(ss, db));
-                        double nb = __dadd_rn(__dmul_rn(ss, da), __dmul_rn(cc, db));
-                        if (lane == 0) {
-                            wd[b0 + ia] = na;
-                            wz[b0 + ia] = 0.0;
-                            kept[b0 + ia] = 0;
-                            wd[b0 + ib] = nb;
-                            wz[b0 + ib] = r;
-                            o.giv_ab[2 * (b0 + ng)] = ia;
-                            o.giv_ab[2 * (b0 + ng) + 1] = ib;
-                            o.giv_cs[2 * (b0 + ng)] = cc0;
-                            o.giv_cs[2 * (b0 + ng) + 1] = ss0;
-                        }
-                        ng++;
-                        db = nb;
-                        zb = r;
+        int ng = 0, e_prev = 0;
+        for (int c = 1; c < S; c += 32) {
+            const int t = c + lane;
+            const bool hf = (t < S) && kept[b0 + surv[b0 + t]] == 2;
+            unsigned mask = __ballot_sync(0xffffffffu, hf);
+            while (mask) {
+                const int h = c + __ffs(mask) - 1;
+                mask &= mask - 1;
+                if (h <= e_prev) continue;   // inside (or ending) the previous chain
+                int tend = h, ngl = ng;
+                if (lane == 0) {
+                    int ia = surv[b0 + h - 1];
+                    double da = wd[b0 + ia], za = wz[b0 + ia];
+                    int t2 = h;
+                    while (t2 < S) {
+                        const int ib = surv[b0 + t2];
+                        const double db = wd[b0 + ib], zb = wz[b0 + ib];
+                        const double lhs = fabs(__dmul_rn(__dmul_rn(__dsub_rn(da, db), za), zb));
+                        const double nrm2 = __dadd_rn(__dmul_rn(za, za), __dmul_rn(zb, zb));
+                        const double rhs = __dmul_rn(nrm2, tau);
+                        if (!(lhs < rhs)) break;
+                        const double r = __dsqrt_rn(nrm2);
+                        const double cc0 = __ddiv_rn(zb, r), ss0 = __ddiv_rn(za, r);
+                        const double cc = __dmul_rn(cc0, cc0), ss = __dmul_rn(ss0, ss0);
+                        const double na = __dadd_rn(__dmul_rn(cc, da), __dmul_rn(ss, db));
+                        const double nb = __dadd_rn(__dmul_rn(ss, da), __dmul_rn(cc, db));
+                        wd[b0 + ia] = na;
+                        wz[b0 + ia] = 0.0;
+                        kept[b0 + ia] = 0;
+                        wd[b0 + ib] = nb;
+                        wz[b0 + ib] = r;
+                        o.giv_ab[2 * (b0 + ngl)] = ia;
+                        o.giv_ab[2 * (b0 + ngl) + 1] = ib;
+                        o.giv_cs[2 * (b0 + ngl)] = cc0;
+                        o.giv_cs[2 * (b0 + ngl) + 1] = ss0;
+                        ngl++;
+                        ia = ib; da = nb; za = r;
+                        t2++;
                     }
+                    tend = t2;
                 }
-                ia = ib; da = db; za = zb; has_a = true;
+                e_prev = __shfl_sync(0xffffffffu, tend, 0);
+                ng = __shfl_sync(0xffffffffu, ngl, 0);
             }
         }
         if (lane == 0) s_ng = ng;
@@ -263,7 +278,7 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     double wpart = 0.0;
     for (int c = 0; c < m; c += DB_T) {
         const int i = c + tid;
-        const int k = (i < m) ? (int)kept[b0 + i] : 0;
+        const int k = (i < m) ? (int)(kept[b0 + i] != 0) : 0;
         int tot;
         int pre = block_exscan(k, sh, &tot);
         if (k) {

@@ -26,7 +26,8 @@ FMM_OFF = -1
 def fmm_batch():
     """Problem shapes that stress the box tree: uniform, clustered, graded
     (geometric), two far groups (a box straddling a wide gap), one dominant
-    z (the last eigenvalue far to the right), sizes across box edges."""
+    z (the last eigenvalue far to the right), an ultra-graded spectrum whose
+    near lists exhaust the pool, sizes across box edges."""
     rng = np.random.default_rng(7)
     probs = []
     for m in (256, 300, 511, 777, 1025, 2049, 4500):
@@ -40,6 +41,10 @@ def fmm_batch():
     z = rng.standard_normal(2000) * 1e-3
     z[5] = 30.0
     probs.append((np.sort(rng.uniform(0, 1, 2000)), z))
+    # 30 decades: every box is wider than all boxes to its left together, so
+    # near lists grow with the index until the list pool runs out and leaves
+    # fall back to direct sums over every source
+    probs.append((np.geomspace(1e-10, 1e20, 4096), rng.standard_normal(4096)))
     offs = np.zeros(len(probs) + 1, np.int64)
     offs[1:] = np.cumsum([len(p[0]) for p in probs])
     d = np.concatenate([p[0] for p in probs]).astype(np.float64)
