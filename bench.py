@@ -399,7 +399,8 @@ def main():
                     "problems": int(fm.sum()), "roots": int(mk[fm].sum()),
                     "direct_problems": int((~fm).sum()), "direct_roots": int(mk[~fm].sum())},
             "secular_sweeps_mean": float(sw[sw > 0].mean()) if np.any(sw > 0) else 0.0,
-            "schedule": {"autotuned": "sched=%d tile_roots=%d" % (opts.sched, opts.tile_roots),
+            "schedule": {"autotuned": "sched=%d tile_roots=%d fmm_min_m=%d" % (opts.sched, opts.tile_roots,
+                                                                             opts.fmm_min_m),
                          "candidates_ms": tune_ms},
             "graph_replay_ms_per_step": graph_ms,
             "unbatched": {"value": unbatched_rps, "unit": "roots/s",

@@ -140,11 +140,13 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
  * superdc_secular_batched result `fwd` (the structured eigenvector matrices of
  * eq. (4.26) with the rotations and the sort), applied to caller columns:
  * X, Y total x ncols column-major (ld ldx, ldy >= total), problem p owning rows
- * [offsets[p], offsets[p+1]).  X is read only; X and Y must not overlap. */
+ * [offsets[p], offsets[p+1]).  X is read only; X and Y must not overlap.
+ * opts (may be NULL: defaults): only fmm_min_m is used (problems whose kept
+ * size reaches it use the triangular FMM for the Cauchy-like sums). */
 superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offsets, int64_t total,
                                    const superdc_rank1_out *fwd, int32_t trans, int64_t ncols,
                                    const double *X, int64_t ldx, double *Y, int64_t ldy,
-                                   cudaStream_t stream);
+                                   const superdc_opts *opts, cudaStream_t stream);
 
 /* Adjoint of superdc_secular_batched (reverse mode through the secular roots
  * by the implicit-function theorem; the row-12 building block).

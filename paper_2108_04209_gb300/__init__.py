@@ -252,15 +252,17 @@ def _apply_rank1_T(offsets, out, X):
     return apply_rank1(offsets, out, X, trans=True)
 
 
-def apply_rank1(offsets, out, X, trans=True):
-    """Qhat^T X (trans) or Qhat X for the factors of a secular_batched result."""
+def apply_rank1(offsets, out, X, trans=True, opts=None):
+    """Qhat^T X (trans) or Qhat X for the factors of a secular_batched result
+    (opts: only fmm_min_m is used; None = defaults)."""
     total = int(offsets[-1].item())
     ncols = X.shape[1]
     Xf = X.t().contiguous().t()
     Y = torch.empty((ncols, total), dtype=torch.float64, device=X.device).t()
     ro = L.Rank1Out(**{k: (_ptr(v).value or None) for k, v in out.items()})
     code = L.lib().superdc_rank1_apply(offsets.numel() - 1, _ptr(offsets), total, ctypes.byref(ro),
-                                       1 if trans else 0, ncols, _ptr(Xf), total, _ptr(Y), total, _stream())
+                                       1 if trans else 0, ncols, _ptr(Xf), total, _ptr(Y), total,
+                                       ctypes.byref(opts) if opts is not None else None, _stream())
     L.check(code, "superdc_rank1_apply")
     return Y
 

@@ -86,7 +86,7 @@ def lib():
                                                        c_void_p, c_int64, c_void_p]
         L.superdc_secular_batched_backward.restype = c_int32
         L.superdc_rank1_apply.argtypes = [c_int64, c_void_p, c_int64, ctypes.POINTER(Rank1Out), c_int32, c_int64,
-                                          c_void_p, c_int64, c_void_p, c_int64, c_void_p]
+                                          c_void_p, c_int64, c_void_p, c_int64, ctypes.POINTER(Opts), c_void_p]
         L.superdc_rank1_apply.restype = c_int32
         L.superdc_eig_backward.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p,
                                            c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64,

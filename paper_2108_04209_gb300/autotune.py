@@ -1,10 +1,13 @@
-"""Autotuner for the secular-root schedule of the batched rank-one step.
+"""Autotuner for the schedule of the batched rank-one step.
 
-Candidates: per-warp root pools (sched=1) with 256..2048 roots per work unit,
-and the pole-split schedule (sched=2) with 64..256 roots per work unit.  Each is timed
-with CUDA events on the caller's batch (device tensors, the same call the
-user makes); the fastest is cached per (device, problem-count bucket,
-root-count bucket) in a JSON file so later calls skip the search.
+Stage 1, the direct secular kernel: per-warp root pools (sched=1) with
+256..2048 roots per work unit, and the pole-split schedule (sched=2) with
+64..256 roots per work unit.  Stage 2, with the stage-1 winner: the kept
+problem size from which the triangular FMM takes over (opts.fmm_min_m; the
+crossover depends on the batch, not only on m).  Each candidate is timed with
+CUDA events on the caller's batch (device tensors, the same call the user
+makes); the fastest is cached per (device, problem-count bucket, root-count
+bucket) in a JSON file so later calls skip the search.
 """
 import json
 import os
@@ -15,6 +18,7 @@ from . import _lib as L
 
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "superdc_gb300", "tune.json")
 CANDIDATES = [(1, t) for t in (2048, 1024, 512, 256)] + [(2, t) for t in (64, 128, 256)]
+FMM_CANDIDATES = (512, 1024, 2048, -1)     # -1: direct evaluator only
 
 
 def _key(nprob, total):
@@ -43,13 +47,12 @@ def tune_secular(offsets, d, z, rho=1.0, tau=1e-12, reps=2, use_cache=True):
     nprob, total = offsets.numel() - 1, d.numel()
     key = _key(nprob, total)
     tab = _load() if use_cache else {}
-    if use_cache and key in tab:
-        s, t = tab[key]["best"]
-        return default_opts(tau=tau, sched=s, tile_roots=t), tab[key]["ms"]
+    if use_cache and key in tab and len(tab[key].get("best", [])) == 3:
+        s, t, f = tab[key]["best"]
+        return default_opts(tau=tau, sched=s, tile_roots=t, fmm_min_m=f), tab[key]["ms"]
     out = alloc_rank1_out(nprob, total, d.device)
-    ms = {}
-    for s, t in CANDIDATES:
-        o = default_opts(tau=tau, sched=s, tile_roots=t)
+
+    def measure(o):
         secular_batched(offsets, d, z, rho, o, out=out, check=False)      # warm-up
         best = float("inf")
         for _ in range(reps):
@@ -59,9 +62,16 @@ def tune_secular(offsets, d, z, rho=1.0, tau=1e-12, reps=2, use_cache=True):
             e1.record()
             e1.synchronize()
             best = min(best, e0.elapsed_time(e1))
-        ms["%d/%d" % (s, t)] = best
+        return best
+
+    ms = {}
+    for s, t in CANDIDATES:
+        ms["%d/%d" % (s, t)] = measure(default_opts(tau=tau, sched=s, tile_roots=t))
     s, t = min(CANDIDATES, key=lambda c: ms["%d/%d" % c])
-    tab[key] = {"best": [s, t], "ms": ms}
+    for f in FMM_CANDIDATES:
+        ms["%d/%d/fmm%d" % (s, t, f)] = measure(default_opts(tau=tau, sched=s, tile_roots=t, fmm_min_m=f))
+    f = min(FMM_CANDIDATES, key=lambda c: ms["%d/%d/fmm%d" % (s, t, c)])
+    tab[key] = {"best": [s, t, f], "ms": ms}
     if use_cache:
         _save(tab)
-    return default_opts(tau=tau, sched=s, tile_roots=t), ms
+    return default_opts(tau=tau, sched=s, tile_roots=t, fmm_min_m=f), ms

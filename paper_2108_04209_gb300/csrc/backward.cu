@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "cauchy.cuh"
+#include "fmm.cuh"
 #include "prof.cuh"
 
 namespace {
@@ -309,8 +310,11 @@ extern "C" superdc_status superdc_secular_batched_backward(
 
 extern "C" superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offsets, int64_t total,
                                               const superdc_rank1_out *fwd, int32_t trans, int64_t ncols,
-                                              const double *X, int64_t ldx, double *Y, int64_t ldy, cudaStream_t st)
+                                              const double *X, int64_t ldx, double *Y, int64_t ldy,
+                                              const superdc_opts *opts, cudaStream_t st)
 {
+    superdc_opts def;
+    if (!opts) { superdc_opts_default(&def); opts = &def; }
     if (nprob < 0 || total < 0 || !fwd || ncols < 0 || (trans != 0 && trans != 1)) return SUPERDC_ERR_ARG;
     if (nprob == 0 || total == 0 || ncols == 0) return SUPERDC_OK;
     if (!offsets || !X || !Y || ldx < total || ldy < total || !fwd->dk || !fwd->eta || !fwd->vhat ||
@@ -328,6 +332,7 @@ extern "C" superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offs
     f.nprob = nprob; f.off = offsets; f.mk = fwd->mk; f.ngiv = fwd->ngiv; f.dk = fwd->dk; f.eta = fwd->eta;
     f.dorg = dorg; f.vhat = fwd->vhat; f.bnorm = fwd->bnorm; f.src = fwd->src; f.perm = fwd->perm; f.pinv = pinv;
     f.giv_ab = fwd->giv_ab; f.giv_cs = fwd->giv_cs;
+    f.fmm_min_m = fmm_resolve(opts->fmm_min_m);
     superdc_status s;
     if (trans) {
         SDC_CHECK(sdc_alloc(&Xw, (size_t)total * ncols, st));

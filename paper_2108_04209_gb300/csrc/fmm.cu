@@ -1346,8 +1346,11 @@ void launch_cn(const FmmPlan &pl, const FactorView &f, const double *X, int64_t 
 
 }  // namespace
 
-// measured on GB300 (batched rank-one steps of equal size m, direct vs FMM):
-// the FMM is 2x slower at m = 512, 1.2x faster at 1024, 3.6x at 2048, 52x at 32768
+// measured on GB300 (python -m paper_2108_04209_gb300.crossover: batches of
+// equal-size rank-one problems, whole step direct vs FMM): at m = 512 the FMM
+// is 1.2x faster with 4096 problems but 2x slower with 256 (fixed costs), from
+// m = 1024 it wins for every batch (2.4x at 1024, 6x at 2048, 100x at 131072);
+// the autotuner refines the threshold per batch
 int fmm_default_min_m() { return 1024; }
 
 superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,

@@ -6,7 +6,9 @@
     python -m paper_2108_04209_gb300.profile_case eig <n> <leaf> <rank>
         superdc_eig twice on a random HSS matrix (seed 4);
     python -m paper_2108_04209_gb300.profile_case applyq <n> <leaf> <rank> <ncols>
-        superdc_eig once, then Q^T times an n x ncols N(0,1) block twice.
+        superdc_eig once, then Q^T times an n x ncols N(0,1) block twice;
+    python -m paper_2108_04209_gb300.profile_case clustered
+        superdc_eig once on the clustered n=16384 matrix (leaf 64, rank 8, seed 2).
 """
 import sys
 
@@ -38,6 +40,11 @@ def main(argv):
                 F.apply_Q(X, trans=True)
         torch.cuda.synchronize()
         print("ok", n)
+    elif what == "clustered":
+        H = sdc.HSSMatrix(inputs.cfg_clustered_16384())
+        lam, F = H.eig(sdc.default_opts(tau=1e-10))
+        torch.cuda.synchronize()
+        print("ok", 16384)
     else:
         raise SystemExit(__doc__)
     return 0
