@@ -155,6 +155,24 @@ def cpu_baseline(batch, budget_s=20.0, tau=1e-12):
             "sample": "first %d of the 4096 problems (%d roots), oracle newton mode, %.1f s" % (nprob, roots, dt)}
 
 
+def max_over_ranks(vals, pg, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the job
+    time); identity without a process group."""
+    if pg is None:
+        return [float(v) for v in vals]
+    import torch
+    tt = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+    return [float(v) for v in tt.cpu()]
+
+
+def job_throughput(units_per_rank_step, steps, ws, tmax_ms):
+    """Whole-job units and units/s: every rank processes units_per_rank_step
+    per step (replicas), the job takes the slowest rank's time."""
+    units = float(units_per_rank_step) * steps * ws
+    return units, units / (tmax_ms * 1e-3)
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -368,15 +386,9 @@ def main():
     h2d = h_off.numel() * 8 + h_d.numel() * 8 + h_z.numel() * 8
     d2h = sum(v.numel() * v.element_size() for v in res.values()) + 4
 
-    # max over ranks
-    tmax = ms
-    e2e_max = e2e_t
-    if pg is not None:
-        tt = torch.tensor([ms, e2e_t], dtype=torch.float64, device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        tmax, e2e_max = float(tt[0]), float(tt[1])
-    roots_all = float(total) * args.steps * ws
-    value = roots_all / (tmax * 1e-3)
+    # max over ranks; every rank solves the whole workload (replicas, weak scaling)
+    tmax, e2e_max = max_over_ranks([ms, e2e_t], pg, dev)
+    roots_all, value = job_throughput(total, args.steps, ws, tmax)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "roots/s", "n_gpus": ws, "steps": args.steps,

@@ -185,114 +185,147 @@ __global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, con
 // A in shared memory with an odd row stride (no bank conflicts on columns),
 // the accumulated rotations in a global scratch block.
 // ---------------------------------------------------------------------------
-constexpr int LEAF_T = 256;
+constexpr int LEAF_T = 1024;
 
+// index of a(i, j) in the packed upper triangle (column j holds rows 0..j)
+__device__ __forceinline__ int pk(int i, int j)
+{
+    return (i <= j) ? i + ((j * (j + 1)) >> 1) : j + ((i * (i + 1)) >> 1);
+}
+
+// Leaf eigendecompositions, one CTA per leaf: Dhat = D - U H U^T (Lemma 2.1),
+// then parallel cyclic Jacobi.  Dhat is kept as a packed upper triangle and
+// the eigenvector matrix V in shared memory (m = 128: 66 KB + 128 KB).  A
+// round of the round-robin ordering rotates m/2 disjoint pairs at once; every
+// 2x2 block of Dhat between two pairs (k, l) becomes J_k^T B J_l in one update
+// (the diagonal blocks by the closed form a_pp - t a_pq, a_qq + t a_pq), so a
+// round costs one pass over the triangle plus one over V.  Threshold rule: a
+// pair is left alone when |a_pq| <= eps sqrt(|a_pp a_qq|) or |a_pq| is
+// negligible against ||Dhat||_F; the sweeps stop when a sweep rotates nothing.
+// Outputs: eigenvalues ascending (ties by index), Q (columns in that order),
+// W = Q^T U.
 __global__ void __launch_bounds__(LEAF_T)
 k_leaf(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
        const int64_t *__restrict__ leaf_doff, const int64_t *__restrict__ leaf_uoff, const int32_t *__restrict__ leaf_id,
        const double *__restrict__ D, const double *__restrict__ U, const double *__restrict__ H,
-       double *__restrict__ Vs, double *__restrict__ Qleaf, const int64_t *__restrict__ qoff,
-       double *__restrict__ lam, double *__restrict__ W, int32_t *status)
+       double *__restrict__ Qleaf, const int64_t *__restrict__ qoff, double *__restrict__ lam,
+       double *__restrict__ W, int32_t *status)
 {
     extern __shared__ double sm[];
-    __shared__ int sp[128], sq[128];
-    __shared__ double sc[128], ss[128];
+    __shared__ int sp[64], sq[64];
+    __shared__ double sc[64], ss[64], st[64];
     __shared__ double red[LEAF_T / 32];
+    __shared__ int s_rot;
+    __shared__ int rank[128];
     const int L = blockIdx.x;
     const int m = (int)leaf_m[L];
-    const int lda = m | 1;
-    double *A = sm;                           // m x lda
-    double *T = sm + (size_t)m * lda;         // m x r  (U H)
+    double *V = sm;                          // m x m, column p at V + p m
+    double *T = sm;                          // m x r = U H, in V's space before V is set
+    double *A = sm + (size_t)max(m * m, m * r);   // packed upper triangle of Dhat
     const double *Dl = D + leaf_doff[L];
     const double *Ul = U + leaf_uoff[L];
     const double *Hl = H + (int64_t)leaf_id[L] * r * r;
-    double *V = Vs + qoff[L];
     const int tid = threadIdx.x;
-    // T = U H
     for (int e = tid; e < m * r; e += LEAF_T) {
-        int i = e % m, k = e / m;
+        const int i = e % m, k = e / m;
         double s = 0;
         for (int q = 0; q < r; q++) s += Ul[i + (int64_t)m * q] * Hl[q + r * k];
         T[i + m * k] = s;
     }
     __syncthreads();
-    // A = D - T U^T, symmetric (upper triangle mirrored)
-    for (int e = tid; e < m * m; e += LEAF_T) {
-        int i = e % m, j = e / m;
-        if (i > j) continue;
-        double s = 0;
-        for (int q = 0; q < r; q++) s += T[i + m * q] * Ul[j + (int64_t)m * q];
-        double v = Dl[i + (int64_t)m * j] - s;
-        A[i * lda + j] = v;
-        A[j * lda + i] = v;
+    const int ntri = (m * (m + 1)) >> 1;
+    for (int j = 0; j < m; j++) {
+        for (int i = tid; i <= j; i += LEAF_T) {
+            double s = 0;
+            for (int q = 0; q < r; q++) s += T[i + m * q] * Ul[j + (int64_t)m * q];
+            A[pk(i, j)] = Dl[i + (int64_t)m * j] - s;
+        }
     }
-    for (int e = tid; e < m * m; e += LEAF_T) V[e] = ((e % m) == (e / m)) ? 1.0 : 0.0;
     __syncthreads();
-    // ||A||_F
+    for (int e = tid; e < m * m; e += LEAF_T) V[e] = ((e % m) == (e / m)) ? 1.0 : 0.0;
+    // ||Dhat||_F
     double part = 0;
-    for (int e = tid; e < m * m; e += LEAF_T) { double v = A[(e / m) * lda + (e % m)]; part += v * v; }
+    for (int j = 0; j < m; j++)
+        for (int i = tid; i <= j; i += LEAF_T) {
+            const double v = A[pk(i, j)];
+            part += (i == j) ? v * v : 2.0 * v * v;
+        }
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if ((tid & 31) == 0) red[tid >> 5] = part;
     __syncthreads();
     double fro2 = 0;
     for (int w = 0; w < LEAF_T / 32; w++) fro2 += red[w];
-    // threshold rule: a pair is left alone when |a_pq| <= eps sqrt(|a_pp a_qq|)
-    // or |a_pq| is negligible against ||A||_F; the sweeps stop when a whole
-    // sweep performs no rotation
     const double negl = SDC_EPS * SDC_EPS * sqrt(fro2);
-    __shared__ int s_rot;
     const int M = m + (m & 1);
     const int np = M / 2;
+    const int nblk = (np * (np + 1)) >> 1;
     int sweep;
     for (sweep = 0; sweep < 60; sweep++) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int rho = 0; rho < M - 1; rho++) {
             if (tid < np) {
-                int pa = (tid == 0) ? 0 : ((tid - 1 + rho) % (M - 1)) + 1;
-                int pb = ((M - 1 - tid - 1 + rho) % (M - 1)) + 1;
+                const int pa = (tid == 0) ? 0 : ((tid - 1 + rho) % (M - 1)) + 1;
+                const int pb = ((M - 1 - tid - 1 + rho) % (M - 1)) + 1;
                 int p = min(pa, pb), q = max(pa, pb);
-                double c = 1.0, s = 0.0;
+                double c = 1.0, s = 0.0, t = 0.0;
                 if (q < m) {
-                    double apq = A[p * lda + q];
-                    double app = A[p * lda + p], aqq = A[q * lda + q];
+                    const double apq = A[pk(p, q)];
+                    const double app = A[pk(p, p)], aqq = A[pk(q, q)];
                     if (fabs(apq) > SDC_EPS * sqrt(fabs(app) * fabs(aqq)) && fabs(apq) > negl) {
-                        double zeta = (aqq - app) / (2.0 * apq);
-                        double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                                   : ((zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)));
+                        const double zeta = (aqq - app) / (2.0 * apq);
+                        t = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                            : ((zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)));
                         c = 1.0 / sqrt(1.0 + t * t);
                         s = t * c;
                         s_rot = 1;
                     }
                 } else {
-                    q = -1;
+                    q = -1;                                   // the padding index of odd m
                 }
-                sp[tid] = p; sq[tid] = (s == 0.0) ? -1 : q; sc[tid] = c; ss[tid] = s;
+                sp[tid] = p; sq[tid] = q; sc[tid] = c; ss[tid] = s; st[tid] = t;
             }
             __syncthreads();
-            for (int it = tid; it < np * m; it += LEAF_T) {          // rows: J^T A
-                int k = it / m, col = it % m;
-                int q = sq[k];
-                if (q < 0) continue;
-                int p = sp[k];
-                double c = sc[k], s = ss[k];
-                double ap = A[p * lda + col], aq = A[q * lda + col];
-                A[p * lda + col] = c * ap - s * aq;
-                A[q * lda + col] = s * ap + c * aq;
+            // blocks (k, l), k <= l, of the triangle: J_k^T B J_l
+            for (int idx = tid; idx < nblk; idx += LEAF_T) {
+                int l = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+                while (((l * (l + 1)) >> 1) > idx) l--;
+                while ((((l + 1) * (l + 2)) >> 1) <= idx) l++;
+                const int k = idx - ((l * (l + 1)) >> 1);
+                const double sk = ss[k], sl = ss[l];
+                if (sk == 0.0 && sl == 0.0) continue;
+                const int p = sp[k], q = sq[k];
+                if (k == l) {
+                    const double apq = A[pk(p, q)];
+                    const double t = st[k];
+                    A[pk(p, p)] -= t * apq;
+                    A[pk(q, q)] += t * apq;
+                    A[pk(p, q)] = 0.0;
+                    continue;
+                }
+                const int r2 = sp[l], s2 = sq[l];
+                const double ck = sc[k], cl = sc[l];
+                const double apr = A[pk(p, r2)];
+                const double aps = (s2 >= 0) ? A[pk(p, s2)] : 0.0;
+                const double aqr = (q >= 0) ? A[pk(q, r2)] : 0.0;
+                const double aqs = (q >= 0 && s2 >= 0) ? A[pk(q, s2)] : 0.0;
+                const double x1 = ck * apr - sk * aqr, x2 = ck * aps - sk * aqs;
+                const double x3 = sk * apr + ck * aqr, x4 = sk * aps + ck * aqs;
+                A[pk(p, r2)] = cl * x1 - sl * x2;
+                if (s2 >= 0) A[pk(p, s2)] = sl * x1 + cl * x2;
+                if (q >= 0) A[pk(q, r2)] = cl * x3 - sl * x4;
+                if (q >= 0 && s2 >= 0) A[pk(q, s2)] = sl * x3 + cl * x4;
             }
-            __syncthreads();
-            for (int it = tid; it < np * m; it += LEAF_T) {          // columns: (J^T A) J, and V J
-                int k = it / m, row = it % m;
-                int q = sq[k];
-                if (q < 0) continue;
-                int p = sp[k];
-                double c = sc[k], s = ss[k];
-                double ap = A[row * lda + p], aq = A[row * lda + q];
-                A[row * lda + p] = c * ap - s * aq;
-                A[row * lda + q] = s * ap + c * aq;
-                double vp = V[(int64_t)p * m + row], vq = V[(int64_t)q * m + row];
-                V[(int64_t)p * m + row] = c * vp - s * vq;
-                V[(int64_t)q * m + row] = s * vp + c * vq;
+            // V J
+            for (int it = tid; it < np * m; it += LEAF_T) {
+                const int k = it / m, row = it % m;
+                const double s = ss[k];
+                if (s == 0.0) continue;
+                const int p = sp[k], q = sq[k];
+                const double c = sc[k];
+                const double vp = V[p * m + row], vq = V[q * m + row];
+                V[p * m + row] = c * vp - s * vq;
+                V[q * m + row] = s * vp + c * vq;
             }
             __syncthreads();
         }
@@ -301,12 +334,11 @@ k_leaf(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__
     }
     if (sweep >= 60 && tid == 0) sdc_latch(status, SUPERDC_DEV_NOCONV);
     // ascending order (ties by index), outputs
-    __shared__ int rank[256];
     for (int i = tid; i < m; i += LEAF_T) {
-        double li = A[i * lda + i];
+        const double li = A[pk(i, i)];
         int rk = 0;
         for (int j = 0; j < m; j++) {
-            double lj = A[j * lda + j];
+            const double lj = A[pk(j, j)];
             rk += (lj < li) || (lj == li && j < i);
         }
         rank[i] = rk;
@@ -316,13 +348,13 @@ k_leaf(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__
     __syncthreads();
     double *Q = Qleaf + qoff[L];
     for (int e = tid; e < m * m; e += LEAF_T) {
-        int row = e % m, i = e / m;
-        Q[(int64_t)rank[i] * m + row] = V[(int64_t)i * m + row];
+        const int row = e % m, i = e / m;
+        Q[(int64_t)rank[i] * m + row] = V[i * m + row];
     }
     for (int e = tid; e < m * r; e += LEAF_T) {
-        int i = e % m, k = e / m;
+        const int i = e % m, k = e / m;
         double s = 0;
-        for (int row = 0; row < m; row++) s += V[(int64_t)i * m + row] * Ul[row + (int64_t)m * k];
+        for (int row = 0; row < m; row++) s += V[i * m + row] * Ul[row + (int64_t)m * k];
         W[leaf_off[L] + rank[i] + n * k] = s;
     }
 }
@@ -670,7 +702,7 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
         }
     }
     // ---- work buffers (released at the end of the call)
-    double *H, *Bts, *sqb, *lamA, *lamB, *Wp, *WK, *WK2, *zk, *wsum, *Vs;
+    double *H, *Bts, *sqb, *lamA, *lamB, *Wp, *WK, *WK2, *zk, *wsum;
     int32_t *org, *perm;
     std::vector<char *> tmp;
     auto talloc = [&](auto **p, size_t cnt) { return dalloc(p, cnt, &tmp); };
@@ -713,7 +745,6 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
     EIG_CHECK(talloc(&wsum, nn));
     EIG_CHECK(talloc(&org, n));
     EIG_CHECK(talloc(&perm, n));
-    EIG_CHECK(talloc(&Vs, qoff.back()));
     EIG_CHECK(cudaMemsetAsync(H, 0, (size_t)nn * rr * sizeof(double), st));
     const int nsm = sdc_num_sms();
     // ---- 1. dividing stage, top-down
@@ -727,10 +758,11 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
     }
     // ---- 2. leaves
     {
-        const size_t smem = ((size_t)h->mmax * (h->mmax | 1) + (size_t)h->mmax * r) * sizeof(double);
+        const size_t mm = (size_t)h->mmax;
+        const size_t smem = (std::max(mm * mm, mm * (size_t)r) + (mm * (mm + 1)) / 2) * sizeof(double);
         EIG_CHECK(cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         PROF_LAUNCH("leaf", st, k_leaf<<<(unsigned)h->nleaves, LEAF_T, smem, st>>>(
-            r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H, Vs,
+            r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H,
             f->Qleaf, f->d_qoff, lamA, Wp, f->status));
     }
     // ---- 3. conquering stage, bottom-up over levels

@@ -711,8 +711,9 @@ __global__ void __launch_bounds__(128) k_fmm_l2l(FmmDev pl, const int32_t *__res
 // ---------------------------------------------------------------------------
 // Secular roots of the FMM problems, one warp per leaf box: a lane takes the
 // next root of the box when its root has converged (the box's roots share
-// the near list).  Each sweep sums the near boxes with shifted differences
-// (staged per warp) and evaluates the four far-field expansions at
+// the near list).  The near boxes' poles and weights (fixed during the
+// iteration) are staged in shared memory once per box; each sweep sums them
+// with shifted differences and evaluates the four far-field expansions at
 // x = d_K + y.  The last root of each problem (outside the tree) is solved
 // by k_secular_last.
 // ---------------------------------------------------------------------------
@@ -720,7 +721,7 @@ __global__ void __launch_bounds__(64)
 k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
               unsigned long long *terms)
 {
-    __shared__ double sd[2][B], sw[2][B];
+    __shared__ double sd[2][SPLIT_NEAR * B], sw[2][SPLIT_NEAR * B];
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nleaf = pl.leaf_base[pl.nprob];
@@ -745,8 +746,18 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
         const int nn = near_len(nnr, (m + B - 1) / B);
         if (nnr < 0 || nnr >= SPLIT_NEAR) continue;     // long near list: k_secular_fmm_split
         int near_terms = 0;
-        if (terms)
-            for (int i = 0; i < nn; i++) near_terms += min(B, m - near_box(pl, g, nnr, i) * B);
+        __syncwarp();
+        for (int i = 0; i < nn; i++) {
+            const int j0 = near_box(pl, g, nnr, i) * B;
+            const int cnt = min(B, m - j0);
+            near_terms += cnt;
+            for (int jj = lane; jj < cnt; jj += 32) {
+                sd[warp][i * B + jj] = dk[j0 + jj];
+                const double z = zk[j0 + jj];
+                sw[warp][i * B + jj] = z * z;
+            }
+        }
+        __syncwarp();
         int k = k0 + lane;
         bool act = k < kend;
         int next = k0 + 32;
@@ -779,18 +790,11 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
                 A.dphi = fma(uu, e1, cf[3 * P] - e2);
             }
             for (int i = 0; i < nn; i++) {
-                const int S = near_box(pl, g, nnr, i);
-                const int j0 = S * B;
+                const int j0 = near_box(pl, g, nnr, i) * B;
                 const int cnt = min(B, m - j0);
-                __syncwarp();
-                for (int jj = lane; jj < cnt; jj += 32) {
-                    sd[warp][jj] = dk[j0 + jj];
-                    const double z = zk[j0 + jj];
-                    sw[warp][jj] = z * z;
-                }
-                __syncwarp();
-                if (p0) sweep<false>(sd[warp], sw[warp], 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
-                else    sweep<true>(sd[warp], sw[warp], 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
+                const double *bd = sd[warp] + i * B, *bw = sw[warp] + i * B;
+                if (p0) sweep<false>(bd, bw, 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
+                else    sweep<true>(bd, bw, 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
             }
             bool fin = false;
             if (act && R.update(A, tol, max_iter, o.status)) {
