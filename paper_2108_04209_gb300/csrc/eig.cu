@@ -179,53 +179,43 @@ __global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, con
 }
 
 // ---------------------------------------------------------------------------
-// Leaf eigendecompositions: Dhat = D - U H U^T, parallel cyclic Jacobi
-// (round-robin pairing, rotations J^T A J with Rutishauser's angle formula),
-// ascending sort, Q_leaf and W_leaf = Q_leaf^T U_leaf.  One CTA per leaf,
-// A in shared memory with an odd row stride (no bank conflicts on columns),
-// the accumulated rotations in a global scratch block.
-// ---------------------------------------------------------------------------
-constexpr int LEAF_T = 1024;
+constexpr int LEAF_T = 256;
 
-// index of a(i, j) in the packed upper triangle (column j holds rows 0..j)
-__device__ __forceinline__ int pk(int i, int j)
-{
-    return (i <= j) ? i + ((j * (j + 1)) >> 1) : j + ((i * (i + 1)) >> 1);
-}
-
-// Leaf eigendecompositions, one CTA per leaf: Dhat = D - U H U^T (Lemma 2.1),
-// then parallel cyclic Jacobi.  Dhat is kept as a packed upper triangle and
-// the eigenvector matrix V in shared memory (m = 128: 66 KB + 128 KB).  A
-// round of the round-robin ordering rotates m/2 disjoint pairs at once; every
-// 2x2 block of Dhat between two pairs (k, l) becomes J_k^T B J_l in one update
-// (the diagonal blocks by the closed form a_pp - t a_pq, a_qq + t a_pq), so a
-// round costs one pass over the triangle plus one over V.  Threshold rule: a
-// pair is left alone when |a_pq| <= eps sqrt(|a_pp a_qq|) or |a_pq| is
-// negligible against ||Dhat||_F; the sweeps stop when a sweep rotates nothing.
-// Outputs: eigenvalues ascending (ties by index), Q (columns in that order),
-// W = Q^T U.
+// Leaf eigendecompositions Dhat = D - U H U^T = Q diag(lambda) Q^T (Lemma 2.1).
+//   k_leaf_tri    one CTA per leaf: Dhat, Householder reduction to tridiagonal
+//                 form (d, e), the orthogonal factor formed in place from the
+//                 reflectors; Q (row-major, unsorted) to the leaf's output slot.
+// Then implicit QL iterations with the usual shift from the leading 2x2 block
+// on (d, e).  A QL sweep is one chain of dependent scalar steps, and on this
+// GPU a scalar FP64 chain is slow, so the chains run in parallel:
+//   large leaves (one CTA per SM): k_leaf_ql runs one leaf per lane and
+//                 records every sweep's rotations; k_leaf_out applies them to
+//                 the rows of Q (each row independently);
+//   small leaves: k_leaf_qlcta, in each leaf's CTA, thread 0 computes one
+//                 sweep while the other warps apply the previous one, and
+//                 several CTAs share an SM.
+// Outputs: eigenvalues ascending (ties by index), Q columns in that order,
+// W = Q^T U.  The FP64 work is about 4 m^3 per leaf (cyclic Jacobi needs about
+// 10 sweeps of 4 m^3).
 __global__ void __launch_bounds__(LEAF_T)
-k_leaf(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
-       const int64_t *__restrict__ leaf_doff, const int64_t *__restrict__ leaf_uoff, const int32_t *__restrict__ leaf_id,
-       const double *__restrict__ D, const double *__restrict__ U, const double *__restrict__ H,
-       double *__restrict__ Qleaf, const int64_t *__restrict__ qoff, double *__restrict__ lam,
-       double *__restrict__ W, int32_t *status)
+k_leaf_tri(int r, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
+           const int64_t *__restrict__ leaf_doff, const int64_t *__restrict__ leaf_uoff,
+           const int32_t *__restrict__ leaf_id, const double *__restrict__ D, const double *__restrict__ U,
+           const double *__restrict__ H, double *__restrict__ Qleaf, const int64_t *__restrict__ qoff,
+           double *__restrict__ dout, double *__restrict__ eout)
 {
     extern __shared__ double sm[];
-    __shared__ int sp[64], sq[64];
-    __shared__ double sc[64], ss[64], st[64];
+    __shared__ double dg[128], ee[128], hh[128];
     __shared__ double red[LEAF_T / 32];
-    __shared__ int s_rot;
-    __shared__ int rank[128];
     const int L = blockIdx.x;
     const int m = (int)leaf_m[L];
-    double *V = sm;                          // m x m, column p at V + p m
-    double *T = sm;                          // m x r = U H, in V's space before V is set
-    double *A = sm + (size_t)max(m * m, m * r);   // packed upper triangle of Dhat
+    const int lda = m | 1;
+    double *A = sm;                              // m x lda, row-major: A[i * lda + j]
+    double *T = sm + (size_t)m * lda;            // m x r = U H, then scratch of length m
     const double *Dl = D + leaf_doff[L];
     const double *Ul = U + leaf_uoff[L];
     const double *Hl = H + (int64_t)leaf_id[L] * r * r;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int e = tid; e < m * r; e += LEAF_T) {
         const int i = e % m, k = e / m;
         double s = 0;
@@ -233,130 +223,363 @@ k_leaf(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__
         T[i + m * k] = s;
     }
     __syncthreads();
-    const int ntri = (m * (m + 1)) >> 1;
-    for (int j = 0; j < m; j++) {
-        for (int i = tid; i <= j; i += LEAF_T) {
+    for (int e = tid; e < m * m; e += LEAF_T) {
+        const int i = e % m, j = e / m;
+        if (i > j) continue;
+        double s = 0;
+        for (int q = 0; q < r; q++) s += T[i + m * q] * Ul[j + (int64_t)m * q];
+        const double v = Dl[i + (int64_t)m * j] - s;
+        A[i * lda + j] = v;
+        A[j * lda + i] = v;
+    }
+    __syncthreads();
+    // block-wide sum; every thread gets the same value
+    auto bsum = [&](double v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        double t = 0;
+        for (int w = 0; w < LEAF_T / 32; w++) t += red[w];
+        __syncthreads();
+        return t;
+    };
+    // Householder reduction: step i zeroes A[i][0 .. i-2] (and the column)
+    for (int i = m - 1; i >= 1; i--) {
+        const int l = i - 1;
+        double sig = 0;
+        for (int k = tid; k < l; k += LEAF_T) sig += A[i * lda + k] * A[i * lda + k];
+        sig = bsum(sig);                                     // without the subdiagonal entry
+        const double f = A[i * lda + l];
+        if (l == 0 || sig == 0.0) {
+            if (tid == 0) { ee[i] = f; hh[i] = 0.0; }
+            __syncthreads();
+            continue;
+        }
+        const double full = sig + f * f;
+        const double g = (f >= 0.0) ? -sqrt(full) : sqrt(full);
+        const double h = full - f * g;                       // = ||u||^2 / 2
+        __syncthreads();
+        if (tid == 0) { ee[i] = g; hh[i] = h; A[i * lda + l] = f - g; }
+        __syncthreads();
+        // p = A u / h on the leading (l+1) x (l+1) block, u = A[i][0..l]
+        double up = 0;
+        for (int j = tid; j <= l; j += LEAF_T) {
             double s = 0;
-            for (int q = 0; q < r; q++) s += T[i + m * q] * Ul[j + (int64_t)m * q];
-            A[pk(i, j)] = Dl[i + (int64_t)m * j] - s;
+            for (int k = 0; k <= l; k++) s += A[j * lda + k] * A[i * lda + k];
+            const double pj = s / h;
+            dg[j] = pj;                                      // p kept in dg until the reduction ends
+            up += A[i * lda + j] * pj;
         }
-    }
-    __syncthreads();
-    for (int e = tid; e < m * m; e += LEAF_T) V[e] = ((e % m) == (e / m)) ? 1.0 : 0.0;
-    // ||Dhat||_F
-    double part = 0;
-    for (int j = 0; j < m; j++)
-        for (int i = tid; i <= j; i += LEAF_T) {
-            const double v = A[pk(i, j)];
-            part += (i == j) ? v * v : 2.0 * v * v;
-        }
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((tid & 31) == 0) red[tid >> 5] = part;
-    __syncthreads();
-    double fro2 = 0;
-    for (int w = 0; w < LEAF_T / 32; w++) fro2 += red[w];
-    const double negl = SDC_EPS * SDC_EPS * sqrt(fro2);
-    const int M = m + (m & 1);
-    const int np = M / 2;
-    const int nblk = (np * (np + 1)) >> 1;
-    int sweep;
-    for (sweep = 0; sweep < 60; sweep++) {
-        if (tid == 0) s_rot = 0;
+        const double K = bsum(up) / (2.0 * h);
+        for (int j = tid; j <= l; j += LEAF_T) dg[j] -= K * A[i * lda + j];   // q = p - K u
         __syncthreads();
-        for (int rho = 0; rho < M - 1; rho++) {
-            if (tid < np) {
-                const int pa = (tid == 0) ? 0 : ((tid - 1 + rho) % (M - 1)) + 1;
-                const int pb = ((M - 1 - tid - 1 + rho) % (M - 1)) + 1;
-                int p = min(pa, pb), q = max(pa, pb);
-                double c = 1.0, s = 0.0, t = 0.0;
-                if (q < m) {
-                    const double apq = A[pk(p, q)];
-                    const double app = A[pk(p, p)], aqq = A[pk(q, q)];
-                    if (fabs(apq) > SDC_EPS * sqrt(fabs(app) * fabs(aqq)) && fabs(apq) > negl) {
-                        const double zeta = (aqq - app) / (2.0 * apq);
-                        t = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                            : ((zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        s = t * c;
-                        s_rot = 1;
-                    }
-                } else {
-                    q = -1;                                   // the padding index of odd m
-                }
-                sp[tid] = p; sq[tid] = q; sc[tid] = c; ss[tid] = s; st[tid] = t;
+        for (int e2 = tid; e2 < (l + 1) * (l + 1); e2 += LEAF_T) {
+            const int j = e2 / (l + 1), k = e2 % (l + 1);
+            A[j * lda + k] -= A[i * lda + j] * dg[k] + dg[j] * A[i * lda + k];
+        }
+        __syncthreads();
+        for (int j = tid; j <= l; j += LEAF_T) A[j * lda + i] = A[i * lda + j] / h;   // u / h in column i
+        __syncthreads();
+    }
+    // diagonal of the tridiagonal matrix, then the orthogonal factor in place
+    for (int i = tid; i < m; i += LEAF_T) dg[i] = A[i * lda + i];
+    __syncthreads();
+    for (int i = 0; i < m; i++) {
+        const int l = i - 1;
+        if (l >= 0 && hh[i] != 0.0) {
+            // Q[0..l][0..l] <- (I - u u^T / h) Q: g_j = sum_k u_k Q[k][j], Q[k][j] -= g_j (u_k / h)
+            for (int j = tid; j <= l; j += LEAF_T) {
+                double g = 0;
+                for (int k = 0; k <= l; k++) g += A[i * lda + k] * A[k * lda + j];
+                T[j] = g;
             }
             __syncthreads();
-            // blocks (k, l), k <= l, of the triangle: J_k^T B J_l
-            for (int idx = tid; idx < nblk; idx += LEAF_T) {
-                int l = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-                while (((l * (l + 1)) >> 1) > idx) l--;
-                while ((((l + 1) * (l + 2)) >> 1) <= idx) l++;
-                const int k = idx - ((l * (l + 1)) >> 1);
-                const double sk = ss[k], sl = ss[l];
-                if (sk == 0.0 && sl == 0.0) continue;
-                const int p = sp[k], q = sq[k];
-                if (k == l) {
-                    const double apq = A[pk(p, q)];
-                    const double t = st[k];
-                    A[pk(p, p)] -= t * apq;
-                    A[pk(q, q)] += t * apq;
-                    A[pk(p, q)] = 0.0;
-                    continue;
-                }
-                const int r2 = sp[l], s2 = sq[l];
-                const double ck = sc[k], cl = sc[l];
-                const double apr = A[pk(p, r2)];
-                const double aps = (s2 >= 0) ? A[pk(p, s2)] : 0.0;
-                const double aqr = (q >= 0) ? A[pk(q, r2)] : 0.0;
-                const double aqs = (q >= 0 && s2 >= 0) ? A[pk(q, s2)] : 0.0;
-                const double x1 = ck * apr - sk * aqr, x2 = ck * aps - sk * aqs;
-                const double x3 = sk * apr + ck * aqr, x4 = sk * aps + ck * aqs;
-                A[pk(p, r2)] = cl * x1 - sl * x2;
-                if (s2 >= 0) A[pk(p, s2)] = sl * x1 + cl * x2;
-                if (q >= 0) A[pk(q, r2)] = cl * x3 - sl * x4;
-                if (q >= 0 && s2 >= 0) A[pk(q, s2)] = sl * x3 + cl * x4;
-            }
-            // V J
-            for (int it = tid; it < np * m; it += LEAF_T) {
-                const int k = it / m, row = it % m;
-                const double s = ss[k];
-                if (s == 0.0) continue;
-                const int p = sp[k], q = sq[k];
-                const double c = sc[k];
-                const double vp = V[p * m + row], vq = V[q * m + row];
-                V[p * m + row] = c * vp - s * vq;
-                V[q * m + row] = s * vp + c * vq;
+            for (int e2 = tid; e2 < (l + 1) * (l + 1); e2 += LEAF_T) {
+                const int k = e2 / (l + 1), j = e2 % (l + 1);
+                A[k * lda + j] -= T[j] * A[k * lda + i];
             }
             __syncthreads();
         }
-        if (s_rot == 0) break;
+        for (int j = tid; j < i; j += LEAF_T) { A[i * lda + j] = 0.0; A[j * lda + i] = 0.0; }
+        if (tid == 0) A[i * lda + i] = 1.0;
         __syncthreads();
     }
-    if (sweep >= 60 && tid == 0) sdc_latch(status, SUPERDC_DEV_NOCONV);
-    // ascending order (ties by index), outputs
+    // outputs: Q row-major into the leaf's slot; d; e shifted so that e[i]
+    // couples d[i] and d[i+1]
+    double *Q = Qleaf + qoff[L];
+    for (int e = tid; e < m * m; e += LEAF_T) Q[e] = A[(e / m) * lda + (e % m)];
+    const int64_t o = leaf_off[L];
     for (int i = tid; i < m; i += LEAF_T) {
-        const double li = A[pk(i, i)];
+        dout[o + i] = dg[i];
+        eout[o + i] = (i + 1 < m) ? ee[i + 1] : 0.0;
+    }
+}
+
+// Givens pair of a QL step: rr = sqrt(f^2 + g^2), c = g / rr, s = f / rr.  In
+// the usual range x^(-1/2) of q = f^2 + g^2 comes from an FP32 seed and two
+// Newton steps y <- y + y (1 - q y^2) / 2 (relative error 2^-22 -> 2^-44 ->
+// below one ulp), which replaces a square root and a division in the chain of
+// dependent operations; elsewhere hypot and one division.
+__device__ __forceinline__ void ql_pair(double f, double g, double &c, double &s, double &rr)
+{
+    const double q = fma(f, f, g * g);
+    if (q > 1e-36 && q < 1e36) {
+        double y = (double)rsqrtf((float)q);
+        double e = fma(-q * y, y, 1.0);
+        y = fma(0.5 * y, e, y);
+        e = fma(-q * y, y, 1.0);
+        y = fma(0.5 * y, e, y);
+        rr = q * y;
+        c = g * y;
+        s = f * y;
+    } else {
+        rr = hypot(f, g);
+        const double inv = (rr != 0.0) ? 1.0 / rr : 0.0;
+        c = g * inv;
+        s = f * inv;
+    }
+}
+
+// Implicit QL on the tridiagonal (d, e) of every leaf, one lane per leaf; d
+// and e staged in shared memory ([index][lane]).  Sweep t of leaf L records
+// its first column and count in hdr[L * caps + t] and its rotations (c, s) in
+// rot[L * cap + ...] (rotation q of the sweep acts on columns (first - q,
+// first - q + 1)).  A leaf whose iterations or records exceed the caps latches
+// SUPERDC_DEV_NOCONV.
+__global__ void __launch_bounds__(32)
+k_leaf_ql(int nleaves, int mmax, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
+          double *__restrict__ dd, const double *__restrict__ ein, double2 *__restrict__ rot, int2 *__restrict__ hdr,
+          int32_t *__restrict__ nsw, int64_t cap, int caps, int32_t *status)
+{
+    extern __shared__ double sq[];
+    const int lane = threadIdx.x;
+    const int L = blockIdx.x * 32 + lane;
+    double *sd = sq, *se = sq + (size_t)mmax * 32;
+    const bool act = L < nleaves;
+    const int m = act ? (int)leaf_m[L] : 0;
+    const int64_t o = act ? leaf_off[L] : 0;
+    for (int i = 0; i < m; i++) { sd[i * 32 + lane] = dd[o + i]; se[i * 32 + lane] = ein[o + i]; }
+    int64_t nrot = 0;
+    int nsweep = 0;
+    bool bad = false;
+    double2 *R = rot + (int64_t)(act ? L : 0) * cap;
+    int2 *Hd = hdr + (int64_t)(act ? L : 0) * caps;
+    for (int l = 0; l < m && !bad; l++) {
+        for (int iter = 0;; iter++) {
+            int mm = l;
+            for (; mm < m - 1; mm++) {
+                const double s2 = fabs(sd[mm * 32 + lane]) + fabs(sd[(mm + 1) * 32 + lane]);
+                if (fabs(se[mm * 32 + lane]) <= SDC_EPS * s2) break;
+            }
+            if (mm == l) break;
+            if (iter >= 64 || nsweep >= caps || nrot + (mm - l) > cap) { bad = true; break; }
+            double g = (sd[(l + 1) * 32 + lane] - sd[l * 32 + lane]) / (2.0 * se[l * 32 + lane]);
+            double rr = hypot(g, 1.0);
+            g = sd[mm * 32 + lane] - sd[l * 32 + lane] + se[l * 32 + lane] / (g + ((g >= 0.0) ? rr : -rr));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int cnt = 0;
+            bool under = false;
+            for (int i = mm - 1; i >= l; i--) {
+                const double ei = se[i * 32 + lane];
+                const double f = s * ei, bb = c * ei;
+                ql_pair(f, g, c, s, rr);
+                se[(i + 1) * 32 + lane] = rr;
+                if (rr == 0.0) { sd[(i + 1) * 32 + lane] -= p; se[mm * 32 + lane] = 0.0; under = true; break; }
+                g = sd[(i + 1) * 32 + lane] - p;
+                rr = (sd[i * 32 + lane] - g) * s + 2.0 * c * bb;
+                p = s * rr;
+                sd[(i + 1) * 32 + lane] = g + p;
+                g = c * rr - bb;
+                R[nrot + cnt] = make_double2(c, s);
+                cnt++;
+            }
+            if (!under) { sd[l * 32 + lane] -= p; se[l * 32 + lane] = g; se[mm * 32 + lane] = 0.0; }
+            if (cnt > 0) { Hd[nsweep] = make_int2(mm - 1, cnt); nsweep++; nrot += cnt; }
+        }
+    }
+    if (act) {
+        nsw[L] = nsweep;
+        for (int i = 0; i < m; i++) dd[o + i] = sd[i * 32 + lane];
+        if (bad) sdc_latch(status, SUPERDC_DEV_NOCONV);
+    }
+}
+
+// eigenvalues ascending (ties by index), Q columns in that order (column-major
+// into the leaf's slot), W = Q^T U; A holds Q row-major (ld lda), dd the
+// eigenvalues (leaf-local); block-wide
+__device__ void leaf_emit(int L, int r, int64_t n, int m, const double *A, int lda, const double *dd,
+                          const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_uoff,
+                          const double *__restrict__ U, double *__restrict__ Q, double *__restrict__ lam,
+                          double *__restrict__ W, int32_t *status, int *rank)
+{
+    const int tid = threadIdx.x;
+    const int64_t o = leaf_off[L];
+    for (int i = tid; i < m; i += blockDim.x) {
+        const double li = dd[i];
         int rk = 0;
         for (int j = 0; j < m; j++) {
-            const double lj = A[pk(j, j)];
+            const double lj = dd[j];
             rk += (lj < li) || (lj == li && j < i);
         }
         rank[i] = rk;
-        lam[leaf_off[L] + rk] = li;
+        lam[o + rk] = li;
         if (!isfinite(li)) sdc_latch(status, SUPERDC_DEV_NONFINITE);
     }
     __syncthreads();
-    double *Q = Qleaf + qoff[L];
-    for (int e = tid; e < m * m; e += LEAF_T) {
+    const double *Ul = U + leaf_uoff[L];
+    for (int e = tid; e < m * m; e += blockDim.x) {
         const int row = e % m, i = e / m;
-        Q[(int64_t)rank[i] * m + row] = V[i * m + row];
+        Q[(int64_t)rank[i] * m + row] = A[row * lda + i];
     }
-    for (int e = tid; e < m * r; e += LEAF_T) {
+    for (int e = tid; e < m * r; e += blockDim.x) {
         const int i = e % m, k = e / m;
         double s = 0;
-        for (int row = 0; row < m; row++) s += V[i * m + row] * Ul[row + (int64_t)m * k];
-        W[leaf_off[L] + rank[i] + n * k] = s;
+        for (int row = 0; row < m; row++) s += A[row * lda + i] * Ul[row + (int64_t)m * k];
+        W[o + rank[i] + n * k] = s;
     }
+}
+
+__global__ void __launch_bounds__(LEAF_T)
+k_leaf_out(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
+           const int64_t *__restrict__ leaf_uoff, const double *__restrict__ U, double *__restrict__ Qleaf,
+           const int64_t *__restrict__ qoff, const double *__restrict__ dd, const double2 *__restrict__ rot,
+           const int2 *__restrict__ hdr, const int32_t *__restrict__ nsw, int64_t cap, int caps,
+           double *__restrict__ lam, double *__restrict__ W, int32_t *status)
+{
+    extern __shared__ double sm[];
+    __shared__ int rank[128];
+    const int L = blockIdx.x;
+    const int m = (int)leaf_m[L];
+    const int lda = m | 1;
+    double *A = sm;
+    const int tid = threadIdx.x;
+    double *Q = Qleaf + qoff[L];
+    for (int e = tid; e < m * m; e += LEAF_T) A[(e / m) * lda + (e % m)] = Q[e];
+    __syncthreads();
+    // every row independently: rotation q of a sweep acts on columns (i, i+1),
+    // i = first - q; the entry at i + 1 is final after it (carry form)
+    const double2 *R = rot + (int64_t)L * cap;
+    const int2 *Hd = hdr + (int64_t)L * caps;
+    const int ns = nsw[L];
+    for (int row = tid; row < m; row += LEAF_T) {
+        double *qr = A + row * lda;
+        int64_t k = 0;
+        for (int t = 0; t < ns; t++) {
+            const int2 h = Hd[t];
+            const int first = h.x, cnt = h.y;
+            double carry = qr[first + 1];
+            for (int q = 0; q < cnt; q++) {
+                const int i = first - q;
+                const double2 cs = R[k + q];
+                const double x = qr[i];
+                qr[i + 1] = cs.y * x + cs.x * carry;
+                carry = cs.x * x - cs.y * carry;
+            }
+            qr[first - cnt + 1] = carry;
+            k += cnt;
+        }
+    }
+    __syncthreads();
+    leaf_emit(L, r, n, m, A, lda, dd + leaf_off[L], leaf_off, leaf_uoff, U, Q, lam, W, status, rank);
+}
+
+// Small leaves (several CTAs per SM): QL on (d, e) inside the leaf's CTA.
+// Thread 0 computes the rotations of one QL sweep into one of two buffers
+// while warps 1.. apply the previous sweep's rotations to the rows of Q
+// (double buffering, one barrier per phase; the sweeps depend only on d, e,
+// which thread 0 alone updates).
+__global__ void __launch_bounds__(LEAF_T)
+k_leaf_qlcta(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
+             const int64_t *__restrict__ leaf_uoff, const double *__restrict__ U, double *__restrict__ Qleaf,
+             const int64_t *__restrict__ qoff, const double *__restrict__ din, const double *__restrict__ ein,
+             double *__restrict__ lam, double *__restrict__ W, int32_t *status)
+{
+    extern __shared__ double sm[];
+    __shared__ double dg[128], ee[128];
+    __shared__ int s_cnt_b[2], s_first_b[2], s_flag;
+    __shared__ int rank[128];
+    const int L = blockIdx.x;
+    const int m = (int)leaf_m[L];
+    const int lda = m | 1;
+    double *A = sm;
+    double *rc = sm + (size_t)m * lda, *rs = rc + 2 * m;     // two buffers of m each
+    const int tid = threadIdx.x;
+    double *Q = Qleaf + qoff[L];
+    const int64_t o = leaf_off[L];
+    for (int e = tid; e < m * m; e += LEAF_T) A[(e / m) * lda + (e % m)] = Q[e];
+    for (int i = tid; i < m; i += LEAF_T) { dg[i] = din[o + i]; ee[i] = ein[o + i]; }
+    if (tid == 0) s_flag = 0;
+    __syncthreads();
+    int ql_l = 0, ql_iter = 0;
+    auto ql_sweep = [&](int b) -> int {
+        double *bc = rc + b * m, *bs = rs + b * m;
+        while (ql_l < m) {
+            const int l = ql_l;
+            int mm = l;
+            for (; mm < m - 1; mm++) {
+                const double dd2 = fabs(dg[mm]) + fabs(dg[mm + 1]);
+                if (fabs(ee[mm]) <= SDC_EPS * dd2) break;
+            }
+            if (mm == l || ql_iter >= 64) {
+                if (mm != l) s_flag = 1;
+                ql_l++;
+                ql_iter = 0;
+                continue;
+            }
+            ql_iter++;
+            double g = (dg[l + 1] - dg[l]) / (2.0 * ee[l]);
+            double rr = hypot(g, 1.0);
+            g = dg[mm] - dg[l] + ee[l] / (g + ((g >= 0.0) ? rr : -rr));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int cnt = 0;
+            bool under = false;
+            for (int i = mm - 1; i >= l; i--) {
+                const double f = s * ee[i], bb = c * ee[i];
+                ql_pair(f, g, c, s, rr);
+                ee[i + 1] = rr;
+                if (rr == 0.0) { dg[i + 1] -= p; ee[mm] = 0.0; under = true; break; }
+                g = dg[i + 1] - p;
+                rr = (dg[i] - g) * s + 2.0 * c * bb;
+                p = s * rr;
+                dg[i + 1] = g + p;
+                g = c * rr - bb;
+                bc[cnt] = c;
+                bs[cnt] = s;
+                cnt++;
+            }
+            if (!under) { dg[l] -= p; ee[l] = g; ee[mm] = 0.0; }
+            s_first_b[b] = mm - 1;
+            return cnt;
+        }
+        return -1;
+    };
+    if (tid == 0) s_cnt_b[0] = ql_sweep(0);
+    __syncthreads();
+    for (int t = 0;; t++) {
+        const int b = t & 1;
+        const int cnt = s_cnt_b[b];
+        if (cnt < 0) break;                          // uniform: read after the barrier
+        if (tid == 0) {
+            s_cnt_b[b ^ 1] = ql_sweep(b ^ 1);
+        } else if (tid >= 32) {
+            const int first = s_first_b[b];
+            const double *bc = rc + b * m, *bs = rs + b * m;
+            for (int k = tid - 32; k < m; k += LEAF_T - 32) {
+                double *qr = A + k * lda;
+                double carry = qr[first + 1];
+                for (int q = 0; q < cnt; q++) {
+                    const int i = first - q;
+                    const double x = qr[i];
+                    qr[i + 1] = bs[q] * x + bc[q] * carry;
+                    carry = bc[q] * x - bs[q] * carry;
+                }
+                qr[first - cnt + 1] = carry;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && s_flag) sdc_latch(status, SUPERDC_DEV_NOCONV);
+    leaf_emit(L, r, n, m, A, lda, dg, leaf_off, leaf_uoff, U, Q, lam, W, status, rank);
 }
 
 // ---------------------------------------------------------------------------
@@ -759,11 +982,41 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
     // ---- 2. leaves
     {
         const size_t mm = (size_t)h->mmax;
-        const size_t smem = (std::max(mm * mm, mm * (size_t)r) + (mm * (mm + 1)) / 2) * sizeof(double);
-        EIG_CHECK(cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PROF_LAUNCH("leaf", st, k_leaf<<<(unsigned)h->nleaves, LEAF_T, smem, st>>>(
-            r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H,
-            f->Qleaf, f->d_qoff, lamA, Wp, f->status));
+        const size_t smem1 = (mm * (mm | 1) + std::max(mm * (size_t)r, mm)) * sizeof(double);
+        const size_t smem2 = 2 * mm * 32 * sizeof(double);
+        const size_t smem3 = mm * (mm | 1) * sizeof(double);
+        const int64_t cap = 3 * (int64_t)mm * mm, caps = 16 * (int64_t)mm;
+        // large leaves (one CTA per SM): QL chases batched one lane per leaf;
+        // small leaves: the chase inside each leaf's CTA, several CTAs per SM
+        const bool batched = mm >= 96;
+        double *dq, *eq;
+        EIG_CHECK(talloc(&dq, n));
+        EIG_CHECK(talloc(&eq, n));
+        EIG_CHECK(cudaFuncSetAttribute(k_leaf_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+        PROF_LAUNCH("leaf", st, k_leaf_tri<<<(unsigned)h->nleaves, LEAF_T, smem1, st>>>(
+            r, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H, f->Qleaf,
+            f->d_qoff, dq, eq));
+        if (batched) {
+            double2 *rot;
+            int2 *hdr;
+            int32_t *nsw;
+            EIG_CHECK(talloc(&rot, (size_t)h->nleaves * cap));
+            EIG_CHECK(talloc(&hdr, (size_t)h->nleaves * caps));
+            EIG_CHECK(talloc(&nsw, h->nleaves));
+            EIG_CHECK(cudaFuncSetAttribute(k_leaf_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+            EIG_CHECK(cudaFuncSetAttribute(k_leaf_out, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+            PROF_LAUNCH("leaf", st, k_leaf_ql<<<(unsigned)((h->nleaves + 31) / 32), 32, smem2, st>>>(
+                h->nleaves, (int)mm, h->d_leaf_off, h->d_leaf_m, dq, eq, rot, hdr, nsw, cap, (int)caps, f->status));
+            PROF_LAUNCH("leaf", st, k_leaf_out<<<(unsigned)h->nleaves, LEAF_T, smem3, st>>>(
+                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, dq, rot, hdr, nsw, cap,
+                (int)caps, lamA, Wp, f->status));
+        } else {
+            const size_t smem4 = (mm * (mm | 1) + 4 * mm) * sizeof(double);
+            EIG_CHECK(cudaFuncSetAttribute(k_leaf_qlcta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
+            PROF_LAUNCH("leaf", st, k_leaf_qlcta<<<(unsigned)h->nleaves, LEAF_T, smem4, st>>>(
+                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, dq, eq, lamA, Wp,
+                f->status));
+        }
     }
     // ---- 3. conquering stage, bottom-up over levels
     double *dcur = lamA, *dnxt = lamB;

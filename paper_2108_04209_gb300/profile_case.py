@@ -8,7 +8,9 @@
     python -m paper_2108_04209_gb300.profile_case applyq <n> <leaf> <rank> <ncols>
         superdc_eig once, then Q^T times an n x ncols N(0,1) block twice;
     python -m paper_2108_04209_gb300.profile_case clustered
-        superdc_eig once on the clustered n=16384 matrix (leaf 64, rank 8, seed 2).
+        superdc_eig once on the clustered n=16384 matrix (leaf 64, rank 8, seed 2);
+    python -m paper_2108_04209_gb300.profile_case secular_m <m> <nprob>
+        two batched secular calls on <nprob> problems of size m (seed 5).
 """
 import sys
 
@@ -40,6 +42,14 @@ def main(argv):
                 F.apply_Q(X, trans=True)
         torch.cuda.synchronize()
         print("ok", n)
+    elif what == "secular_m":
+        m, nprob = int(argv[2]), int(argv[3])
+        b = inputs.secular_batch(nprob, m, m, seed=5)
+        o, d, z = (torch.from_numpy(x).to(dev) for x in (b.offsets, b.d, b.z))
+        for _ in range(2):
+            sdc.secular_batched(o, d, z, 1.0, sdc.default_opts(tau=1e-12))
+        torch.cuda.synchronize()
+        print("ok", int(b.offsets[-1]))
     elif what == "clustered":
         H = sdc.HSSMatrix(inputs.cfg_clustered_16384())
         lam, F = H.eig(sdc.default_opts(tau=1e-10))
