@@ -142,6 +142,7 @@ __global__ void k_deflate(int64_t nprob, const int64_t *__restrict__ off,
 // decisions and rotated values agree bit for bit.
 // ---------------------------------------------------------------------------
 constexpr int DB_T = 512;
+constexpr int WALK_CAP = 64;      // speculative steps of one chain before one thread finishes it
 
 // exclusive block scan of one int per thread; returns the prefix, *total = sum
 __device__ __forceinline__ int block_exscan(int v, int *sh, int *total)
@@ -209,12 +210,17 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     // previous survivor, so a test can differ from its value on the original
     // data only right after a rotation.  B1 evaluates every adjacent test on
     // the original values in parallel and marks the survivors whose test
-    // passes (kept = 2, "chain heads"); B2 walks the chains in order in one
-    // lane: from each head not already inside the previous chain, rotate and
-    // re-test the next pair with the rotated values until a test fails.  The
-    // tests and rotations are the same explicitly rounded operations in the
-    // same order as the plain sequential scan (k_deflate), so the decisions
-    // and rotated values agree bit for bit.
+    // passes (kept = 2, "chain heads").  B2 takes the positions in rounds of
+    // DB_T: every head of the round walks its chain in its own thread on the
+    // original values (rotate, re-test the next pair with the rotated values,
+    // until a test fails; at most WALK_CAP steps); one thread then decides in
+    // order which heads start a chain of the sequential scan (a head inside or
+    // at the end of the previous chain does not) and gives each chain its
+    // offset in the rotation list; finally the chains write their rotations in
+    // parallel (chains are disjoint; a chain longer than WALK_CAP is finished
+    // and written by that one thread).  Each chain evaluates the same
+    // explicitly rounded operations in the same order as the plain sequential
+    // scan (k_deflate), so decisions and rotated values agree bit for bit.
     for (int t = 1 + tid; t < S; t += DB_T) {
         const int ia = surv[b0 + t - 1], ib = surv[b0 + t];
         const double da = wd[b0 + ia], za = wz[b0 + ia], db = wd[b0 + ib], zb = wz[b0 + ib];
@@ -223,54 +229,91 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
         if (lhs < rhs) kept[b0 + ib] = 2;
     }
     __syncthreads();
-    if (tid < 32) {
-        const int lane = tid;
-        int ng = 0, e_prev = 0;
-        for (int c = 1; c < S; c += 32) {
-            const int t = c + lane;
-            const bool hf = (t < S) && kept[b0 + surv[b0 + t]] == 2;
-            unsigned mask = __ballot_sync(0xffffffffu, hf);
-            while (mask) {
-                const int h = c + __ffs(mask) - 1;
-                mask &= mask - 1;
-                if (h <= e_prev) continue;   // inside (or ending) the previous chain
-                int tend = h, ngl = ng;
-                if (lane == 0) {
-                    int ia = surv[b0 + h - 1];
-                    double da = wd[b0 + ia], za = wz[b0 + ia];
-                    int t2 = h;
-                    while (t2 < S) {
-                        const int ib = surv[b0 + t2];
-                        const double db = wd[b0 + ib], zb = wz[b0 + ib];
-                        const double lhs = fabs(__dmul_rn(__dmul_rn(__dsub_rn(da, db), za), zb));
-                        const double nrm2 = __dadd_rn(__dmul_rn(za, za), __dmul_rn(zb, zb));
-                        const double rhs = __dmul_rn(nrm2, tau);
-                        if (!(lhs < rhs)) break;
-                        const double r = __dsqrt_rn(nrm2);
-                        const double cc0 = __ddiv_rn(zb, r), ss0 = __ddiv_rn(za, r);
-                        const double cc = __dmul_rn(cc0, cc0), ss = __dmul_rn(ss0, ss0);
-                        const double na = __dadd_rn(__dmul_rn(cc, da), __dmul_rn(ss, db));
-                        const double nb = __dadd_rn(__dmul_rn(ss, da), __dmul_rn(cc, db));
-                        wd[b0 + ia] = na;
-                        wz[b0 + ia] = 0.0;
-                        kept[b0 + ia] = 0;
-                        wd[b0 + ib] = nb;
-                        wz[b0 + ib] = r;
-                        o.giv_ab[2 * (b0 + ngl)] = ia;
-                        o.giv_ab[2 * (b0 + ngl) + 1] = ib;
-                        o.giv_cs[2 * (b0 + ngl)] = cc0;
-                        o.giv_cs[2 * (b0 + ngl) + 1] = ss0;
-                        ngl++;
-                        ia = ib; da = nb; za = r;
-                        t2++;
-                    }
-                    tend = t2;
+    {
+        __shared__ int h_pos[DB_T], h_end[DB_T], h_off[DB_T];
+        __shared__ int s_nh, s_eprev;
+        // one chain from position h (candidate s_{h-1}); write = false: count
+        // only.  Returns the first position whose test fails (or S), or -1 when
+        // max_steps rotations were taken without reaching it.  nrot >= 0: take
+        // exactly nrot rotations without testing (the chain's length is known;
+        // its last, failing test would read the first entry of the next chain,
+        // which that chain may be rotating at the same time).
+        auto walk = [&](int h, int max_steps, bool write, int ng0, int nrot) -> int {
+            int ia = surv[b0 + h - 1];
+            double da = wd[b0 + ia], za = wz[b0 + ia];
+            int t2 = h, k = 0;
+            while (t2 < S) {
+                if (nrot >= 0 && k == nrot) break;
+                if (k == max_steps) return -1;
+                const int ib = surv[b0 + t2];
+                const double db = wd[b0 + ib], zb = wz[b0 + ib];
+                const double nrm2 = __dadd_rn(__dmul_rn(za, za), __dmul_rn(zb, zb));
+                if (nrot < 0) {
+                    const double lhs = fabs(__dmul_rn(__dmul_rn(__dsub_rn(da, db), za), zb));
+                    const double rhs = __dmul_rn(nrm2, tau);
+                    if (!(lhs < rhs)) break;
                 }
-                e_prev = __shfl_sync(0xffffffffu, tend, 0);
-                ng = __shfl_sync(0xffffffffu, ngl, 0);
+                const double r = __dsqrt_rn(nrm2);
+                const double cc0 = __ddiv_rn(zb, r), ss0 = __ddiv_rn(za, r);
+                const double cc = __dmul_rn(cc0, cc0), ss = __dmul_rn(ss0, ss0);
+                const double na = __dadd_rn(__dmul_rn(cc, da), __dmul_rn(ss, db));
+                const double nb = __dadd_rn(__dmul_rn(ss, da), __dmul_rn(cc, db));
+                if (write) {
+                    wd[b0 + ia] = na;
+                    wz[b0 + ia] = 0.0;
+                    kept[b0 + ia] = 0;
+                    wd[b0 + ib] = nb;
+                    wz[b0 + ib] = r;
+                    o.giv_ab[2 * (b0 + ng0 + k)] = ia;
+                    o.giv_ab[2 * (b0 + ng0 + k) + 1] = ib;
+                    o.giv_cs[2 * (b0 + ng0 + k)] = cc0;
+                    o.giv_cs[2 * (b0 + ng0 + k) + 1] = ss0;
+                }
+                ia = ib; da = nb; za = r;
+                t2++;
+                k++;
             }
+            return t2;
+        };
+        if (tid == 0) { s_eprev = 0; s_ng = 0; }
+        for (int c = 1; c < S; c += DB_T) {
+            const int t = c + tid;
+            const int hf = (t < S && kept[b0 + surv[b0 + t]] == 2) ? 1 : 0;
+            int nh;
+            const int pre = block_exscan(hf, sh, &nh);
+            if (hf) h_pos[pre] = t;
+            __syncthreads();
+            if (nh == 0) continue;
+            // speculative walks; a head at or before the previous chain's end is
+            // not a chain start, and such a head may read rotated values, so its
+            // result is only used once that has been ruled out
+            if (tid < nh) {
+                const int h = h_pos[tid];
+                h_end[tid] = (h <= s_eprev) ? 0 : walk(h, WALK_CAP, false, 0, -1);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int e_prev = s_eprev, ng = s_ng;
+                for (int i = 0; i < nh; i++) {
+                    const int h = h_pos[i];
+                    if (h <= e_prev) { h_off[i] = -1; continue; }
+                    int e = h_end[i];
+                    if (e < 0) {                         // long chain: finished and written here
+                        e = walk(h, S, true, ng, -1);
+                        h_off[i] = -1;
+                    } else {
+                        h_off[i] = ng;
+                    }
+                    ng += e - h;
+                    e_prev = e;
+                }
+                s_eprev = e_prev;
+                s_ng = ng;
+            }
+            __syncthreads();
+            if (tid < nh && h_off[tid] >= 0) walk(h_pos[tid], S, true, h_off[tid], h_end[tid] - h_pos[tid]);
+            __syncthreads();
         }
-        if (lane == 0) s_ng = ng;
     }
     __syncthreads();
     // C: compaction, kept slots in index order, then deflated slots in index order
