@@ -67,26 +67,46 @@ __global__ void k_tiles_c(int64_t nprob, const int32_t *__restrict__ mk, int tr,
 }
 
 // rotations of the deflation, in scan order (forward) or reversed with the
-// transposed rotation (inverse); one thread per (problem, column)
-__global__ void k_givens(FactorView f, double *X, int64_t ldx, int ncols, int inverse)
+// transposed rotation (inverse).  The rotation list is a sequence of chains
+// (rotation k + 1 continues rotation k when its first index is the second
+// index of k); different chains touch disjoint entries, so one thread per
+// (chain, column) applies its chain in order (reversed for the inverse).
+__global__ void k_givens(FactorView f, int64_t total, double *X, int64_t ldx, int ncols, int inverse)
 {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= f.nprob * ncols) return;
-    const int64_t p = t / ncols;
-    const int col = (int)(t - p * ncols);
-    const int ng = f.ngiv[p];
-    if (ng == 0) return;
-    const int64_t b0 = f.off[p];
-    double *x = X + b0 + (int64_t)col * ldx;
-    const int32_t *ab = f.giv_ab + 2 * b0;
-    const double *cs = f.giv_cs + 2 * b0;
-    for (int g0 = 0; g0 < ng; g0++) {
-        const int g = inverse ? ng - 1 - g0 : g0;
-        const int a = ab[2 * g], b = ab[2 * g + 1];
-        const double c = cs[2 * g], s = cs[2 * g + 1];
-        const double xa = x[a], xb = x[b];
-        if (!inverse) { x[a] = c * xa - s * xb; x[b] = s * xa + c * xb; }
-        else          { x[a] = c * xa + s * xb; x[b] = -s * xa + c * xb; }
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total * ncols;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = t % total;
+        const int col = (int)(t / total);
+        if (x < f.off[0] || x >= f.off[f.nprob]) continue;
+        const int64_t p = sdc_upper_index(f.off, f.nprob, x);
+        const int64_t b0 = f.off[p];
+        const int g = (int)(x - b0);
+        const int ng = f.ngiv[p];
+        if (g >= ng) continue;
+        const int32_t *ab = f.giv_ab + 2 * b0;
+        const double *cs = f.giv_cs + 2 * b0;
+        double *xv = X + b0 + (int64_t)col * ldx;
+        if (!inverse) {
+            if (g > 0 && ab[2 * g] == ab[2 * (g - 1) + 1]) continue;      // not a chain start
+            for (int k = g; k < ng; k++) {
+                if (k > g && ab[2 * k] != ab[2 * (k - 1) + 1]) break;
+                const int a = ab[2 * k], b = ab[2 * k + 1];
+                const double c = cs[2 * k], s = cs[2 * k + 1];
+                const double xa = xv[a], xb = xv[b];
+                xv[a] = c * xa - s * xb;
+                xv[b] = s * xa + c * xb;
+            }
+        } else {
+            if (g + 1 < ng && ab[2 * (g + 1)] == ab[2 * g + 1]) continue;  // not a chain end
+            for (int k = g; k >= 0; k--) {
+                if (k < g && ab[2 * (k + 1)] != ab[2 * k + 1]) break;
+                const int a = ab[2 * k], b = ab[2 * k + 1];
+                const double c = cs[2 * k], s = cs[2 * k + 1];
+                const double xa = xv[a], xb = xv[b];
+                xv[a] = c * xa + s * xb;
+                xv[b] = -s * xa + c * xb;
+            }
+        }
     }
 }
 
@@ -266,11 +286,8 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
     SDC_CHECK(sdc_alloc(&tile_off, f.nprob + 1, st));
     k_tiles_c<<<1, 1024, 0, st>>>(f.nprob, f.mk, TJ, tile_off);
     const int gthreads = 128;
-    if (trans) {
-        int64_t nt = f.nprob * ncols;
-        PROF_LAUNCH("givens", st, k_givens<<<(unsigned)((nt + gthreads - 1) / gthreads), gthreads, 0, st>>>(
-            f, Xmut, ldx, ncols, 0));
-    }
+    if (trans)
+        PROF_LAUNCH("givens", st, k_givens<<<(unsigned)(nsm * 8), gthreads, 0, st>>>(f, total, Xmut, ldx, ncols, 0));
     // problems whose kept size reaches the threshold: triangular FMM
     FmmPlan fp;
     {
@@ -290,11 +307,8 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
     }
     PROF_LAUNCH("deflcopy", st, k_defl_copy<<<(unsigned)(nsm * 8), 256, 0, st>>>(f, total, X, ldx, Y, ldy, ncols,
                                                                                   trans ? 1 : 0));
-    if (!trans) {
-        int64_t nt = f.nprob * ncols;
-        PROF_LAUNCH("givens", st, k_givens<<<(unsigned)((nt + gthreads - 1) / gthreads), gthreads, 0, st>>>(
-            f, Y, ldy, ncols, 1));
-    }
+    if (!trans)
+        PROF_LAUNCH("givens", st, k_givens<<<(unsigned)(nsm * 8), gthreads, 0, st>>>(f, total, Y, ldy, ncols, 1));
     SDC_CHECK(cudaGetLastError());
     SDC_CHECK(cudaFreeAsync(tile_off, st));
     fmm_free(fp, st);
