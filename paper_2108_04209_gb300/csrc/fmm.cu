@@ -543,7 +543,10 @@ __global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__res
 // admissible to T) at T's Chebyshev nodes.  "All near" boxes and the top box
 // get no far field.  Kernels (s source, t target):
 //   K_SEC: 1/(s-t) and 1/(s-t)^2 into four fields (psi, phi, psi', phi' by side)
-//   K_1: 1/(s-t)   K_2: 1/(s-t)^2   K_1N: 1/(t-s)   K_LOG: log|s-t|
+//   K_1: 1/(s-t)   K_2: 1/(s-t)^2   K_1N: 1/(t-s)
+//   K_LOG: log|s-t|, as its t-derivative 1/(t-s) at the nodes plus the sum
+//     itself at the box centre; the derivative's Chebyshev series is
+//     integrated exactly, so a box pair costs P logs instead of P^2
 enum { K_SEC = 0, K_1 = 1, K_2 = 2, K_1N = 3, K_LOG = 4 };
 
 template <int KER>
@@ -556,6 +559,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
     __shared__ double Ws[P][WMAX + 1];
     __shared__ double K1[P][P + 1];
     __shared__ double K2[(KER == K_SEC) ? P : 1][P + 1];
+    __shared__ double Fp[P], An[P + 2], s_f0;
     cheb_tables(xq, Tx);
     const int nf = (KER == K_SEC) ? 4 : nw;
     const int tid = threadIdx.x;
@@ -572,6 +576,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
         double acc[RMAX];
 #pragma unroll
         for (int r = 0; r < RMAX; r++) acc[r] = 0.0;
+        double f0 = 0.0;          // K_LOG: the far field at the box centre (thread 0)
         if (l < L - 1 && pl.nnear[g] >= 0) {
             double cT, hT;
             box_ch(pl.blo[g], pl.bhi[g], cT, hT);
@@ -598,7 +603,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                         const int q = t / P, q2 = t % P;
                         const double diff = (cS + hS * xq[q2]) - tq[q];
                         if (KER == K_LOG) {
-                            K1[q][q2] = log(fabs(diff));
+                            K1[q][q2] = -rcp_nr2(diff);          // d/dt log|s - t| = 1/(t - s)
                         } else {
                             const double r = rcp_nr2(diff);
                             if (KER == K_SEC) { K1[q][q2] = r; K2[q][q2] = r * r; }
@@ -608,6 +613,12 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                         }
                     }
                     __syncthreads();
+                    if (KER == K_LOG && tid < 32) {
+                        // the log sum itself only at the box centre
+                        double v = (tid < P) ? Ws[tid][0] * log(fabs((cS + hS * xq[tid]) - cT)) : 0.0;
+                        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
+                        if (tid == 0) f0 += v;
+                    }
 #pragma unroll
                     for (int r = 0; r < RMAX; r++) {
                         const int t = tid + r * NT;
@@ -625,6 +636,32 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                             acc[r] += s2;
                         }
                     }
+                }
+            }
+            if (KER == K_LOG) {
+                // F' at the nodes (thread q holds it) -> Chebyshev coefficients,
+                // integrated exactly in coefficient space; F = F(centre) +
+                // h (G(x_q) - G(0)) with G the antiderivative in u
+                __syncthreads();
+                if (tid < P) Fp[tid] = acc[0];
+                if (tid == 0) s_f0 = f0;
+                __syncthreads();
+                if (tid < P) {
+                    double a = 0.0;
+                    for (int q = 0; q < P; q++) a = fma(Fp[q], Tx[q * P + tid], a);
+                    An[tid] = a * ((tid == 0) ? 1.0 : 2.0) / P;
+                }
+                if (tid == 0) { An[P] = 0.0; An[P + 1] = 0.0; }
+                __syncthreads();
+                if (tid < P) {
+                    // the degree-P term vanishes at the first-kind nodes but not at 0
+                    double gq = 0.0, g0 = 0.0;
+                    for (int k = 1; k <= P; k++) {
+                        const double bk = (k == 1) ? 0.5 * (2.0 * An[0] - An[2]) : (An[k - 1] - An[k + 1]) / (2.0 * k);
+                        if (k < P) gq = fma(bk, Tx[tid * P + k], gq);
+                        if ((k & 1) == 0) g0 += ((k & 2) ? -bk : bk);      // T_k(0) = (-1)^(k/2)
+                    }
+                    acc[0] = s_f0 + hT * (gq - g0);
                 }
             }
         }

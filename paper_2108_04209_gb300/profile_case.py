@@ -1,8 +1,9 @@
 """Run one named workload through the public API (for profilers such as ncu).
 
-    python -m paper_2108_04209_gb300.profile_case secular <nprob>
+    python -m paper_2108_04209_gb300.profile_case secular <nprob> [fmm_min_m]
         two batched secular calls on the 4096-problem distribution
-        (m ~ U{32..2048}, seed 1) restricted to <nprob> problems;
+        (m ~ U{32..2048}, seed 1) restricted to <nprob> problems, with the
+        FMM threshold fmm_min_m (default: the library's);
     python -m paper_2108_04209_gb300.profile_case eig <n> <leaf> <rank>
         superdc_eig twice on a random HSS matrix (seed 4);
     python -m paper_2108_04209_gb300.profile_case applyq <n> <leaf> <rank> <ncols>
@@ -25,10 +26,12 @@ def main(argv):
     dev = torch.device("cuda")
     if what == "secular":
         n = int(argv[2]) if len(argv) > 2 else 4096
+        fm = int(argv[3]) if len(argv) > 3 else 0
         b = inputs.secular_batch(n, 32, 2048, seed=1)
         o, d, z = (torch.from_numpy(x).to(dev) for x in (b.offsets, b.d, b.z))
         for _ in range(2):
-            sdc.secular_batched(o, d, z, 1.0, sdc.default_opts(tau=1e-12))
+            sdc.secular_batched(o, d, z, 1.0, sdc.default_opts(tau=1e-12, fmm_min_m=fm))
+        torch.cuda.synchronize()
         print("ok", int(b.offsets[-1]))
     elif what in ("eig", "applyq"):
         n, leaf, r = int(argv[2]), int(argv[3]), int(argv[4])
