@@ -236,13 +236,11 @@ __global__ void k_defl_copy(FactorView f, int64_t total, const double *__restric
 template <template <int> class K>
 struct Dummy {};
 
+// the inner loops run all NC columns: even widths up to 20 (the ranks of
+// typical HSS generators) waste at most one FMA per term
 int pick_nc(int c)
 {
-    if (c <= 4) return 4;
-    if (c <= 8) return 8;
-    if (c <= 12) return 12;
-    if (c <= 16) return 16;
-    if (c <= 20) return 20;
+    if (c <= 20) return std::max(2, (c + 1) & ~1);
     if (c <= 24) return 24;
     return 32;
 }
@@ -267,12 +265,10 @@ typedef void (*LaunchFn)(const FactorView &, const int64_t *, const double *, in
 LaunchFn pick(bool trans, int nc)
 {
     switch (nc) {
-    case 4: return trans ? launch_T<4> : launch_N<4>;
-    case 8: return trans ? launch_T<8> : launch_N<8>;
-    case 12: return trans ? launch_T<12> : launch_N<12>;
-    case 16: return trans ? launch_T<16> : launch_N<16>;
-    case 20: return trans ? launch_T<20> : launch_N<20>;
-    case 24: return trans ? launch_T<24> : launch_N<24>;
+#define SDC_NC(W) case W: return trans ? launch_T<W> : launch_N<W>;
+    SDC_NC(2) SDC_NC(4) SDC_NC(6) SDC_NC(8) SDC_NC(10) SDC_NC(12) SDC_NC(14) SDC_NC(16) SDC_NC(18) SDC_NC(20)
+    SDC_NC(24)
+#undef SDC_NC
     default: return trans ? launch_T<32> : launch_N<32>;
     }
 }

@@ -1515,11 +1515,14 @@ superdc_status fmm_cauchy(const FmmPlan &pl, const FactorView &f, const double *
     typedef void (*Fn)(const FmmPlan &, const FactorView &, const double *, int64_t, double *, int64_t, int, int,
                        cudaStream_t);
     Fn fn;
-    if (nc <= 4) fn = trans ? launch_ct<4> : launch_cn<4>;
-    else if (nc <= 8) fn = trans ? launch_ct<8> : launch_cn<8>;
-    else if (nc <= 16) fn = trans ? launch_ct<16> : launch_cn<16>;
-    else if (nc <= 24) fn = trans ? launch_ct<24> : launch_cn<24>;
+    // the inner loops run all NC columns: even widths up to 20 (the ranks of
+    // typical HSS generators) waste at most one FMA per term
+#define SDC_FMM_NC(W) else if (nc <= W) fn = trans ? launch_ct<W> : launch_cn<W>;
+    if (false) {}
+    SDC_FMM_NC(2) SDC_FMM_NC(4) SDC_FMM_NC(6) SDC_FMM_NC(8) SDC_FMM_NC(10) SDC_FMM_NC(12)
+    SDC_FMM_NC(14) SDC_FMM_NC(16) SDC_FMM_NC(18) SDC_FMM_NC(20) SDC_FMM_NC(24)
     else fn = trans ? launch_ct<32> : launch_cn<32>;
+#undef SDC_FMM_NC
     PROF_LAUNCH("fmm_cauchy", st, fn(pl, f, X, ldx, Y, ldy, col0, nc, st));
     SDC_CHECK(cudaGetLastError());
     return SUPERDC_OK;
