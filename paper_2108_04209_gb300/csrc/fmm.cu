@@ -851,6 +851,10 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
             next += __popc(mask);
         }
     }
+    // launched as a programmatic dependent of k_secular_last (independent
+    // roots, so the two overlap): finish only after it has finished, so that
+    // later work in the stream sees its results
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Leaf boxes with long near lists (SPLIT_NEAR boxes or more, or "all near"),
@@ -969,6 +973,8 @@ k_secular_last(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
     __shared__ int s_done, s_p0;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // k_secular_fmm (the other roots) may start at once
+    asm volatile("griddepcontrol.launch_dependents;");
     const int nf = *pl.nfmm;
     for (int f = blockIdx.x; f < nf; f += gridDim.x) {
         const int64_t p = pl.fprob[f];
@@ -1100,39 +1106,17 @@ __global__ void __launch_bounds__(B) k_lowner_fmm(FmmDev pl, const int64_t *__re
 }
 
 // b of the FMM problems, eq. (4.27): near boxes with the shifted entries of
-// eq. (4.28), far boxes by expansion at lambda_j = d_{K_j} + eta_j; the last
-// target j = m-1 (outside the tree) summed directly by a whole CTA.
+// eq. (4.28), far boxes by expansion at lambda_j = d_{K_j} + eta_j.  The last
+// target j = m-1 (outside the tree) is summed directly, spread over the leaf
+// boxes: each box adds up its own sources in a fixed order into lastp, and
+// k_fmm_lastsum combines the boxes (so no single CTA walks all m sources).
 __global__ void __launch_bounds__(B) k_bnorm_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o)
 {
     __shared__ double sd[B], sv[B];
     __shared__ double red[B];
     const int tid = threadIdx.x;
-    const int nf = *pl.nfmm;
     const int64_t nleaf = pl.leaf_base[pl.nprob];
-    for (int64_t u = blockIdx.x; u < nf + nleaf; u += gridDim.x) {
-        if (u < nf) {
-            const int64_t p = pl.fprob[u];
-            if (pl.fslot[p] < 0) continue;
-            const int64_t b0 = off[p];
-            const int m = o.mk[p];
-            const double dK = o.dorg[b0 + m - 1], e = o.eta[b0 + m - 1];
-            double s = 0.0;
-            for (int i = tid; i < m; i += B) {
-                const double r = rcp_nr2((o.dk[b0 + i] - dK) - e);
-                const double vr = o.vhat[b0 + i] * r;
-                s = fma(vr, vr, s);
-            }
-            __syncthreads();
-            red[tid] = s;
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0.0;
-                for (int q = 0; q < B; q++) t += red[q];
-                o.bnorm[b0 + m - 1] = 1.0 / sqrt(t);
-            }
-            continue;
-        }
-        const int64_t gl = u - nf;
+    for (int64_t gl = blockIdx.x; gl < nleaf; gl += gridDim.x) {
         const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
         if (pl.fslot[p] < 0) continue;
         const int64_t b0 = off[p];
@@ -1166,11 +1150,59 @@ __global__ void __launch_bounds__(B) k_bnorm_fmm(FmmDev pl, const int64_t *__res
             }
         }
         if (act) o.bnorm[b0 + j] = 1.0 / sqrt(s);
+        // this box's sources in the sum for the last target
+        double t = 0.0;
+        if (j < m) {
+            const double r = rcp_nr2((o.dk[b0 + j] - o.dorg[b0 + m - 1]) - o.eta[b0 + m - 1]);
+            const double vr = o.vhat[b0 + j] * r;
+            t = vr * vr;
+        }
+        __syncthreads();
+        red[tid] = t;
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0;
+            for (int q = 0; q < B; q++) a += red[q];
+            pl.lastp[gl * pl.ncol] = a;
+        }
+    }
+}
+
+// The last eigenvalue's sums from the leaf boxes' shares (lastp), one warp per
+// (FMM problem, column), in a fixed order: lane-strided partial sums, then a
+// butterfly.  MODE 0: b_{m-1} = sum^{-1/2} into bout.  MODE 1: row pinv_{m-1}
+// of Y = Qhat^T X, b_{m-1} (from bnorm) times the sum.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_fmm_lastsum(FmmDev pl, const int64_t *__restrict__ off,
+                                                     const int32_t *__restrict__ mk, double *__restrict__ bout,
+                                                     const double *__restrict__ bnorm,
+                                                     const int32_t *__restrict__ pinv, double *__restrict__ Y,
+                                                     int64_t ldy, int col0, int nc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)(*pl.nfmm) * nc;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t p = pl.fprob[w / nc];
+        const int q = (int)(w % nc);
+        if (pl.fslot[p] < 0) continue;
+        const int64_t l0 = pl.leaf_base[p], l1 = pl.leaf_base[p + 1];
+        double a = 0.0;
+        for (int64_t gl = l0 + lane; gl < l1; gl += 32) a += pl.lastp[gl * pl.ncol + q];
+        for (int sh = 16; sh > 0; sh >>= 1) a += __shfl_xor_sync(0xffffffffu, a, sh);
+        if (lane == 0) {
+            const int64_t b0 = off[p];
+            const int m = mk[p];
+            if (MODE == 0) bout[b0 + m - 1] = 1.0 / sqrt(a);
+            else Y[b0 + pinv[b0 + m - 1] + (int64_t)(col0 + q) * ldy] = bnorm[b0 + m - 1] * a;
+        }
     }
 }
 
 // Y = Qhat^T X (columns [col0, col0+nc)) for the FMM problems:
 //   y_{pinv_j} = b_j sum_i vhat_i x_{src_i} / ((d_i - d_{K_j}) - eta_j)
+// The row of the last eigenvalue (outside the tree) is summed directly,
+// spread over the leaf boxes (lastp, then k_fmm_lastsum).
 template <int NC>
 __global__ void __launch_bounds__(B)
 k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx, double *__restrict__ Y,
@@ -1179,39 +1211,11 @@ k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
     __shared__ double sd[B];
     __shared__ double sx[NC][B + 1];
     const int tid = threadIdx.x;
-    const int nf = *pl.nfmm;
     const int64_t nleaf = pl.leaf_base[pl.nprob];
-    for (int64_t u = blockIdx.x; u < nf + nleaf; u += gridDim.x) {
+    for (int64_t gl = blockIdx.x; gl < nleaf; gl += gridDim.x) {
         double acc[NC];
 #pragma unroll
         for (int q = 0; q < NC; q++) acc[q] = 0.0;
-        if (u < nf) {
-            const int64_t p = pl.fprob[u];
-            if (pl.fslot[p] < 0) continue;
-            const int64_t b0 = f.off[p];
-            const int m = f.mk[p];
-            const int j = m - 1;
-            const double dK = f.dorg[b0 + j], e = f.eta[b0 + j];
-            for (int i = tid; i < m; i += B) {
-                const double r = rcp_nr2((f.dk[b0 + i] - dK) - e);
-                const double v = f.vhat[b0 + i] * r;
-                const int64_t row = b0 + f.src[b0 + i];
-#pragma unroll
-                for (int q = 0; q < NC; q++)
-                    if (q < nc) acc[q] = fma(v, X[row + (int64_t)(col0 + q) * ldx], acc[q]);
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < NC; q++) sx[q][tid] = acc[q];
-            __syncthreads();
-            if (tid < nc) {
-                double t = 0.0;
-                for (int i = 0; i < B; i++) t += sx[tid][i];
-                Y[b0 + f.pinv[b0 + j] + (int64_t)(col0 + tid) * ldy] = f.bnorm[b0 + j] * t;
-            }
-            continue;
-        }
-        const int64_t gl = u - nf;
         const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
         if (pl.fslot[p] < 0) continue;
         const int64_t b0 = f.off[p];
@@ -1260,6 +1264,24 @@ k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
 #pragma unroll
             for (int q = 0; q < NC; q++)
                 if (q < nc) Y[row + (int64_t)(col0 + q) * ldy] = bj * acc[q];
+        }
+        // this box's sources in the row of the last eigenvalue
+        __syncthreads();
+        if (j < m) {
+            const double r = rcp_nr2((f.dk[b0 + j] - f.dorg[b0 + m - 1]) - f.eta[b0 + m - 1]);
+            const double v = f.vhat[b0 + j] * r;
+            const int64_t row = b0 + f.src[b0 + j];
+#pragma unroll
+            for (int q = 0; q < NC; q++) sx[q][tid] = (q < nc) ? v * X[row + (int64_t)(col0 + q) * ldx] : 0.0;
+        } else {
+#pragma unroll
+            for (int q = 0; q < NC; q++) sx[q][tid] = 0.0;
+        }
+        __syncthreads();
+        if (tid < nc) {
+            double t = 0.0;
+            for (int i = 0; i < B; i++) t += sx[tid][i];
+            pl.lastp[gl * pl.ncol + tid] = t;
         }
     }
 }
@@ -1341,6 +1363,13 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
 }
 
 unsigned fmm_grid() { return (unsigned)(sdc_num_sms() * 8); }
+
+// one warp per (FMM problem, column) of k_fmm_lastsum, 4 warps per CTA
+unsigned lastsum_grid(const FmmPlan &pl, int nc)
+{
+    const int64_t w = std::max<int64_t>(1, pl.cap_f) * nc;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((w + 3) / 4, (int64_t)sdc_num_sms() * 8));
+}
 
 // grid of a level launch: at most one CTA per box the level can hold
 unsigned lev_grid(const FmmPlan &pl, int l)
@@ -1441,6 +1470,7 @@ superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t 
     SDC_CHECK(al(&d.W, (size_t)pl.cap_boxes * P * ncol));
     SDC_CHECK(al(&d.coef, (size_t)pl.cap_leaves * nfield * P));
     SDC_CHECK(al(&d.F, (size_t)pl.cap_boxes * P * nfield));
+    SDC_CHECK(al(&d.lastp, (size_t)pl.cap_leaves * ncol));
     int64_t *lev_off;
     SDC_CHECK(al(&lev_off, (size_t)pl.lmax * (nf_cap + 1)));
     d.lev_off = lev_off;
@@ -1476,8 +1506,22 @@ superdc_status fmm_secular(const FmmPlan &pl, const int64_t *off, const R1Out &o
     unsigned long long *lterms = prof_counter("fmm_secular_last_terms");
     PROF_LAUNCH("fmm_secular_last", st, k_secular_last<<<gl, SL_T, 0, st>>>(pl.dv, off, o, stop_c, max_iter,
                                                                              lterms));
-    PROF_LAUNCH("fmm_secular", st, k_secular_fmm<<<fmm_grid(), 64, 0, st>>>(pl.dv, off, o, stop_c, max_iter,
-                                                                             terms));
+    {
+        // programmatic dependent launch: overlaps k_secular_last (a few CTAs
+        // walking all m poles per sweep) instead of running after it
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(fmm_grid());
+        cfg.blockDim = dim3(64);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        PROF_LAUNCH("fmm_secular", st, SDC_CHECK(cudaLaunchKernelEx(&cfg, k_secular_fmm, pl.dv, off, o, stop_c,
+                                                                    max_iter, terms)));
+    }
     PROF_LAUNCH("fmm_secular", st, (k_secular_fmm_split<8><<<fmm_grid(), 256, 0, st>>>(pl.dv, off, o, stop_c,
                                                                                       max_iter, terms)));
     SDC_CHECK(cudaGetLastError());
@@ -1498,6 +1542,8 @@ superdc_status fmm_bnorm(const FmmPlan &pl, const int64_t *off, const R1Out &o, 
     if (!pl.on) return SUPERDC_OK;
     far_field<M_BN, K_2>(pl, src_from_r1(off, o), 1, st);
     PROF_LAUNCH("fmm_bnorm", st, k_bnorm_fmm<<<fmm_grid(), B, 0, st>>>(pl.dv, off, o));
+    PROF_LAUNCH("fmm_bnorm", st, k_fmm_lastsum<0><<<lastsum_grid(pl, 1), 128, 0, st>>>(
+                                     pl.dv, off, o.mk, o.bnorm, nullptr, nullptr, nullptr, 0, 0, 1));
     SDC_CHECK(cudaGetLastError());
     return SUPERDC_OK;
 }
@@ -1524,6 +1570,9 @@ superdc_status fmm_cauchy(const FmmPlan &pl, const FactorView &f, const double *
     else fn = trans ? launch_ct<32> : launch_cn<32>;
 #undef SDC_FMM_NC
     PROF_LAUNCH("fmm_cauchy", st, fn(pl, f, X, ldx, Y, ldy, col0, nc, st));
+    if (trans)
+        PROF_LAUNCH("fmm_cauchy", st, k_fmm_lastsum<1><<<lastsum_grid(pl, nc), 128, 0, st>>>(
+                                          pl.dv, f.off, f.mk, nullptr, f.bnorm, f.pinv, Y, ldy, col0, nc));
     SDC_CHECK(cudaGetLastError());
     return SUPERDC_OK;
 }

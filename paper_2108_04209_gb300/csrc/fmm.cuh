@@ -29,6 +29,8 @@ struct FmmDev {
     const int64_t *nstart;                 // per box: start of its near list in the pool
     double *M, *W, *coef;                  // workspace: moments, node weights, leaf coefficients
     double *F;                             // workspace: far field at every box's nodes
+    double *lastp;                         // workspace: per leaf box (ncol wide), its sources' share of
+                                           // the sums for the last eigenvalue (outside the tree)
     const int64_t *lev_off;                // per level: prefix of the FMM problems' box counts
     int64_t cap_f;                         // capacity of the FMM problem list
     int ncol, nfield;                      // workspace widths
