@@ -365,7 +365,7 @@ def main():
                                  SECULAR_FLOPS_PER_INTERACTION, fmm_terms, FMM_FAR_FLOPS, fmm_root_sweeps)}
     dom = max(rl, key=lambda k: rl[k]["ms"]) if rl else "k_secular"
     prof = _profiled("k_secular_batched4096_dram.md", "paper_2108_04209_gb300/csrc/rank1.cu") \
-        if dom == "k_secular" else _profiled("fmm_secular_batched4096_dram.md", "paper_2108_04209_gb300/csrc/fmm.cu")
+        if dom == "k_secular" else _profiled("fmm_secular_batched4096_dram.md", "paper_2108_04209_gb300/csrc/fmm_impl.cuh")
     achieved = rl[dom]["achieved"] if rl else 0.0
 
     # e2e: host buffers, copies inside the timed region

@@ -12,7 +12,6 @@
 #include "rank1.cuh"
 #include "cauchy.cuh"
 
-constexpr int FMM_B = 64;      // indices per leaf box
 constexpr int FMM_P = 24;      // Chebyshev nodes (expansion order) per box
 constexpr int FMM_NPOOL = 24;  // near-list pool entries per box (average; lists have any length)
 
@@ -41,6 +40,7 @@ struct FmmPlan {
     int64_t cap_boxes = 0, cap_leaves = 0, cap_f = 0;
     int lmax = 0;                          // upper bound on tree levels
     int nb0max = 0;                        // upper bound on leaf boxes per problem
+    int box = 0;                           // indices per leaf box (32 or 64) of this plan
     bool on = false;                       // some problem may take the FMM path
     std::vector<void *> bufs;
 };
@@ -49,9 +49,11 @@ struct FmmPlan {
 // kept poles dk.  max_m: an upper bound on the problem sizes (-1 unknown).
 // ncol / nfield: widths of the moment and coefficient workspaces.
 // used (may be NULL): per problem 1 if it takes the FMM path, else 0.
+// box: indices per leaf box, 32 or 64 (smaller boxes halve the near field,
+// larger ones halve the number of box pairs whose expansions are translated).
 superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
                         const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,
-                        cudaStream_t st);
+                        int box, cudaStream_t st);
 void fmm_free(FmmPlan &pl, cudaStream_t st);
 
 // Roots of the FMM problems (same outputs as the direct secular kernel).
