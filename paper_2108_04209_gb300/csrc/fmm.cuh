@@ -12,7 +12,7 @@
 #include "rank1.cuh"
 #include "cauchy.cuh"
 
-constexpr int FMM_P = 24;      // Chebyshev nodes (expansion order) per box
+constexpr int FMM_P = 22;      // Chebyshev nodes (expansion order) per box
 constexpr int FMM_NPOOL = 24;  // near-list pool entries per box (average; lists have any length)
 
 // Device view of a plan: which problems of the batch use the FMM and their

@@ -229,13 +229,31 @@ __device__ __forceinline__ int near_count(const double *__restrict__ blo, const 
     return cnt;
 }
 
+// exclusive scan of one value per thread of the CTA (warp shuffles, then the
+// warp totals); sh holds one entry per warp
+__device__ __forceinline__ int64_t cta_exscan(int64_t v, int64_t *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    int64_t before = 0;
+    for (int w = 0; w < warp; w++) before += sh[w];
+    __syncthreads();
+    return before + x - v;
+}
+
 __global__ void __launch_bounds__(256)
 k_fmm_tree(int64_t nprob, const int64_t *__restrict__ off, const int32_t *__restrict__ mk,
            const double *__restrict__ dk, const int64_t *__restrict__ box_base, int32_t *__restrict__ fslot,
            double *__restrict__ blo, double *__restrict__ bhi, int32_t *__restrict__ nnear,
            int64_t *__restrict__ nstart, int32_t *__restrict__ near, int32_t *__restrict__ used)
 {
-    __shared__ int64_t part[256];
+    __shared__ int64_t wsum[8];
     __shared__ int64_t s_pos;
     const int T = blockDim.x;
     for (int64_t p = blockIdx.x; p < nprob; p += gridDim.x) {
@@ -269,14 +287,7 @@ k_fmm_tree(int64_t nprob, const int64_t *__restrict__ off, const int32_t *__rest
                 const int npn = nnear[gp];
                 if (npn >= 0) sum += near_count(blo, bhi, near, gb, nb, b, nstart[gp], npn);
             }
-            part[threadIdx.x] = sum;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int64_t acc = 0;
-                for (int i = 0; i < T; i++) { const int64_t v = part[i]; part[i] = acc; acc += v; }
-            }
-            __syncthreads();
-            int64_t pos = s_pos + part[threadIdx.x];
+            int64_t pos = s_pos + cta_exscan(sum, wsum);
             for (int b = bb; b < be; b++) {
                 int cnt;
                 if (l == L - 1) {
@@ -560,7 +571,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
 {
     constexpr int NT = 128;
     constexpr int RMAX = (P * WMAX + NT - 1) / NT;
-    __shared__ double xq[P], tq[P];
+    __shared__ double xq[P], tq[P], sq[P];
     __shared__ double Tx[P * P];
     __shared__ double Ws[P][WMAX + 1];
     __shared__ double K1[P][P + 1];
@@ -607,9 +618,11 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                     box_ch(loS, hiS, cS, hS);
                     __syncthreads();
                     for (int t = tid; t < P * nw; t += NT) Ws[t / nw][t % nw] = pl.W[(gS * P + t / nw) * pl.ncol + t % nw];
+                    if (tid < P) sq[tid] = cS + hS * xq[tid];
+                    __syncthreads();
                     for (int t = tid; t < P * P; t += NT) {
                         const int q = t / P, q2 = t % P;
-                        const double diff = (cS + hS * xq[q2]) - tq[q];
+                        const double diff = sq[q2] - tq[q];
                         if (KER == K_LOG) {
                             K1[q][q2] = -rcp_nr2(diff);          // d/dt log|s - t| = 1/(t - s)
                         } else {
@@ -623,7 +636,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                     __syncthreads();
                     if (KER == K_LOG && tid < 32) {
                         // the log sum itself only at the box centre
-                        double v = (tid < P) ? Ws[tid][0] * log(fabs((cS + hS * xq[tid]) - cT)) : 0.0;
+                        double v = (tid < P) ? Ws[tid][0] * log(fabs(sq[tid] - cT)) : 0.0;
                         for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_down_sync(0xffffffffu, v, sh);
                         if (tid == 0) f0 += v;
                     }
@@ -875,214 +888,6 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
     // launched as a programmatic dependent of k_secular_last (independent
     // roots, so the two overlap): finish only after it has finished, so that
     // later work in the stream sees its results
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-// Sweep over one staged near box in box-relative indices 0..j1-1; entries at
-// or beyond cnt (this lane's count: a short last box, or no box for this
-// lane) add nothing.  Index split as in sweep(): j <= k to psi, j > k to phi,
-// in regions bounded by the warp's kwlo / kwhi (k = B: the whole box is to the
-// lane's left; k = -1: to its right).
-template <bool DERIV>
-__device__ __forceinline__ void sweep_cnt(const double *__restrict__ sd, const double *__restrict__ sw, int j1,
-                                          int cnt, int k, int kwlo, int kwhi, double dK, double y, Acc &A)
-{
-    const int ea = min(j1, max(0, kwlo + 1));
-    const int eb = min(j1, max(ea, kwhi + 1));
-#pragma unroll 4
-    for (int j = 0; j < ea; j++) {
-        const bool v = j < cnt;
-        const double t = v ? shifted_t(sd[j], dK, y) : 1.0;
-        const double w = v ? sw[j] : 0.0;
-        const double r = rcp_nr1(t);
-        if (DERIV) {
-            const double a = w * r;
-            A.psi += a;
-            A.dpsi = fma(a, r, A.dpsi);
-        } else {
-            A.psi = fma(w, r, A.psi);
-        }
-    }
-    for (int j = ea; j < eb; j++) {
-        const bool v = j < cnt;
-        const double t = v ? shifted_t(sd[j], dK, y) : 1.0;
-        const double w = v ? sw[j] : 0.0;
-        const double r = rcp_nr1(t);
-        const double a = w * r;
-        if (j <= k) { A.psi += a; if (DERIV) A.dpsi = fma(a, r, A.dpsi); }
-        else        { A.phi += a; if (DERIV) A.dphi = fma(a, r, A.dphi); }
-    }
-#pragma unroll 4
-    for (int j = eb; j < j1; j++) {
-        const bool v = j < cnt;
-        const double t = v ? shifted_t(sd[j], dK, y) : 1.0;
-        const double w = v ? sw[j] : 0.0;
-        const double r = rcp_nr1(t);
-        if (DERIV) {
-            const double a = w * r;
-            A.phi += a;
-            A.dphi = fma(a, r, A.dphi);
-        } else {
-            A.phi = fma(w, r, A.phi);
-        }
-    }
-}
-
-// Secular roots with leaf boxes of 32 indices: one warp per pair of adjacent
-// leaf boxes (T, T+1), T even, so that a lane whose root has converged takes
-// the next of the pair's 64 roots (with one box per warp converged lanes would
-// idle).  The two near lists are merged into one set of staged boxes; each
-// lane walks its own box's list over that staging, and the far field of its
-// own box.  Boxes with long near lists are left to k_secular_fmm_split.
-constexpr int PAIR_SLOTS = 2 * SPLIT_NEAR;
-constexpr bool PAIRED = false;
-
-__global__ void __launch_bounds__(64)
-k_secular_fmm_pair(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
-                   unsigned long long *terms)
-{
-    __shared__ double sd[2][PAIR_SLOTS * B], sw[2][PAIR_SLOTS * B];
-    __shared__ int lst[2][2][SPLIT_NEAR];      // near lists of the two boxes (box indices)
-    __shared__ int lslot[2][2][SPLIT_NEAR];    // their staging slots
-    __shared__ int ubox[2][PAIR_SLOTS];        // box of each staging slot
-    __shared__ int s_nu[2], s_nterm[2][2];
-    const unsigned FULL = 0xffffffffu;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nleaf = pl.leaf_base[pl.nprob];
-    for (int64_t gl = (int64_t)blockIdx.x * 2 + warp; gl < nleaf; gl += (int64_t)gridDim.x * 2) {
-        const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
-        if (pl.fslot[p] < 0) continue;
-        const int Tb = (int)(gl - pl.leaf_base[p]);
-        if (Tb & 1) continue;                                   // pairs start at even boxes
-        const int m = o.mk[p];
-        const int nb0 = (m + B - 1) / B;
-        const int64_t g = pl.box_base[p] + Tb;
-        int nn[2];
-        bool own[2];
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int nnr = (Tb + h < nb0) ? pl.nnear[g + h] : -1;
-            own[h] = nnr >= 0 && nnr < SPLIT_NEAR;
-            nn[h] = own[h] ? nnr : 0;
-        }
-        const int k0 = Tb * B;
-        const int klo = own[0] ? k0 : k0 + B;
-        const int khi = own[1] ? min(k0 + 2 * B, m - 1) : (own[0] ? min(k0 + B, m - 1) : klo);
-        if (klo >= khi) continue;
-        const int64_t b0 = off[p];
-        const double *dk = o.dk + b0, *zk = o.zk + b0;
-        __syncwarp();
-        if (lane < nn[0]) lst[warp][0][lane] = pl.near[pl.nstart[g] + lane];
-        if (lane >= 16 && lane - 16 < nn[1]) lst[warp][1][lane - 16] = pl.near[pl.nstart[g + 1] + lane - 16];
-        __syncwarp();
-        if (lane == 0) {
-            // merge the two increasing lists into distinct staging slots
-            int i0 = 0, i1 = 0, nu = 0, t0 = 0, t1 = 0;
-            while (i0 < nn[0] || i1 < nn[1]) {
-                const int a = (i0 < nn[0]) ? lst[warp][0][i0] : 0x7fffffff;
-                const int b = (i1 < nn[1]) ? lst[warp][1][i1] : 0x7fffffff;
-                const int S = min(a, b);
-                const int c = min(B, m - S * B);
-                ubox[warp][nu] = S;
-                if (a == S) { lslot[warp][0][i0++] = nu; t0 += c; }
-                if (b == S) { lslot[warp][1][i1++] = nu; t1 += c; }
-                nu++;
-            }
-            s_nu[warp] = nu;
-            s_nterm[warp][0] = t0;
-            s_nterm[warp][1] = t1;
-        }
-        __syncwarp();
-        const int nu = s_nu[warp];
-        for (int u = 0; u < nu; u++) {
-            const int S = ubox[warp][u];
-            const int j = S * B + lane;
-            if (j < m) {
-                sd[warp][u * B + lane] = dk[j];
-                const double z = zk[j];
-                sw[warp][u * B + lane] = z * z;
-            }
-        }
-        __syncwarp();
-        const double W = o.wsum[p];
-        const double tol = stop_c * (double)m * SDC_EPS;
-        double cB[2] = {0.0, 0.0}, ihB[2] = {1.0, 1.0};
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            if (!own[h]) continue;
-            double hT;
-            box_ch(pl.blo[g + h], pl.bhi[g + h], cB[h], hT);
-            ihB[h] = 1.0 / hT;
-        }
-        int k = klo + lane;
-        bool act = k < khi;
-        int next = klo + 32;
-        Root R;
-        R.dK = 0.0; R.y = 1.0; R.phase = 1;
-        if (act) R.init(dk, zk, k, m, W);
-        while (__any_sync(FULL, act)) {
-            const bool p0 = __all_sync(FULL, !act || R.phase == 0);
-            const int h = (act && k - k0 >= B) ? 1 : 0;
-            const int Tl = Tb + h;
-            const int nl = act ? nn[h] : 0;
-            const int nmax = __reduce_max_sync(FULL, (unsigned)nl);
-            if (terms) {
-                const unsigned nt = __reduce_add_sync(FULL, act ? (unsigned)s_nterm[warp][h] : 0u);
-                if (lane == 0) atomicAdd(terms, (unsigned long long)nt);
-            }
-            Acc A = {0.0, 0.0, 0.0, 0.0};
-            if (act) {
-                // far field of the lane's box at the plain position x = d_K + y
-                const double *cf = pl.coef + (gl + h) * pl.nfield * P;
-                const double uu = ((R.dK + R.y) - (h ? cB[1] : cB[0])) * (h ? ihB[1] : ihB[0]);
-                const double u2 = uu + uu;
-                double a1 = 0, a2 = 0, b1 = 0, b2 = 0, c1 = 0, c2 = 0, e1 = 0, e2 = 0;
-                for (int n = P - 1; n >= 1; n--) {
-                    double t;
-                    t = fma(u2, a1, cf[n] - a2);         a2 = a1; a1 = t;
-                    t = fma(u2, b1, cf[P + n] - b2);     b2 = b1; b1 = t;
-                    t = fma(u2, c1, cf[2 * P + n] - c2); c2 = c1; c1 = t;
-                    t = fma(u2, e1, cf[3 * P + n] - e2); e2 = e1; e1 = t;
-                }
-                A.psi = fma(uu, a1, cf[0] - a2);
-                A.phi = fma(uu, b1, cf[P] - b2);
-                A.dpsi = fma(uu, c1, cf[2 * P] - c2);
-                A.dphi = fma(uu, e1, cf[3 * P] - e2);
-            }
-            for (int i = 0; i < nmax; i++) {
-                const bool on = i < nl;
-                int slot = 0, cnt = 0, kk = -1;
-                if (on) {
-                    slot = lslot[warp][h][i];
-                    const int S = ubox[warp][slot];
-                    cnt = min(B, m - S * B);
-                    kk = (S < Tl) ? B : ((S > Tl) ? -1 : k - Tl * B);
-                }
-                const int kwlo = __reduce_min_sync(FULL, on ? kk : 0x7fffffff);
-                const int kwhi = __reduce_max_sync(FULL, on ? kk : -1);
-                const double *bd = sd[warp] + slot * B, *bw = sw[warp] + slot * B;
-                if (p0) sweep_cnt<false>(bd, bw, B, cnt, kk, kwlo, kwhi, R.dK, R.y, A);
-                else    sweep_cnt<true>(bd, bw, B, cnt, kk, kwlo, kwhi, R.dK, R.y, A);
-            }
-            bool fin = false;
-            if (act && R.update(A, tol, max_iter, o.status)) {
-                o.org[b0 + k] = R.K;
-                o.eta[b0 + k] = R.y;
-                o.dorg[b0 + k] = R.dK;
-                o.lamk[b0 + k] = R.dK + R.y;
-                if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
-                fin = true;
-            }
-            const unsigned mask = __ballot_sync(FULL, fin);
-            if (fin) {
-                k = next + __popc(mask & ((1u << lane) - 1u));
-                act = k < khi;
-                if (act) R.init(dk, zk, k, m, W);
-            }
-            next += __popc(mask);
-        }
-    }
-    // launched as a programmatic dependent of k_secular_last (see k_secular_fmm)
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
@@ -1743,12 +1548,8 @@ superdc_status secular(const FmmPlan &pl, const int64_t *off, const R1Out &o, do
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        if (PAIRED && B == 32)
-            PROF_LAUNCH("fmm_secular", st, SDC_CHECK(cudaLaunchKernelEx(&cfg, k_secular_fmm_pair, pl.dv, off, o,
-                                                                        stop_c, max_iter, terms)));
-        else
-            PROF_LAUNCH("fmm_secular", st, SDC_CHECK(cudaLaunchKernelEx(&cfg, k_secular_fmm, pl.dv, off, o, stop_c,
-                                                                        max_iter, terms)));
+        PROF_LAUNCH("fmm_secular", st, SDC_CHECK(cudaLaunchKernelEx(&cfg, k_secular_fmm, pl.dv, off, o, stop_c,
+                                                                    max_iter, terms)));
     }
     PROF_LAUNCH("fmm_secular", st, (k_secular_fmm_split<8><<<fmm_grid(), 256, 0, st>>>(pl.dv, off, o, stop_c,
                                                                                       max_iter, terms)));

@@ -1,9 +1,9 @@
 """GPU parity of the triangular FMM path (opts.fmm_min_m; Sections 4.1.2,
 4.2.2, 4.3) against the CPU oracle and against the direct tiled evaluator.
 
-The FMM replaces far-field sums by Chebyshev expansions (order 24, boxes of
-64 indices, admissible when the gap is at least the larger box width), whose
-relative error is ~1e-14 per far box: well below the stopping tolerance of
+The FMM replaces far-field sums by Chebyshev expansions (order 22, boxes of
+32 or 64 indices, admissible when the gap is at least the larger box width),
+whose relative error is ~1e-14 per far box: well below the stopping tolerance of
 eq. (4.12), so roots, zhat and b keep the direct path's tolerances against
 the oracle."""
 import numpy as np
