@@ -291,7 +291,7 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
         // boxes of 32 halve the near field; with many columns the translations
         // (P^2 per column and box pair) dominate and boxes of 64 halve those
         superdc_status fs = fmm_plan(fp, f.nprob, f.off, total, f.max_m, f.mk, f.dk, f.fmm_min_m, w, w, nullptr,
-                                     (w <= 24) ? 32 : 64, st);
+                                     (w <= 24) ? 32 : 64, 0, st);
         if (fs != SUPERDC_OK) { fmm_free(fp, st); cudaFreeAsync(tile_off, st); return fs; }
     }
     const int32_t *fslot = fp.on ? fp.dv.fslot : nullptr;

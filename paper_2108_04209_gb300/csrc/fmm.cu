@@ -5,7 +5,7 @@
 namespace fmm_b32 {
 superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
                     const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,
-                    cudaStream_t st);
+                    int kslots, cudaStream_t st);
 void free_plan(FmmPlan &pl, cudaStream_t st);
 superdc_status secular(const FmmPlan &pl, const int64_t *off, const R1Out &o, double stop_c, int max_iter,
                        cudaStream_t st);
@@ -17,7 +17,7 @@ superdc_status cauchy(const FmmPlan &pl, const FactorView &f, const double *X, i
 namespace fmm_b64 {
 superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
                     const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,
-                    cudaStream_t st);
+                    int kslots, cudaStream_t st);
 void free_plan(FmmPlan &pl, cudaStream_t st);
 superdc_status secular(const FmmPlan &pl, const int64_t *off, const R1Out &o, double stop_c, int max_iter,
                        cudaStream_t st);
@@ -36,10 +36,12 @@ int fmm_default_min_m() { return 1024; }
 
 superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
                         const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,
-                        int box, cudaStream_t st)
+                        int box, int kslots, cudaStream_t st)
 {
-    if (box == 64) return fmm_b64::plan(pl, nprob, off, total, max_m, mk, dk, min_m, ncol, nfield, used, st);
-    if (box == 32) return fmm_b32::plan(pl, nprob, off, total, max_m, mk, dk, min_m, ncol, nfield, used, st);
+    if (box == 64)
+        return fmm_b64::plan(pl, nprob, off, total, max_m, mk, dk, min_m, ncol, nfield, used, kslots, st);
+    if (box == 32)
+        return fmm_b32::plan(pl, nprob, off, total, max_m, mk, dk, min_m, ncol, nfield, used, kslots, st);
     return SUPERDC_ERR_ARG;
 }
 

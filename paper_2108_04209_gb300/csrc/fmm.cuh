@@ -30,6 +30,9 @@ struct FmmDev {
     double *F;                             // workspace: far field at every box's nodes
     double *lastp;                         // workspace: per leaf box (ncol wide), its sources' share of
                                            // the sums for the last eigenvalue (outside the tree)
+    double *kmat;                          // per box, its first kslots interaction pairs: the P x P
+    int kslots;                            // matrix 1/(s_q2 - t_q) of nodes (M2L kernel, shared by
+                                           // the far fields built on one plan)
     const int64_t *lev_off;                // per level: prefix of the FMM problems' box counts
     int64_t cap_f;                         // capacity of the FMM problem list
     int ncol, nfield;                      // workspace widths
@@ -51,9 +54,11 @@ struct FmmPlan {
 // used (may be NULL): per problem 1 if it takes the FMM path, else 0.
 // box: indices per leaf box, 32 or 64 (smaller boxes halve the near field,
 // larger ones halve the number of box pairs whose expansions are translated).
+// kslots: M2L kernel matrices kept per box for the later far fields of the
+// same plan (0: none).
 superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
                         const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,
-                        int box, cudaStream_t st);
+                        int box, int kslots, cudaStream_t st);
 void fmm_free(FmmPlan &pl, cudaStream_t st);
 
 // Roots of the FMM problems (same outputs as the direct secular kernel).

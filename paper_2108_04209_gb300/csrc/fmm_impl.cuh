@@ -567,7 +567,10 @@ __global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__res
 enum { K_SEC = 0, K_1 = 1, K_2 = 2, K_1N = 3, K_LOG = 4 };
 
 template <int KER>
-__global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__restrict__ mk, int nw)
+// kmode: 0 evaluate the kernel matrices, 1 evaluate and keep the first
+// kslots of every box (kmat), 2 read those back (the same enumeration of
+// pairs: the plan's tree and near lists do not change between far fields)
+__global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__restrict__ mk, int nw, int kmode)
 {
     constexpr int NT = 128;
     constexpr int RMAX = (P * WMAX + NT - 1) / NT;
@@ -606,6 +609,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
             const double loT = pl.blo[g], hiT = pl.bhi[g];
             const int nbl = lev_nb(nb0, l);
             const int npn = pl.nnear[gPT];
+            int js = 0;                                   // index of the pair in T's interaction list
             for (int i = 0; i < npn; i++) {
                 const int s = pl.near[pl.nstart[gPT] + i];
                 for (int S = 2 * s; S <= 2 * s + 1 && S < nbl; S++) {
@@ -620,18 +624,23 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                     for (int t = tid; t < P * nw; t += NT) Ws[t / nw][t % nw] = pl.W[(gS * P + t / nw) * pl.ncol + t % nw];
                     if (tid < P) sq[tid] = cS + hS * xq[tid];
                     __syncthreads();
+                    const bool kept = js < pl.kslots;
+                    double *km = kept ? pl.kmat + ((g * pl.kslots + js) * P) * P : nullptr;
+                    js++;
                     for (int t = tid; t < P * P; t += NT) {
                         const int q = t / P, q2 = t % P;
-                        const double diff = sq[q2] - tq[q];
-                        if (KER == K_LOG) {
-                            K1[q][q2] = -rcp_nr2(diff);          // d/dt log|s - t| = 1/(t - s)
+                        double r;                                // 1/(s - t)
+                        if (kmode == 2 && kept) {
+                            r = km[t];
                         } else {
-                            const double r = rcp_nr2(diff);
-                            if (KER == K_SEC) { K1[q][q2] = r; K2[q][q2] = r * r; }
-                            else if (KER == K_1) K1[q][q2] = r;
-                            else if (KER == K_1N) K1[q][q2] = -r;
-                            else K1[q][q2] = r * r;
+                            r = rcp_nr2(sq[q2] - tq[q]);
+                            if (kmode == 1 && kept) km[t] = r;
                         }
+                        if (KER == K_LOG) K1[q][q2] = -r;        // d/dt log|s - t| = 1/(t - s)
+                        else if (KER == K_SEC) { K1[q][q2] = r; K2[q][q2] = r * r; }
+                        else if (KER == K_1) K1[q][q2] = r;
+                        else if (KER == K_1N) K1[q][q2] = -r;
+                        else K1[q][q2] = r * r;
                     }
                     __syncthreads();
                     if (KER == K_LOG && tid < 32) {
@@ -1421,14 +1430,15 @@ SrcArgs src_from_r1(const int64_t *off, const R1Out &o)
 }
 
 template <int MODE, int KER>
-superdc_status far_field(const FmmPlan &pl, const SrcArgs &a, int nw, cudaStream_t st)
+superdc_status far_field(const FmmPlan &pl, const SrcArgs &a, int nw, int kmode, cudaStream_t st)
 {
     const unsigned g = fmm_grid();
     const int nf = (KER == K_SEC) ? 4 : nw;
     PROF_LAUNCH("fmm_mom", st, k_fmm_leafmom<MODE><<<g, B, 0, st>>>(pl.dv, a));
     for (int l = 1; l < pl.lmax; l++)
         PROF_LAUNCH("fmm_m2m", st, k_fmm_m2m<<<lev_grid(pl, l), 128, 0, st>>>(pl.dv, a.mk, l, nw));
-    PROF_LAUNCH("fmm_m2l", st, k_fmm_m2l<KER><<<g, 128, 0, st>>>(pl.dv, a.mk, nw));
+    PROF_LAUNCH("fmm_m2l", st, k_fmm_m2l<KER><<<g, 128, 0, st>>>(pl.dv, a.mk, nw,
+                                                                  pl.dv.kslots > 0 ? kmode : 0));
     for (int l = pl.lmax - 2; l >= 0; l--)
         PROF_LAUNCH("fmm_l2l", st, k_fmm_l2l<<<lev_grid(pl, l), 128, 0, st>>>(pl.dv, a.mk, l, nf));
     return SUPERDC_OK;
@@ -1453,7 +1463,7 @@ void launch_cn(const FmmPlan &pl, const FactorView &f, const double *X, int64_t 
 
 superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
                         const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,
-                        cudaStream_t st)
+                        int kslots, cudaStream_t st)
 {
     pl = FmmPlan();
     pl.box = B;
@@ -1500,6 +1510,12 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     SDC_CHECK(al(&d.coef, (size_t)pl.cap_leaves * nfield * P));
     SDC_CHECK(al(&d.F, (size_t)pl.cap_boxes * P * nfield));
     SDC_CHECK(al(&d.lastp, (size_t)pl.cap_leaves * ncol));
+    // kernel matrices kept for the later far fields of this plan, if they fit
+    // a few GB (otherwise every far field evaluates its own)
+    const double kbytes = (double)pl.cap_boxes * kslots * P * P * sizeof(double);
+    d.kslots = (kslots > 0 && kbytes <= 8.0e9) ? kslots : 0;
+    d.kmat = nullptr;
+    if (d.kslots > 0) SDC_CHECK(al(&d.kmat, (size_t)pl.cap_boxes * d.kslots * P * P));
     int64_t *lev_off;
     SDC_CHECK(al(&lev_off, (size_t)pl.lmax * (nf_cap + 1)));
     d.lev_off = lev_off;
@@ -1529,7 +1545,7 @@ superdc_status secular(const FmmPlan &pl, const int64_t *off, const R1Out &o, do
                            cudaStream_t st)
 {
     if (!pl.on) return SUPERDC_OK;
-    far_field<M_SEC, K_SEC>(pl, src_from_r1(off, o), 1, st);
+    far_field<M_SEC, K_SEC>(pl, src_from_r1(off, o), 1, 1, st);      // keeps the kernel matrices
     const unsigned gl = (unsigned)std::max<int64_t>(1, std::min<int64_t>(pl.cap_f, (int64_t)sdc_num_sms() * 2));
     unsigned long long *terms = prof_counter("fmm_secular_terms");
     unsigned long long *lterms = prof_counter("fmm_secular_last_terms");
@@ -1560,7 +1576,7 @@ superdc_status secular(const FmmPlan &pl, const int64_t *off, const R1Out &o, do
 superdc_status lowner(const FmmPlan &pl, const int64_t *off, const R1Out &o, cudaStream_t st)
 {
     if (!pl.on) return SUPERDC_OK;
-    far_field<M_LOW, K_LOG>(pl, src_from_r1(off, o), 1, st);
+    far_field<M_LOW, K_LOG>(pl, src_from_r1(off, o), 1, 2, st);      // reads them
     PROF_LAUNCH("fmm_lowner", st, k_lowner_fmm<<<fmm_grid(), B, 0, st>>>(pl.dv, off, o));
     SDC_CHECK(cudaGetLastError());
     return SUPERDC_OK;
@@ -1569,7 +1585,7 @@ superdc_status lowner(const FmmPlan &pl, const int64_t *off, const R1Out &o, cud
 superdc_status bnorm(const FmmPlan &pl, const int64_t *off, const R1Out &o, cudaStream_t st)
 {
     if (!pl.on) return SUPERDC_OK;
-    far_field<M_BN, K_2>(pl, src_from_r1(off, o), 1, st);
+    far_field<M_BN, K_2>(pl, src_from_r1(off, o), 1, 2, st);
     PROF_LAUNCH("fmm_bnorm", st, k_bnorm_fmm<<<fmm_grid(), B, 0, st>>>(pl.dv, off, o));
     PROF_LAUNCH("fmm_bnorm", st, k_fmm_lastsum<0><<<lastsum_grid(pl, 1), 128, 0, st>>>(
                                      pl.dv, off, o.mk, o.bnorm, nullptr, nullptr, nullptr, 0, 0, 1));
@@ -1585,8 +1601,8 @@ superdc_status cauchy(const FmmPlan &pl, const FactorView &f, const double *X, i
     SrcArgs a{};
     a.off = f.off; a.mk = f.mk; a.dk = f.dk; a.vhat = f.vhat; a.bnorm = f.bnorm; a.dorg = f.dorg; a.eta = f.eta;
     a.src = f.src; a.pinv = f.pinv; a.X = X; a.ldx = ldx; a.col0 = col0; a.nc = nc;
-    if (trans) far_field<M_CT, K_1>(pl, a, nc, st);
-    else far_field<M_CN, K_1N>(pl, a, nc, st);
+    if (trans) far_field<M_CT, K_1>(pl, a, nc, 0, st);
+    else far_field<M_CN, K_1N>(pl, a, nc, 0, st);
     typedef void (*Fn)(const FmmPlan &, const FactorView &, const double *, int64_t, double *, int64_t, int, int,
                        cudaStream_t);
     Fn fn;

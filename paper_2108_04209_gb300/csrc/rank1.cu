@@ -767,7 +767,7 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     {
         // boxes of 32: the secular sweeps repeat the near field every iteration
         superdc_status fs = fmm_plan(fp, a.nprob, a.off, a.total, a.max_m, a.o.mk, a.o.dk, a.fmm_min_m, 1, 4,
-                                     a.o.fmm_used, 32, st);
+                                     a.o.fmm_used, 32, 3, st);
         if (fs != SUPERDC_OK) { fmm_free(fp, st); return fs; }
     }
     const int32_t *fslot = fp.on ? fp.dv.fslot : nullptr;
