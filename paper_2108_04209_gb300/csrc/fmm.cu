@@ -28,11 +28,13 @@ superdc_status cauchy(const FmmPlan &pl, const FactorView &f, const double *X, i
 }
 
 // measured on GB300 (python -m paper_2108_04209_gb300.crossover: batches of
-// equal-size rank-one problems, whole step direct vs FMM): at m = 512 the FMM
-// is 1.2x faster with 4096 problems but 2x slower with 256 (fixed costs), from
-// m = 1024 it wins for every batch (2.4x at 1024, 6x at 2048, 100x at 131072);
-// the autotuner refines the threshold per batch
-int fmm_default_min_m() { return 1024; }
+// equal-size rank-one problems, whole step direct vs FMM): at m = 256 few
+// problems keep enough poles for the tree and the direct path is 10 % faster;
+// at m = 512 the FMM step is 1.4x faster (4096 problems), at 1024 2.6x, at
+// 2048 7x; in the n = 131072 eigendecomposition (256 problems of 512 on that
+// level) the threshold 512 beats 1024 and 256.  The autotuner refines it per
+// batch.
+int fmm_default_min_m() { return 512; }
 
 superdc_status fmm_plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t total, int64_t max_m,
                         const int32_t *mk, const double *dk, int min_m, int ncol, int nfield, int32_t *used,

@@ -379,8 +379,9 @@ __global__ void __launch_bounds__(B) k_fmm_leafmom(FmmDev pl, SrcArgs a)
             // D_{n+1} = 2 delta T_n(b) + 2 a D_n - D_{n-1} (no cancellation)
             double av = 0.0, dl = 0.0;
             if (act) {
-                av = (a.dk[b0 + j] - c) / h;
-                dl = ((a.dorg[b0 + j] - a.dk[b0 + j]) + a.eta[b0 + j]) / h;
+                const double ih = 1.0 / h;
+                av = (a.dk[b0 + j] - c) * ih;
+                dl = ((a.dorg[b0 + j] - a.dk[b0 + j]) + a.eta[b0 + j]) * ih;
             }
             const double bv = av + dl;
             double tb0 = 1.0, tb1 = bv, D0 = 0.0, D1 = dl;
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(B) k_fmm_leafmom(FmmDev pl, SrcArgs a)
             const int qn = t / nw, q = t % nw;
             double s = Ms[0][q];
             for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
-            pl.W[(g * P + qn) * pl.ncol + q] = s / P;
+            pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
         }
     }
 }
@@ -508,8 +509,12 @@ __global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__res
         int64_t p, g;
         int nb0, b;
         if (!level_box(pl, mk, l, u, p, nb0, b, g)) continue;
-        double cP, hP;
-        box_ch(pl.blo[g], pl.bhi[g], cP, hP);
+        double cP = 0.0, ihP = 1.0;
+        if (tid < 2 * P) {                 // the warps that build Tv (uniform FP64 work costs every warp)
+            double hP;
+            box_ch(pl.blo[g], pl.bhi[g], cP, hP);
+            ihP = 1.0 / hP;
+        }
         const int nbc = lev_nb(nb0, l - 1);
         const int64_t gcb = pl.box_base[p] + lev_base(nb0, l - 1);
         const int nch = (2 * b + 1 < nbc) ? 2 : 1;
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__res
             const int64_t gc = gcb + 2 * b + ci;
             double cc, hc;
             box_ch(pl.blo[gc], pl.bhi[gc], cc, hc);
-            const double v = (cc + hc * xq[q] - cP) / hP;
+            const double v = (cc + hc * xq[q] - cP) * ihP;
             double t0 = 1.0, t1 = v;
             Tv[ci][q][0] = 1.0;
             Tv[ci][q][1] = v;
@@ -550,7 +555,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__res
             const int qn = t / nw, q = t % nw;
             double s = Ms[0][q];
             for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
-            pl.W[(g * P + qn) * pl.ncol + q] = s / P;
+            pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
         }
     }
 }
@@ -579,8 +584,10 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
     __shared__ double Ws[P][WMAX + 1];
     __shared__ double K1[P][P + 1];
     __shared__ double K2[(KER == K_SEC) ? P : 1][P + 1];
-    __shared__ double Fp[P], An[P + 2], s_f0;
+    __shared__ double Fp[P], An[P + 2], Bk[P + 1], hk[P + 1], s_f0;
+    __shared__ int s_list[32], s_nlist;
     cheb_tables(xq, Tx);
+    if (KER == K_LOG && threadIdx.x >= 1 && threadIdx.x <= P) hk[threadIdx.x] = 0.5 / threadIdx.x;   // 1 / (2k)
     const int nf = (KER == K_SEC) ? 4 : nw;
     const int tid = threadIdx.x;
     const int64_t nbox = pl.box_base[pl.nprob];
@@ -600,29 +607,47 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
         double accL = 0.0, accR = 0.0;   // K_SEC: thread t < 2P, node t % P, kernel 1/(s-t)^(1 + t/P),
                                          // sums of the boxes to the left / right
         if (l < L - 1 && pl.nnear[g] >= 0) {
-            double cT, hT;
-            box_ch(pl.blo[g], pl.bhi[g], cT, hT);
+            // FP64 instructions cost a warp slot of the FP64 pipe even when every
+            // lane computes the same value, so the box geometry and the
+            // admissibility tests run once, in warp 0 (lane-parallel over the
+            // candidates), not in every warp
+            double cT = 0.0, hT = 1.0;
+            if (tid < 32) box_ch(pl.blo[g], pl.bhi[g], cT, hT);
             __syncthreads();
             if (tid < P) tq[tid] = cT + hT * xq[tid];
             const int64_t gbl = pl.box_base[p] + lev_base(nb0, l);
             const int64_t gPT = pl.box_base[p] + lev_base(nb0, l + 1) + (Tb >> 1);
-            const double loT = pl.blo[g], hiT = pl.bhi[g];
             const int nbl = lev_nb(nb0, l);
             const int npn = pl.nnear[gPT];
+            const int64_t pst = pl.nstart[gPT];
             int js = 0;                                   // index of the pair in T's interaction list
-            for (int i = 0; i < npn; i++) {
-                const int s = pl.near[pl.nstart[gPT] + i];
-                for (int S = 2 * s; S <= 2 * s + 1 && S < nbl; S++) {
-                    if (S == Tb) continue;
-                    const int64_t gS = gbl + S;
-                    const double loS = pl.blo[gS], hiS = pl.bhi[gS];
-                    if (!adm(loS, hiS, loT, hiT)) continue;
+            for (int c0 = 0; c0 < 2 * npn; c0 += 32) {
+                // candidates c0 .. c0+31: children of the parent's near boxes, in list order
+                if (tid < 32) {
+                    const int c = c0 + tid;
+                    int S = -1;
+                    bool ok = false;
+                    if (c < 2 * npn) {
+                        S = 2 * pl.near[pst + (c >> 1)] + (c & 1);
+                        ok = S < nbl && S != Tb && adm(pl.blo[gbl + S], pl.bhi[gbl + S], pl.blo[g], pl.bhi[g]);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                    if (ok) s_list[__popc(bal & ((1u << tid) - 1u))] = S;
+                    if (tid == 0) s_nlist = __popc(bal);
+                }
+                __syncthreads();
+                const int nlist = s_nlist;
+                for (int ii = 0; ii < nlist; ii++) {
+                    const int S = s_list[ii];
                     const bool left = S < Tb;
-                    double cS, hS;
-                    box_ch(loS, hiS, cS, hS);
-                    __syncthreads();
+                    const int64_t gS = gbl + S;
+                    if (ii > 0) __syncthreads();
                     for (int t = tid; t < P * nw; t += NT) Ws[t / nw][t % nw] = pl.W[(gS * P + t / nw) * pl.ncol + t % nw];
-                    if (tid < P) sq[tid] = cS + hS * xq[tid];
+                    if (tid < P) {
+                        double cS, hS;
+                        box_ch(pl.blo[gS], pl.bhi[gS], cS, hS);
+                        sq[tid] = cS + hS * xq[tid];
+                    }
                     __syncthreads();
                     const bool kept = js < pl.kslots;
                     double *km = kept ? pl.kmat + ((g * pl.kslots + js) * P) * P : nullptr;
@@ -671,30 +696,33 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                         }
                     }
                 }
+                __syncthreads();        // s_list, Ws and the kernel blocks are reused
             }
             if (KER == K_LOG) {
                 // F' at the nodes (thread q holds it) -> Chebyshev coefficients,
                 // integrated exactly in coefficient space; F = F(centre) +
                 // h (G(x_q) - G(0)) with G the antiderivative in u
-                __syncthreads();
                 if (tid < P) Fp[tid] = acc[0];
                 if (tid == 0) s_f0 = f0;
                 __syncthreads();
                 if (tid < P) {
                     double a = 0.0;
                     for (int q = 0; q < P; q++) a = fma(Fp[q], Tx[q * P + tid], a);
-                    An[tid] = a * ((tid == 0) ? 1.0 : 2.0) / P;
+                    An[tid] = a * ((tid == 0) ? (1.0 / P) : (2.0 / P));
                 }
                 if (tid == 0) { An[P] = 0.0; An[P + 1] = 0.0; }
+                __syncthreads();
+                // antiderivative coefficients b_k, k = 1..P, once (thread k)
+                if (tid >= 1 && tid <= P) {
+                    const int k = tid;
+                    Bk[k] = (k == 1) ? 0.5 * (2.0 * An[0] - An[2]) : (An[k - 1] - An[k + 1]) * hk[k];
+                }
                 __syncthreads();
                 if (tid < P) {
                     // the degree-P term vanishes at the first-kind nodes but not at 0
                     double gq = 0.0, g0 = 0.0;
-                    for (int k = 1; k <= P; k++) {
-                        const double bk = (k == 1) ? 0.5 * (2.0 * An[0] - An[2]) : (An[k - 1] - An[k + 1]) / (2.0 * k);
-                        if (k < P) gq = fma(bk, Tx[tid * P + k], gq);
-                        if ((k & 1) == 0) g0 += ((k & 2) ? -bk : bk);      // T_k(0) = (-1)^(k/2)
-                    }
+                    for (int k = 1; k < P; k++) gq = fma(Bk[k], Tx[tid * P + k], gq);
+                    for (int k = 2; k <= P; k += 2) g0 += (k & 2) ? -Bk[k] : Bk[k];      // T_k(0) = (-1)^(k/2)
                     acc[0] = s_f0 + hT * (gq - g0);
                 }
             }
@@ -742,10 +770,10 @@ __global__ void __launch_bounds__(128) k_fmm_l2l(FmmDev pl, const int32_t *__res
         if (!alln) {
             // parent's Chebyshev coefficients
             for (int t = tid; t < P * nf; t += blockDim.x) Fs[t / nf][t % nf] = pl.F[(gP * P + t / nf) * pl.nfield + t % nf];
-            double cP, hP, cT, hT;
-            box_ch(pl.blo[gP], pl.bhi[gP], cP, hP);
-            box_ch(pl.blo[g], pl.bhi[g], cT, hT);
             if (tid < P) {
+                double cP, hP, cT, hT;
+                box_ch(pl.blo[gP], pl.bhi[gP], cP, hP);
+                box_ch(pl.blo[g], pl.bhi[g], cT, hT);
                 const double v = (cT + hT * xq[tid] - cP) / hP;
                 double t0 = 1.0, t1 = v;
                 Tv[tid][0] = 1.0;
@@ -761,7 +789,7 @@ __global__ void __launch_bounds__(128) k_fmm_l2l(FmmDev pl, const int32_t *__res
                 const int n = t / nf, f = t % nf;
                 double s = 0.0;
                 for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
-                Ac[n][f] = s * ((n == 0) ? 1.0 : 2.0) / P;
+                Ac[n][f] = s * ((n == 0) ? (1.0 / P) : (2.0 / P));
             }
             __syncthreads();
             for (int t = tid; t < P * nf; t += blockDim.x) {
@@ -782,7 +810,7 @@ __global__ void __launch_bounds__(128) k_fmm_l2l(FmmDev pl, const int32_t *__res
                 const int n = t / nf, f = t % nf;
                 double s = 0.0;
                 for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
-                pl.coef[(gl * pl.nfield + f) * P + n] = s * ((n == 0) ? 1.0 : 2.0) / P;
+                pl.coef[(gl * pl.nfield + f) * P + n] = s * ((n == 0) ? (1.0 / P) : (2.0 / P));
             }
         }
     }
@@ -894,10 +922,6 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
             next += __popc(mask);
         }
     }
-    // launched as a programmatic dependent of k_secular_last (independent
-    // roots, so the two overlap): finish only after it has finished, so that
-    // later work in the stream sees its results
-    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Leaf boxes with long near lists (SPLIT_NEAR boxes or more, or "all near"),
@@ -1016,8 +1040,6 @@ k_secular_last(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
     __shared__ int s_done, s_p0;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // k_secular_fmm (the other roots) may start at once
-    asm volatile("griddepcontrol.launch_dependents;");
     const int nf = *pl.nfmm;
     for (int f = blockIdx.x; f < nf; f += gridDim.x) {
         const int64_t p = pl.fprob[f];
@@ -1551,22 +1573,8 @@ superdc_status secular(const FmmPlan &pl, const int64_t *off, const R1Out &o, do
     unsigned long long *lterms = prof_counter("fmm_secular_last_terms");
     PROF_LAUNCH("fmm_secular_last", st, k_secular_last<<<gl, SL_T, 0, st>>>(pl.dv, off, o, stop_c, max_iter,
                                                                              lterms));
-    {
-        // programmatic dependent launch: overlaps k_secular_last (a few CTAs
-        // walking all m poles per sweep) instead of running after it
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(fmm_grid());
-        cfg.blockDim = dim3(64);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        PROF_LAUNCH("fmm_secular", st, SDC_CHECK(cudaLaunchKernelEx(&cfg, k_secular_fmm, pl.dv, off, o, stop_c,
-                                                                    max_iter, terms)));
-    }
+    PROF_LAUNCH("fmm_secular", st, k_secular_fmm<<<fmm_grid(), 64, 0, st>>>(pl.dv, off, o, stop_c, max_iter,
+                                                                             terms));
     PROF_LAUNCH("fmm_secular", st, (k_secular_fmm_split<8><<<fmm_grid(), 256, 0, st>>>(pl.dv, off, o, stop_c,
                                                                                       max_iter, terms)));
     SDC_CHECK(cudaGetLastError());
