@@ -15,6 +15,14 @@
 constexpr int FMM_P = 22;      // Chebyshev nodes (expansion order) per box
 constexpr int FMM_NPOOL = 24;  // near-list pool entries per box (average; lists have any length)
 
+// State of a secular root handed from the per-box sweep kernel to the tail
+// pass (the box's last few unconverged roots).
+struct FmmTail {
+    int64_t p;                             // problem
+    int32_t k, K, phase, nsw;              // root index, origin, iteration state
+    double dK, y, lo, hi;
+};
+
 // Device view of a plan: which problems of the batch use the FMM and their
 // box trees (index-based binary tree over the kept poles, near lists from the
 // geometric admissibility test).
@@ -30,6 +38,8 @@ struct FmmDev {
     double *F;                             // workspace: far field at every box's nodes
     double *lastp;                         // workspace: per leaf box (ncol wide), its sources' share of
                                            // the sums for the last eigenvalue (outside the tree)
+    FmmTail *tail;                         // roots left to the tail pass (capacity: every kept root)
+    unsigned int *ntail;                   // their count
     double *kmat;                          // per box, its first kslots interaction pairs: the P x P
     int kslots;                            // matrix 1/(s_q2 - t_q) of nodes (M2L kernel, shared by
                                            // the far fields built on one plan)

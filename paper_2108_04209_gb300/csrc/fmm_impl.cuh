@@ -59,6 +59,7 @@ constexpr int P = FMM_P;
 constexpr int B = FMM_BOX;
 constexpr double FMM_KAPPA = 1.0;
 constexpr int SPLIT_NEAR = 8;     // leaf boxes with this many near boxes or more: CTA-split secular sweeps
+constexpr int TAIL_X = 12;        // k_secular_fmm hands a box's last roots to the tail pass below this many busy lanes
 constexpr int WMAX = 32;          // widest moment / coefficient block (columns)
 
 // ---------------------------------------------------------------------------
@@ -920,6 +921,113 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
                 if (act) R.init(dk, zk, k, m, W);
             }
             next += __popc(mask);
+            // no root left to refill and fewer than TAIL_X lanes busy: the
+            // stragglers go to k_secular_tail, which runs 32 of them per warp
+            if (next >= kend) {
+                const unsigned am = __ballot_sync(FULL, act);
+                const int nact = __popc(am);
+                if (nact > 0 && nact < TAIL_X) {
+                    unsigned base = 0;
+                    if (lane == 0) base = atomicAdd(pl.ntail, (unsigned)nact);
+                    base = __shfl_sync(FULL, base, 0);
+                    if (act) {
+                        FmmTail tr;
+                        tr.p = p; tr.k = k; tr.K = R.K; tr.phase = R.phase; tr.nsw = R.nsw;
+                        tr.dK = R.dK; tr.y = R.y; tr.lo = R.lo; tr.hi = R.hi;
+                        pl.tail[base + __popc(am & ((1u << lane) - 1u))] = tr;
+                    }
+                    break;
+                }
+            }
+        }
+    }
+}
+
+// The stragglers of k_secular_fmm: one root per lane, each lane walking its
+// own box's near list (poles read through L1) and its own box's far field.
+// A root's arithmetic is the same sequence as in k_secular_fmm (near boxes in
+// list order, poles in index order, the same split by index), so its result
+// does not depend on which kernel finishes it.
+__global__ void __launch_bounds__(128)
+k_secular_tail(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
+               unsigned long long *terms)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = *pl.ntail;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nwarp * 32) {
+        const int64_t it = base + lane;
+        bool act = it < n;
+        Root R;
+        R.dK = 0.0; R.y = 1.0; R.phase = 1; R.k = 0;
+        int64_t b0 = 0, g = 0, gl = 0;
+        int m = 1, nnr = 0, nn = 0;
+        unsigned nterm = 0;
+        double cT = 0.0, ihT = 1.0, tol = 0.0;
+        if (act) {
+            const FmmTail tr = pl.tail[it];
+            const int64_t p = tr.p;
+            b0 = off[p];
+            m = o.mk[p];
+            R.init(o.dk + b0, o.zk + b0, tr.k, m, o.wsum[p]);
+            R.K = tr.K; R.phase = tr.phase; R.nsw = tr.nsw;
+            R.dK = tr.dK; R.y = tr.y; R.lo = tr.lo; R.hi = tr.hi;
+            const int Tb = tr.k / B;
+            g = pl.box_base[p] + Tb;
+            gl = pl.leaf_base[p] + Tb;
+            nnr = pl.nnear[g];
+            nn = near_len(nnr, (m + B - 1) / B);
+            for (int i = 0; i < nn; i++) nterm += min(B, m - near_box(pl, g, nnr, i) * B);
+            double hT;
+            box_ch(pl.blo[g], pl.bhi[g], cT, hT);
+            ihT = 1.0 / hT;
+            tol = stop_c * (double)m * SDC_EPS;
+        }
+        while (__any_sync(FULL, act)) {
+            if (terms) {
+                const unsigned nt = __reduce_add_sync(FULL, act ? nterm : 0u);
+                if (lane == 0) atomicAdd(terms, (unsigned long long)nt);
+            }
+            if (act) {
+                Acc A = {0.0, 0.0, 0.0, 0.0};
+                const double *cf = pl.coef + gl * pl.nfield * P;
+                const double uu = ((R.dK + R.y) - cT) * ihT;
+                const double u2 = uu + uu;
+                double a1 = 0, a2 = 0, b1 = 0, b2 = 0, c1 = 0, c2 = 0, e1 = 0, e2 = 0;
+                for (int q = P - 1; q >= 1; q--) {
+                    double t;
+                    t = fma(u2, a1, cf[q] - a2);         a2 = a1; a1 = t;
+                    t = fma(u2, b1, cf[P + q] - b2);     b2 = b1; b1 = t;
+                    t = fma(u2, c1, cf[2 * P + q] - c2); c2 = c1; c1 = t;
+                    t = fma(u2, e1, cf[3 * P + q] - e2); e2 = e1; e1 = t;
+                }
+                A.psi = fma(uu, a1, cf[0] - a2);
+                A.phi = fma(uu, b1, cf[P] - b2);
+                A.dpsi = fma(uu, c1, cf[2 * P] - c2);
+                A.dphi = fma(uu, e1, cf[3 * P] - e2);
+                for (int i = 0; i < nn; i++) {
+                    const int j0 = near_box(pl, g, nnr, i) * B;
+                    const int cnt = min(B, m - j0);
+                    const double *dd = o.dk + b0 + j0, *zz = o.zk + b0 + j0;
+                    for (int jj = 0; jj < cnt; jj++) {
+                        const double r = rcp_nr1(shifted_t(dd[jj], R.dK, R.y));
+                        const double z = zz[jj];
+                        const double a = (z * z) * r;
+                        if (j0 + jj <= R.k) { A.psi += a; A.dpsi = fma(a, r, A.dpsi); }
+                        else                { A.phi += a; A.dphi = fma(a, r, A.dphi); }
+                    }
+                }
+                if (R.update(A, tol, max_iter, o.status)) {
+                    const int k = R.k;
+                    o.org[b0 + k] = R.K;
+                    o.eta[b0 + k] = R.y;
+                    o.dorg[b0 + k] = R.dK;
+                    o.lamk[b0 + k] = R.dK + R.y;
+                    if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
+                    act = false;
+                }
+            }
         }
     }
 }
@@ -1532,6 +1640,9 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     SDC_CHECK(al(&d.coef, (size_t)pl.cap_leaves * nfield * P));
     SDC_CHECK(al(&d.F, (size_t)pl.cap_boxes * P * nfield));
     SDC_CHECK(al(&d.lastp, (size_t)pl.cap_leaves * ncol));
+    SDC_CHECK(al(&d.tail, (size_t)std::max<int64_t>(1, total)));
+    SDC_CHECK(al(&d.ntail, 1));
+    SDC_CHECK(cudaMemsetAsync(d.ntail, 0, sizeof(unsigned int), st));
     // kernel matrices kept for the later far fields of this plan, if they fit
     // a few GB (otherwise every far field evaluates its own)
     const double kbytes = (double)pl.cap_boxes * kslots * P * P * sizeof(double);
@@ -1575,6 +1686,8 @@ superdc_status secular(const FmmPlan &pl, const int64_t *off, const R1Out &o, do
                                                                              lterms));
     PROF_LAUNCH("fmm_secular", st, k_secular_fmm<<<fmm_grid(), 64, 0, st>>>(pl.dv, off, o, stop_c, max_iter,
                                                                              terms));
+    PROF_LAUNCH("fmm_secular", st, k_secular_tail<<<(unsigned)(sdc_num_sms() * 4), 128, 0, st>>>(
+                                       pl.dv, off, o, stop_c, max_iter, terms));
     PROF_LAUNCH("fmm_secular", st, (k_secular_fmm_split<8><<<fmm_grid(), 256, 0, st>>>(pl.dv, off, o, stop_c,
                                                                                       max_iter, terms)));
     SDC_CHECK(cudaGetLastError());
