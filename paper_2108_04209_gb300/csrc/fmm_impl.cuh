@@ -943,21 +943,25 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
     }
 }
 
-// The stragglers of k_secular_fmm: one root per lane, each lane walking its
-// own box's near list (poles read through L1) and its own box's far field.
-// A root's arithmetic is the same sequence as in k_secular_fmm (near boxes in
-// list order, poles in index order, the same split by index), so its result
-// does not depend on which kernel finishes it.
+// The stragglers of k_secular_fmm, eight per warp: four lanes per root, each
+// summing every fourth pole of each near box of the root's box (poles read
+// through L1), combined by a fixed butterfly; the root's far field and update
+// are computed by all four lanes alike.  Few stragglers per launch make this
+// pass latency-bound, hence the split of each root's sums over four lanes.
+constexpr int TAIL_LANES = 4;
+
 __global__ void __launch_bounds__(128)
 k_secular_tail(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
                unsigned long long *terms)
 {
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, part = lane & (TAIL_LANES - 1);
     const int64_t n = *pl.ntail;
+    const int per = 32 / TAIL_LANES;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nwarp * 32) {
-        const int64_t it = base + lane;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per; base < n;
+         base += nwarp * per) {
+        const int64_t it = base + lane / TAIL_LANES;
         bool act = it < n;
         Root R;
         R.dK = 0.0; R.y = 1.0; R.phase = 1; R.k = 0;
@@ -978,7 +982,8 @@ k_secular_tail(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
             gl = pl.leaf_base[p] + Tb;
             nnr = pl.nnear[g];
             nn = near_len(nnr, (m + B - 1) / B);
-            for (int i = 0; i < nn; i++) nterm += min(B, m - near_box(pl, g, nnr, i) * B);
+            if (part == 0)
+                for (int i = 0; i < nn; i++) nterm += min(B, m - near_box(pl, g, nnr, i) * B);
             double hT;
             box_ch(pl.blo[g], pl.bhi[g], cT, hT);
             ihT = 1.0 / hT;
@@ -989,8 +994,29 @@ k_secular_tail(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
                 const unsigned nt = __reduce_add_sync(FULL, act ? nterm : 0u);
                 if (lane == 0) atomicAdd(terms, (unsigned long long)nt);
             }
+            Acc A = {0.0, 0.0, 0.0, 0.0};
             if (act) {
-                Acc A = {0.0, 0.0, 0.0, 0.0};
+                for (int i = 0; i < nn; i++) {
+                    const int j0 = near_box(pl, g, nnr, i) * B;
+                    const int cnt = min(B, m - j0);
+                    const double *dd = o.dk + b0 + j0, *zz = o.zk + b0 + j0;
+                    for (int jj = part; jj < cnt; jj += TAIL_LANES) {
+                        const double r = rcp_nr1(shifted_t(dd[jj], R.dK, R.y));
+                        const double z = zz[jj];
+                        const double a = (z * z) * r;
+                        if (j0 + jj <= R.k) { A.psi += a; A.dpsi = fma(a, r, A.dpsi); }
+                        else                { A.phi += a; A.dphi = fma(a, r, A.dphi); }
+                    }
+                }
+            }
+            // the four lanes of a root are consecutive: butterfly over lane bits 0, 1
+            for (int sh = 1; sh < TAIL_LANES; sh <<= 1) {
+                A.psi += __shfl_xor_sync(FULL, A.psi, sh);
+                A.phi += __shfl_xor_sync(FULL, A.phi, sh);
+                A.dpsi += __shfl_xor_sync(FULL, A.dpsi, sh);
+                A.dphi += __shfl_xor_sync(FULL, A.dphi, sh);
+            }
+            if (act) {
                 const double *cf = pl.coef + gl * pl.nfield * P;
                 const double uu = ((R.dK + R.y) - cT) * ihT;
                 const double u2 = uu + uu;
@@ -1002,29 +1028,19 @@ k_secular_tail(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
                     t = fma(u2, c1, cf[2 * P + q] - c2); c2 = c1; c1 = t;
                     t = fma(u2, e1, cf[3 * P + q] - e2); e2 = e1; e1 = t;
                 }
-                A.psi = fma(uu, a1, cf[0] - a2);
-                A.phi = fma(uu, b1, cf[P] - b2);
-                A.dpsi = fma(uu, c1, cf[2 * P] - c2);
-                A.dphi = fma(uu, e1, cf[3 * P] - e2);
-                for (int i = 0; i < nn; i++) {
-                    const int j0 = near_box(pl, g, nnr, i) * B;
-                    const int cnt = min(B, m - j0);
-                    const double *dd = o.dk + b0 + j0, *zz = o.zk + b0 + j0;
-                    for (int jj = 0; jj < cnt; jj++) {
-                        const double r = rcp_nr1(shifted_t(dd[jj], R.dK, R.y));
-                        const double z = zz[jj];
-                        const double a = (z * z) * r;
-                        if (j0 + jj <= R.k) { A.psi += a; A.dpsi = fma(a, r, A.dpsi); }
-                        else                { A.phi += a; A.dphi = fma(a, r, A.dphi); }
-                    }
-                }
+                A.psi += fma(uu, a1, cf[0] - a2);
+                A.phi += fma(uu, b1, cf[P] - b2);
+                A.dpsi += fma(uu, c1, cf[2 * P] - c2);
+                A.dphi += fma(uu, e1, cf[3 * P] - e2);
                 if (R.update(A, tol, max_iter, o.status)) {
-                    const int k = R.k;
-                    o.org[b0 + k] = R.K;
-                    o.eta[b0 + k] = R.y;
-                    o.dorg[b0 + k] = R.dK;
-                    o.lamk[b0 + k] = R.dK + R.y;
-                    if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
+                    if (part == 0) {
+                        const int k = R.k;
+                        o.org[b0 + k] = R.K;
+                        o.eta[b0 + k] = R.y;
+                        o.dorg[b0 + k] = R.dK;
+                        o.lamk[b0 + k] = R.dK + R.y;
+                        if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
+                    }
                     act = false;
                 }
             }
