@@ -274,7 +274,7 @@ LaunchFn pick(bool trans, int nc)
 }
 
 superdc_status run(const FactorView &f, int64_t total, double *Xmut, const double *X, int64_t ldx, double *Y,
-                   int64_t ldy, int ncols, bool trans, cudaStream_t st)
+                   int64_t ldy, int ncols, bool trans, cudaStream_t st, const FmmPlan *shared)
 {
     if (ncols <= 0 || total <= 0) return SUPERDC_OK;
     const int nsm = sdc_num_sms();
@@ -286,22 +286,27 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
         PROF_LAUNCH("givens", st, k_givens<<<(unsigned)(nsm * 8), gthreads, 0, st>>>(f, total, Xmut, ldx, ncols, 0));
     // problems whose kept size reaches the threshold: triangular FMM
     FmmPlan fp;
-    {
-        const int w = std::min(32, ncols);
+    const int w = std::min(32, ncols);
+    const int box = (w <= 24) ? 32 : 64;
+    // the plan of this factor's rank-one step serves when its boxes and widths fit
+    const bool use_shared = shared && shared->on && shared->box == box && shared->dv.ncol >= w &&
+                            shared->dv.nfield >= w;
+    if (!use_shared) {
         // boxes of 32 halve the near field; with many columns the translations
         // (P^2 per column and box pair) dominate and boxes of 64 halve those
         superdc_status fs = fmm_plan(fp, f.nprob, f.off, total, f.max_m, f.mk, f.dk, f.fmm_min_m, w, w, nullptr,
-                                     (w <= 24) ? 32 : 64, 0, st);
+                                     box, 0, st);
         if (fs != SUPERDC_OK) { fmm_free(fp, st); cudaFreeAsync(tile_off, st); return fs; }
     }
-    const int32_t *fslot = fp.on ? fp.dv.fslot : nullptr;
+    const FmmPlan &pl = use_shared ? *shared : fp;
+    const int32_t *fslot = pl.on ? pl.dv.fslot : nullptr;
     superdc_status fs = SUPERDC_OK;
     const unsigned grid = (unsigned)(nsm * 4);
     for (int c0 = 0; c0 < ncols; c0 += 32) {
         const int c = min(32, ncols - c0);
         LaunchFn fn = pick(trans, pick_nc(c));
         PROF_LAUNCH("cauchy", st, fn(f, tile_off, X, ldx, Y, ldy, c0, ncols, grid, fslot, st));
-        if (fs == SUPERDC_OK) fs = fmm_cauchy(fp, f, X, ldx, Y, ldy, c0, c, trans, st);
+        if (fs == SUPERDC_OK) fs = fmm_cauchy(pl, f, X, ldx, Y, ldy, c0, c, trans, st);
     }
     PROF_LAUNCH("deflcopy", st, k_defl_copy<<<(unsigned)(nsm * 8), 256, 0, st>>>(f, total, X, ldx, Y, ldy, ncols,
                                                                                   trans ? 1 : 0));
@@ -316,13 +321,13 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
 }  // namespace
 
 superdc_status cauchy_apply_T(const FactorView &f, int64_t total, double *X, int64_t ldx, double *Y, int64_t ldy,
-                              int ncols, cudaStream_t st)
+                              int ncols, cudaStream_t st, const FmmPlan *plan)
 {
-    return run(f, total, X, X, ldx, Y, ldy, ncols, true, st);
+    return run(f, total, X, X, ldx, Y, ldy, ncols, true, st, plan);
 }
 
 superdc_status cauchy_apply_N(const FactorView &f, int64_t total, const double *X, int64_t ldx, double *Y,
                               int64_t ldy, int ncols, cudaStream_t st)
 {
-    return run(f, total, nullptr, X, ldx, Y, ldy, ncols, false, st);
+    return run(f, total, nullptr, X, ldx, Y, ldy, ncols, false, st, nullptr);
 }

@@ -18,11 +18,15 @@ struct FactorView {
     int64_t max_m = -1;      // upper bound on the problem sizes (-1: unknown)
 };
 
+struct FmmPlan;
+
 // Y = Qhat^T X.  X (rows in the step's input order) is overwritten by the
 // rotations; Y rows in merged order.  Column-major with leading dims ldx/ldy;
-// row r of problem p lives at off[p] + r.  ncols columns.
+// row r of problem p lives at off[p] + r.  ncols columns.  plan (may be NULL):
+// the FMM plan the rank-one step of this factor kept (R1Args::keep), used
+// instead of a new one when its boxes and widths fit.
 superdc_status cauchy_apply_T(const FactorView &f, int64_t total, double *X, int64_t ldx,
-                              double *Y, int64_t ldy, int ncols, cudaStream_t st);
+                              double *Y, int64_t ldy, int ncols, cudaStream_t st, const FmmPlan *plan = nullptr);
 
 // Y = Qhat X.  X rows in merged order (read only); Y rows in input order.
 superdc_status cauchy_apply_N(const FactorView &f, int64_t total, const double *X, int64_t ldx,

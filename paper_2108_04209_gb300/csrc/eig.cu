@@ -1057,9 +1057,13 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
                 a.o.giv_cs = S.giv_cs; a.o.mk = S.mk + q; a.o.ngiv = S.ngiv + q; a.o.sweeps = S.sweeps;
                 a.o.status = f->status; a.o.dorg = S.dorg; a.o.pinv = S.pinv; a.o.wsum = wsum + q;
                 a.o.fmm_used = S.fmm + q;
-                superdc_status s1 = r1_run(a, st);
-                if (s1 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s1; }
                 const int c = ctot - (j + 1);
+                // the step's FMM plan (tree, near lists, M2L kernel matrices)
+                // also serves the Cauchy-like update of the remaining columns
+                FmmPlan keep;
+                if (opts->batching && c > 0 && c <= 24) { a.keep = &keep; a.keep_width = c; }
+                superdc_status s1 = r1_run(a, st);
+                if (s1 != SUPERDC_OK) { fmm_free(keep, st); free_tmp(); superdc_eigfact_free(f); return s1; }
                 if (c > 0) {
                     FactorView v = view(f, l, j);
                     if (!opts->batching) {
@@ -1067,9 +1071,11 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
                         v.max_m = h->size[h->lev_nodes[l][q]];
                     }
                     superdc_status s2 = cauchy_apply_T(v, n, WK + (int64_t)(j + 1) * n, n,
-                                                       WK2 + (int64_t)(j + 1) * n, n, c, st);
-                    if (s2 != SUPERDC_OK) { free_tmp(); superdc_eigfact_free(f); return s2; }
+                                                       WK2 + (int64_t)(j + 1) * n, n, c, st,
+                                                       a.keep ? &keep : nullptr);
+                    if (s2 != SUPERDC_OK) { fmm_free(keep, st); free_tmp(); superdc_eigfact_free(f); return s2; }
                 }
+                fmm_free(keep, st);
             }
             if (ctot - (j + 1) > 0) std::swap(WK, WK2);
             std::swap(dcur, dnxt);

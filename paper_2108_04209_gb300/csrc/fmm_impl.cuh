@@ -1738,8 +1738,9 @@ superdc_status cauchy(const FmmPlan &pl, const FactorView &f, const double *X, i
     SrcArgs a{};
     a.off = f.off; a.mk = f.mk; a.dk = f.dk; a.vhat = f.vhat; a.bnorm = f.bnorm; a.dorg = f.dorg; a.eta = f.eta;
     a.src = f.src; a.pinv = f.pinv; a.X = X; a.ldx = ldx; a.col0 = col0; a.nc = nc;
-    if (trans) far_field<M_CT, K_1>(pl, a, nc, 0, st);
-    else far_field<M_CN, K_1N>(pl, a, nc, 0, st);
+    // a plan kept from the factor's rank-one step holds its M2L kernel matrices
+    if (trans) far_field<M_CT, K_1>(pl, a, nc, 2, st);
+    else far_field<M_CN, K_1N>(pl, a, nc, 2, st);
     typedef void (*Fn)(const FmmPlan &, const FactorView &, const double *, int64_t, double *, int64_t, int, int,
                        cudaStream_t);
     Fn fn;

@@ -766,8 +766,9 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     FmmPlan fp;
     {
         // boxes of 32: the secular sweeps repeat the near field every iteration
-        superdc_status fs = fmm_plan(fp, a.nprob, a.off, a.total, a.max_m, a.o.mk, a.o.dk, a.fmm_min_m, 1, 4,
-                                     a.o.fmm_used, 32, 3, st);
+        const int w = a.keep ? std::min(32, a.keep_width) : 0;
+        superdc_status fs = fmm_plan(fp, a.nprob, a.off, a.total, a.max_m, a.o.mk, a.o.dk, a.fmm_min_m,
+                                     std::max(1, w), std::max(4, w), a.o.fmm_used, 32, 3, st);
         if (fs != SUPERDC_OK) { fmm_free(fp, st); return fs; }
     }
     const int32_t *fslot = fp.on ? fp.dv.fslot : nullptr;
@@ -809,7 +810,8 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     SDC_CHECK(cudaFreeAsync(surv, st));
     SDC_CHECK(cudaFreeAsync(a.o.lamk, st));
     SDC_CHECK(cudaFreeAsync(ucount, st));
-    fmm_free(fp, st);
+    if (a.keep && fs == SUPERDC_OK) *a.keep = fp;
+    else fmm_free(fp, st);
     return fs;
 }
 

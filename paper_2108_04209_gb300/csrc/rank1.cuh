@@ -16,6 +16,8 @@ struct R1Out {
     int32_t *fmm_used = nullptr;   // per problem: 1 if it took the FMM path (may be NULL)
 };
 
+struct FmmPlan;
+
 struct R1Args {
     int64_t nprob, total;   // problems; extent of the row-indexed arrays (rows are absolute)
     int64_t rows = -1;      // rows covered by the problems (scheduling), -1 = total
@@ -26,6 +28,11 @@ struct R1Args {
     int sched = 0;          // 0 automatic, 1 whole problems per CTA (root pools per warp), 2 pole split
     int fmm_min_m = 0;      // kept size from which a problem takes the FMM path (0: direct only)
     int64_t max_m = -1;     // upper bound on the problem sizes (-1: unknown)
+    // keep (may be NULL): receives the step's FMM plan instead of freeing it,
+    // with workspaces keep_width columns wide, for a Cauchy-like application
+    // of the same factor (cauchy_apply_T with that plan); the caller frees it
+    FmmPlan *keep = nullptr;
+    int keep_width = 0;
     R1Out o;
 };
 
