@@ -39,7 +39,7 @@ struct FmmDev {
     double *lastp;                         // workspace: per leaf box (ncol wide), its sources' share of
                                            // the sums for the last eigenvalue (outside the tree)
     FmmTail *tail;                         // roots left to the tail pass (capacity: every kept root)
-    unsigned int *ntail;                   // their count
+    unsigned int *ntail;                   // their count, then the tail pass's next unclaimed entry
     double *kmat;                          // per box, its first kslots interaction pairs: the P x P
     int kslots;                            // matrix 1/(s_q2 - t_q) of nodes (M2L kernel, shared by
                                            // the far fields built on one plan)

@@ -943,11 +943,13 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
     }
 }
 
-// The stragglers of k_secular_fmm, eight per warp: four lanes per root, each
-// summing every fourth pole of each near box of the root's box (poles read
-// through L1), combined by a fixed butterfly; the root's far field and update
-// are computed by all four lanes alike.  Few stragglers per launch make this
-// pass latency-bound, hence the split of each root's sums over four lanes.
+// The stragglers of k_secular_fmm: four lanes per root, each summing every
+// fourth pole of each near box of the root's box (poles read through L1),
+// combined by a fixed butterfly; the root's far field and update are computed
+// by all four lanes alike.  The warps are persistent: a lane group whose root
+// has converged claims the next straggler (ntail[1]), so lanes do not wait for
+// the slowest root of a fixed batch.  A root's arithmetic does not depend on
+// which group runs it.
 constexpr int TAIL_LANES = 4;
 
 __global__ void __launch_bounds__(128)
@@ -955,94 +957,101 @@ k_secular_tail(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
                unsigned long long *terms)
 {
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, part = lane & (TAIL_LANES - 1);
-    const int64_t n = *pl.ntail;
-    const int per = 32 / TAIL_LANES;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * per; base < n;
-         base += nwarp * per) {
-        const int64_t it = base + lane / TAIL_LANES;
-        bool act = it < n;
-        Root R;
-        R.dK = 0.0; R.y = 1.0; R.phase = 1; R.k = 0;
-        int64_t b0 = 0, g = 0, gl = 0;
-        int m = 1, nnr = 0, nn = 0;
-        unsigned nterm = 0;
-        double cT = 0.0, ihT = 1.0, tol = 0.0;
-        if (act) {
-            const FmmTail tr = pl.tail[it];
-            const int64_t p = tr.p;
-            b0 = off[p];
-            m = o.mk[p];
-            R.init(o.dk + b0, o.zk + b0, tr.k, m, o.wsum[p]);
-            R.K = tr.K; R.phase = tr.phase; R.nsw = tr.nsw;
-            R.dK = tr.dK; R.y = tr.y; R.lo = tr.lo; R.hi = tr.hi;
-            const int Tb = tr.k / B;
-            g = pl.box_base[p] + Tb;
-            gl = pl.leaf_base[p] + Tb;
-            nnr = pl.nnear[g];
-            nn = near_len(nnr, (m + B - 1) / B);
-            if (part == 0)
-                for (int i = 0; i < nn; i++) nterm += min(B, m - near_box(pl, g, nnr, i) * B);
-            double hT;
-            box_ch(pl.blo[g], pl.bhi[g], cT, hT);
-            ihT = 1.0 / hT;
-            tol = stop_c * (double)m * SDC_EPS;
+    const int lane = threadIdx.x & 31, part = lane & (TAIL_LANES - 1), lead = lane & ~(TAIL_LANES - 1);
+    const unsigned n = pl.ntail[0];
+    unsigned *claim = pl.ntail + 1;
+    bool act = false, dry = false;
+    Root R;
+    R.dK = 0.0; R.y = 1.0; R.phase = 1; R.k = 0;
+    int64_t b0 = 0, g = 0, gl = 0;
+    int m = 1, nnr = 0, nn = 0;
+    unsigned nterm = 0;
+    double cT = 0.0, ihT = 1.0, tol = 0.0;
+    while (true) {
+        // groups without a root claim the next one (warp-wide shuffle of the claim)
+        const bool need = !act && !dry;
+        unsigned idx = 0;
+        if (need && part == 0) idx = atomicAdd(claim, 1u);
+        idx = __shfl_sync(FULL, idx, lead);
+        if (need) {
+            if (idx < n) {
+                const FmmTail tr = pl.tail[idx];
+                const int64_t p = tr.p;
+                b0 = off[p];
+                m = o.mk[p];
+                R.init(o.dk + b0, o.zk + b0, tr.k, m, o.wsum[p]);
+                R.K = tr.K; R.phase = tr.phase; R.nsw = tr.nsw;
+                R.dK = tr.dK; R.y = tr.y; R.lo = tr.lo; R.hi = tr.hi;
+                const int Tb = tr.k / B;
+                g = pl.box_base[p] + Tb;
+                gl = pl.leaf_base[p] + Tb;
+                nnr = pl.nnear[g];
+                nn = near_len(nnr, (m + B - 1) / B);
+                nterm = 0;
+                if (part == 0)
+                    for (int i = 0; i < nn; i++) nterm += min(B, m - near_box(pl, g, nnr, i) * B);
+                double hT;
+                box_ch(pl.blo[g], pl.bhi[g], cT, hT);
+                ihT = 1.0 / hT;
+                tol = stop_c * (double)m * SDC_EPS;
+                act = true;
+            } else {
+                dry = true;
+            }
         }
-        while (__any_sync(FULL, act)) {
-            if (terms) {
-                const unsigned nt = __reduce_add_sync(FULL, act ? nterm : 0u);
-                if (lane == 0) atomicAdd(terms, (unsigned long long)nt);
-            }
-            Acc A = {0.0, 0.0, 0.0, 0.0};
-            if (act) {
-                for (int i = 0; i < nn; i++) {
-                    const int j0 = near_box(pl, g, nnr, i) * B;
-                    const int cnt = min(B, m - j0);
-                    const double *dd = o.dk + b0 + j0, *zz = o.zk + b0 + j0;
-                    for (int jj = part; jj < cnt; jj += TAIL_LANES) {
-                        const double r = rcp_nr1(shifted_t(dd[jj], R.dK, R.y));
-                        const double z = zz[jj];
-                        const double a = (z * z) * r;
-                        if (j0 + jj <= R.k) { A.psi += a; A.dpsi = fma(a, r, A.dpsi); }
-                        else                { A.phi += a; A.dphi = fma(a, r, A.dphi); }
-                    }
+        if (!__any_sync(FULL, act)) break;
+        if (terms) {
+            const unsigned nt = __reduce_add_sync(FULL, act ? nterm : 0u);
+            if (lane == 0) atomicAdd(terms, (unsigned long long)nt);
+        }
+        Acc A = {0.0, 0.0, 0.0, 0.0};
+        if (act) {
+            for (int i = 0; i < nn; i++) {
+                const int j0 = near_box(pl, g, nnr, i) * B;
+                const int cnt = min(B, m - j0);
+                const double *dd = o.dk + b0 + j0, *zz = o.zk + b0 + j0;
+                for (int jj = part; jj < cnt; jj += TAIL_LANES) {
+                    const double r = rcp_nr1(shifted_t(dd[jj], R.dK, R.y));
+                    const double z = zz[jj];
+                    const double a = (z * z) * r;
+                    if (j0 + jj <= R.k) { A.psi += a; A.dpsi = fma(a, r, A.dpsi); }
+                    else                { A.phi += a; A.dphi = fma(a, r, A.dphi); }
                 }
             }
-            // the four lanes of a root are consecutive: butterfly over lane bits 0, 1
-            for (int sh = 1; sh < TAIL_LANES; sh <<= 1) {
-                A.psi += __shfl_xor_sync(FULL, A.psi, sh);
-                A.phi += __shfl_xor_sync(FULL, A.phi, sh);
-                A.dpsi += __shfl_xor_sync(FULL, A.dpsi, sh);
-                A.dphi += __shfl_xor_sync(FULL, A.dphi, sh);
+        }
+        // the four lanes of a root are consecutive: butterfly over lane bits 0, 1
+        for (int sh = 1; sh < TAIL_LANES; sh <<= 1) {
+            A.psi += __shfl_xor_sync(FULL, A.psi, sh);
+            A.phi += __shfl_xor_sync(FULL, A.phi, sh);
+            A.dpsi += __shfl_xor_sync(FULL, A.dpsi, sh);
+            A.dphi += __shfl_xor_sync(FULL, A.dphi, sh);
+        }
+        if (act) {
+            const double *cf = pl.coef + gl * pl.nfield * P;
+            const double uu = ((R.dK + R.y) - cT) * ihT;
+            const double u2 = uu + uu;
+            double a1 = 0, a2 = 0, b1 = 0, b2 = 0, c1 = 0, c2 = 0, e1 = 0, e2 = 0;
+            for (int q = P - 1; q >= 1; q--) {
+                double t;
+                t = fma(u2, a1, cf[q] - a2);         a2 = a1; a1 = t;
+                t = fma(u2, b1, cf[P + q] - b2);     b2 = b1; b1 = t;
+                t = fma(u2, c1, cf[2 * P + q] - c2); c2 = c1; c1 = t;
+                t = fma(u2, e1, cf[3 * P + q] - e2); e2 = e1; e1 = t;
             }
-            if (act) {
-                const double *cf = pl.coef + gl * pl.nfield * P;
-                const double uu = ((R.dK + R.y) - cT) * ihT;
-                const double u2 = uu + uu;
-                double a1 = 0, a2 = 0, b1 = 0, b2 = 0, c1 = 0, c2 = 0, e1 = 0, e2 = 0;
-                for (int q = P - 1; q >= 1; q--) {
-                    double t;
-                    t = fma(u2, a1, cf[q] - a2);         a2 = a1; a1 = t;
-                    t = fma(u2, b1, cf[P + q] - b2);     b2 = b1; b1 = t;
-                    t = fma(u2, c1, cf[2 * P + q] - c2); c2 = c1; c1 = t;
-                    t = fma(u2, e1, cf[3 * P + q] - e2); e2 = e1; e1 = t;
+            A.psi += fma(uu, a1, cf[0] - a2);
+            A.phi += fma(uu, b1, cf[P] - b2);
+            A.dpsi += fma(uu, c1, cf[2 * P] - c2);
+            A.dphi += fma(uu, e1, cf[3 * P] - e2);
+            if (R.update(A, tol, max_iter, o.status)) {
+                if (part == 0) {
+                    const int k = R.k;
+                    o.org[b0 + k] = R.K;
+                    o.eta[b0 + k] = R.y;
+                    o.dorg[b0 + k] = R.dK;
+                    o.lamk[b0 + k] = R.dK + R.y;
+                    if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
                 }
-                A.psi += fma(uu, a1, cf[0] - a2);
-                A.phi += fma(uu, b1, cf[P] - b2);
-                A.dpsi += fma(uu, c1, cf[2 * P] - c2);
-                A.dphi += fma(uu, e1, cf[3 * P] - e2);
-                if (R.update(A, tol, max_iter, o.status)) {
-                    if (part == 0) {
-                        const int k = R.k;
-                        o.org[b0 + k] = R.K;
-                        o.eta[b0 + k] = R.y;
-                        o.dorg[b0 + k] = R.dK;
-                        o.lamk[b0 + k] = R.dK + R.y;
-                        if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
-                    }
-                    act = false;
-                }
+                act = false;
             }
         }
     }
@@ -1657,8 +1666,8 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     SDC_CHECK(al(&d.F, (size_t)pl.cap_boxes * P * nfield));
     SDC_CHECK(al(&d.lastp, (size_t)pl.cap_leaves * ncol));
     SDC_CHECK(al(&d.tail, (size_t)std::max<int64_t>(1, total)));
-    SDC_CHECK(al(&d.ntail, 1));
-    SDC_CHECK(cudaMemsetAsync(d.ntail, 0, sizeof(unsigned int), st));
+    SDC_CHECK(al(&d.ntail, 2));
+    SDC_CHECK(cudaMemsetAsync(d.ntail, 0, 2 * sizeof(unsigned int), st));
     // kernel matrices kept for the later far fields of this plan, if they fit
     // a few GB (otherwise every far field evaluates its own)
     const double kbytes = (double)pl.cap_boxes * kslots * P * P * sizeof(double);
