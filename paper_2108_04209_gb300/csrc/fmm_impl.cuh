@@ -58,7 +58,7 @@ namespace {
 constexpr int P = FMM_P;
 constexpr int B = FMM_BOX;
 constexpr double FMM_KAPPA = 1.0;
-constexpr int SPLIT_NEAR = 8;     // leaf boxes with this many near boxes or more: CTA-split secular sweeps
+constexpr int SPLIT_NEAR = 512 / B;   // leaf boxes with this many near boxes (512 poles) or more: CTA-split sweeps
 constexpr int TAIL_X = 12;        // k_secular_fmm hands a box's last roots to the tail pass below this many busy lanes
 constexpr int WMAX = 32;          // widest moment / coefficient block (columns)
 
