@@ -1159,10 +1159,16 @@ k_secular_fmm_split(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double 
     }
 }
 
-// The last root of every FMM problem (in (d_{m-1}, d_{m-1} + sum w]): every
-// pole direct, split over a CTA; thread 0 holds the root state, the partial
-// sums are reduced in a fixed order.
+// The last root of every FMM problem (in (d_{m-1}, d_{m-1} + sum w]), one CTA
+// per problem: boxes at least their own width to the left of the bracket are
+// summed through their Chebyshev node weights at the plain position (far
+// field), the leaf boxes next to the bracket directly with shifted
+// differences; if the lists overflow, every pole directly.  Thread 0 holds
+// the root state, the partial sums are reduced in a fixed order.
 constexpr int SL_T = 256;
+
+constexpr int LAST_FAR = 112;     // boxes summed through their node weights for the last root
+constexpr int LAST_NEAR = 32;     // leaf boxes summed directly for it
 
 __global__ void __launch_bounds__(SL_T)
 k_secular_last(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
@@ -1171,8 +1177,13 @@ k_secular_last(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
     __shared__ double red[2][SL_T / 32];
     __shared__ double s_dK, s_y;
     __shared__ int s_done, s_p0;
+    __shared__ double xq[P];
+    __shared__ double fs[LAST_FAR * P], fw[LAST_FAR * P];      // far boxes: node positions, weights
+    __shared__ int64_t s_far[LAST_FAR];
+    __shared__ int s_near[LAST_NEAR], s_nfar, s_nnear, s_ok;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int q = tid; q < P; q += SL_T) xq[q] = cospi((double)(2 * q + 1) / (2.0 * P));
     const int nf = *pl.nfmm;
     for (int f = blockIdx.x; f < nf; f += gridDim.x) {
         const int64_t p = pl.fprob[f];
@@ -1186,18 +1197,86 @@ k_secular_last(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
         if (tid == 0) {
             R.init(dk, zk, m - 1, m, o.wsum[p]);
             s_dK = R.dK; s_y = R.y; s_done = 0; s_p0 = 1;
+            // every pole lies to the left of the root's bracket [d_{m-1}, d_{m-1} + W]:
+            // a box at least its own width away from the bracket is summed
+            // through its node weights (multipole to point), the leaf boxes
+            // next to it directly; walk the tree from the top
+            const int nb0 = (m + B - 1) / B;
+            const int L = lev_count(nb0);
+            const double tlo = dk[m - 1];
+            int nfar = 0, nnear = 0, ok = 1;
+            int cand[2 * LAST_NEAR], nc = 1, ncand[2 * LAST_NEAR];
+            cand[0] = 0;
+            for (int l = L - 1; l >= 0 && ok; l--) {
+                const int64_t gb = pl.box_base[p] + lev_base(nb0, l);
+                int nn2 = 0;
+                for (int i = 0; i < nc && ok; i++) {
+                    const int bx = cand[i];
+                    const double lo = pl.blo[gb + bx], hi = pl.bhi[gb + bx];
+                    if (tlo - hi >= FMM_KAPPA * (hi - lo) && hi > lo) {
+                        if (nfar < LAST_FAR) s_far[nfar++] = gb + bx; else ok = 0;
+                    } else if (l == 0) {
+                        if (nnear < LAST_NEAR) s_near[nnear++] = bx; else ok = 0;
+                    } else {
+                        const int nbc = lev_nb(nb0, l - 1);
+                        for (int c = 2 * bx; c <= 2 * bx + 1 && c < nbc; c++) {
+                            if (nn2 < 2 * LAST_NEAR) ncand[nn2++] = c; else ok = 0;
+                        }
+                    }
+                }
+                for (int i = 0; i < nn2; i++) cand[i] = ncand[i];
+                nc = nn2;
+            }
+            s_nfar = nfar; s_nnear = nnear; s_ok = ok;
         }
         __syncthreads();
+        const bool tree = s_ok != 0;
+        const int nfar = s_nfar, nnear = s_nnear;
+        int64_t nterms = m;
+        if (tree) {
+            for (int t = tid; t < nfar * P; t += SL_T) {
+                const int64_t g = s_far[t / P];
+                const int q = t % P;
+                double c, h;
+                box_ch(pl.blo[g], pl.bhi[g], c, h);
+                fs[t] = c + h * xq[q];
+                fw[t] = pl.W[(g * P + q) * pl.ncol];
+            }
+            nterms = (int64_t)nfar * P;
+            for (int i = 0; i < nnear; i++) nterms += min(B, m - s_near[i] * B);
+            __syncthreads();
+        }
         while (!s_done) {
             const double dK = s_dK, y = s_y;
             const bool p0 = s_p0 != 0;
             double ps = 0.0, dps = 0.0;
-            for (int j = tid; j < m; j += SL_T) {
-                const double r = rcp_nr1(shifted_t(dk[j], dK, y));
-                const double z = zk[j];
-                const double a = (z * z) * r;
-                ps += a;
-                if (!p0) dps = fma(a, r, dps);
+            if (tree) {
+                // far boxes at the plain position x = d_K + y (local shifting)
+                const double x = dK + y;
+                for (int t = tid; t < nfar * P; t += SL_T) {
+                    const double r = rcp_nr1(fs[t] - x);
+                    const double a = fw[t] * r;
+                    ps += a;
+                    if (!p0) dps = fma(a, r, dps);
+                }
+                for (int i = 0; i < nnear; i++) {
+                    const int j0 = s_near[i] * B, cnt = min(B, m - j0);
+                    for (int jj = tid; jj < cnt; jj += SL_T) {
+                        const double r = rcp_nr1(shifted_t(dk[j0 + jj], dK, y));
+                        const double z = zk[j0 + jj];
+                        const double a = (z * z) * r;
+                        ps += a;
+                        if (!p0) dps = fma(a, r, dps);
+                    }
+                }
+            } else {
+                for (int j = tid; j < m; j += SL_T) {
+                    const double r = rcp_nr1(shifted_t(dk[j], dK, y));
+                    const double z = zk[j];
+                    const double a = (z * z) * r;
+                    ps += a;
+                    if (!p0) dps = fma(a, r, dps);
+                }
             }
             for (int sh = 16; sh > 0; sh >>= 1) {
                 ps += __shfl_down_sync(FULL, ps, sh);
@@ -1209,7 +1288,7 @@ k_secular_last(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
                 Acc A = {0.0, 0.0, 0.0, 0.0};
                 for (int w = 0; w < SL_T / 32; w++) { A.psi += red[0][w]; A.dpsi += red[1][w]; }
                 const bool fin = R.update(A, tol, max_iter, o.status);
-                if (terms) atomicAdd(terms, (unsigned long long)m);
+                if (terms) atomicAdd(terms, (unsigned long long)nterms);
                 s_dK = R.dK; s_y = R.y; s_p0 = (R.phase == 0); s_done = fin;
                 if (fin) {
                     const int k = m - 1;
