@@ -189,8 +189,9 @@ constexpr int LEAF_T = 256;
 // on (d, e).  A QL sweep is one chain of dependent scalar steps, and on this
 // GPU a scalar FP64 chain is slow, so the chains run in parallel:
 //   large leaves (one CTA per SM): k_leaf_ql runs one leaf per lane and
-//                 records every sweep's rotations; k_leaf_out applies them to
-//                 the rows of Q (each row independently);
+//                 records every sweep's rotations; k_leaf_rot applies them to
+//                 the rows of Q (each row independently, a leaf's rows split
+//                 over several CTAs), k_leaf_out sorts and emits;
 //   small leaves: k_leaf_qlcta, in each leaf's CTA, thread 0 computes one
 //                 sweep while the other warps apply the previous one, and
 //                 several CTAs share an SM.
@@ -439,30 +440,34 @@ __device__ void leaf_emit(int L, int r, int64_t n, int m, const double *A, int l
     }
 }
 
-__global__ void __launch_bounds__(LEAF_T)
-k_leaf_out(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
-           const int64_t *__restrict__ leaf_uoff, const double *__restrict__ U, double *__restrict__ Qleaf,
-           const int64_t *__restrict__ qoff, const double *__restrict__ dd, const double2 *__restrict__ rot,
-           const int2 *__restrict__ hdr, const int32_t *__restrict__ nsw, int64_t cap, int caps,
-           double *__restrict__ lam, double *__restrict__ W, int32_t *status)
+// Rows [y * LEAF_R, ...) of every leaf's Q get the recorded rotations, one
+// thread per row (rows are independent): rotation q of a sweep acts on columns
+// (i, i+1), i = first - q, and the entry at i + 1 is final after it (carry
+// form).  A leaf's Q (128 x 129 doubles) fills the shared memory of an SM, so
+// its rows are split over several CTAs, several of which share an SM.
+constexpr int LEAF_R = 32;
+
+__global__ void __launch_bounds__(LEAF_R)
+k_leaf_rot(const int64_t *__restrict__ leaf_m, double *__restrict__ Qleaf, const int64_t *__restrict__ qoff,
+           const double2 *__restrict__ rot, const int2 *__restrict__ hdr, const int32_t *__restrict__ nsw,
+           int64_t cap, int caps)
 {
     extern __shared__ double sm[];
-    __shared__ int rank[128];
     const int L = blockIdx.x;
     const int m = (int)leaf_m[L];
+    const int r0 = blockIdx.y * LEAF_R;
+    if (r0 >= m) return;
+    const int nr = min(LEAF_R, m - r0);
     const int lda = m | 1;
-    double *A = sm;
+    double *Q = Qleaf + qoff[L] + (int64_t)r0 * m;
     const int tid = threadIdx.x;
-    double *Q = Qleaf + qoff[L];
-    for (int e = tid; e < m * m; e += LEAF_T) A[(e / m) * lda + (e % m)] = Q[e];
+    for (int e = tid; e < nr * m; e += LEAF_R) sm[(e / m) * lda + (e % m)] = Q[e];
     __syncthreads();
-    // every row independently: rotation q of a sweep acts on columns (i, i+1),
-    // i = first - q; the entry at i + 1 is final after it (carry form)
-    const double2 *R = rot + (int64_t)L * cap;
-    const int2 *Hd = hdr + (int64_t)L * caps;
-    const int ns = nsw[L];
-    for (int row = tid; row < m; row += LEAF_T) {
-        double *qr = A + row * lda;
+    if (tid < nr) {
+        const double2 *R = rot + (int64_t)L * cap;
+        const int2 *Hd = hdr + (int64_t)L * caps;
+        const int ns = nsw[L];
+        double *qr = sm + tid * lda;
         int64_t k = 0;
         for (int t = 0; t < ns; t++) {
             const int2 h = Hd[t];
@@ -479,6 +484,26 @@ k_leaf_out(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t
             k += cnt;
         }
     }
+    __syncthreads();
+    for (int e = tid; e < nr * m; e += LEAF_R) Q[e] = sm[(e / m) * lda + (e % m)];
+}
+
+// Q (rotations applied) to the outputs: see leaf_emit
+__global__ void __launch_bounds__(LEAF_T)
+k_leaf_out(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
+           const int64_t *__restrict__ leaf_uoff, const double *__restrict__ U, double *__restrict__ Qleaf,
+           const int64_t *__restrict__ qoff, const double *__restrict__ dd, double *__restrict__ lam,
+           double *__restrict__ W, int32_t *status)
+{
+    extern __shared__ double sm[];
+    __shared__ int rank[128];
+    const int L = blockIdx.x;
+    const int m = (int)leaf_m[L];
+    const int lda = m | 1;
+    double *A = sm;
+    const int tid = threadIdx.x;
+    double *Q = Qleaf + qoff[L];
+    for (int e = tid; e < m * m; e += LEAF_T) A[(e / m) * lda + (e % m)] = Q[e];
     __syncthreads();
     leaf_emit(L, r, n, m, A, lda, dd + leaf_off[L], leaf_off, leaf_uoff, U, Q, lam, W, status, rank);
 }
@@ -1007,9 +1032,13 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
             EIG_CHECK(cudaFuncSetAttribute(k_leaf_out, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
             PROF_LAUNCH("leaf", st, k_leaf_ql<<<(unsigned)((h->nleaves + 31) / 32), 32, smem2, st>>>(
                 h->nleaves, (int)mm, h->d_leaf_off, h->d_leaf_m, dq, eq, rot, hdr, nsw, cap, (int)caps, f->status));
+            const size_t smem5 = (size_t)LEAF_R * (mm | 1) * sizeof(double);
+            PROF_LAUNCH("leaf", st, k_leaf_rot<<<dim3((unsigned)h->nleaves, (unsigned)((mm + LEAF_R - 1) / LEAF_R)),
+                                                 LEAF_R, smem5, st>>>(h->d_leaf_m, f->Qleaf, f->d_qoff, rot, hdr, nsw,
+                                                                      cap, (int)caps));
             PROF_LAUNCH("leaf", st, k_leaf_out<<<(unsigned)h->nleaves, LEAF_T, smem3, st>>>(
-                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, dq, rot, hdr, nsw, cap,
-                (int)caps, lamA, Wp, f->status));
+                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, dq, lamA, Wp,
+                f->status));
         } else {
             const size_t smem4 = (mm * (mm | 1) + 4 * mm) * sizeof(double);
             EIG_CHECK(cudaFuncSetAttribute(k_leaf_qlcta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
