@@ -41,14 +41,23 @@ FMM_P = 22                              # Chebyshev order of the FMM expansions
 FMM_FAR_FLOPS = 4 * (FMM_P - 1) * 3     # per root and sweep: four Clenshaw sums (fma + sub per step)
 
 
-def _profiled(name, src):
-    """Numbers of a committed ncu summary, if it was taken on the current kernel source."""
+def _code_sha1(text):
+    """sha1 of a C/CUDA source without its comments and blank space (the code
+    the counters were taken on, unchanged by edits to comments)."""
     import hashlib
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [ln for ln in (re.sub(r"//.*$", "", ln).strip() for ln in text.splitlines()) if ln]
+    return hashlib.sha1("\n".join(lines).encode()).hexdigest()
+
+
+def _profiled(name, src):
+    """Numbers of a committed ncu summary, if it was taken on the current kernel code."""
     import re
     try:
         txt = open(os.path.join(ROOT, "profiles", name)).read()
-        sha = hashlib.sha1(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
-        if ("sha1: %s" % sha) not in txt:
+        code = _code_sha1(open(os.path.join(ROOT, src)).read())
+        if ("code sha1: %s" % code) not in txt:
             return None
         return {k: float(v) for k, v in re.findall(r"^(\w+): ([0-9.]+)$", txt, re.M)}
     except OSError:

@@ -3,9 +3,9 @@
 // Geometry.  The kept poles d_0 < ... < d_{m-1} of a problem and the targets
 // (roots x_k in (d_k, d_{k+1}), eigenvalues lambda_j, or the poles themselves)
 // interlace (eq. (4.4)), so one index-based binary tree serves both: a leaf
-// box holds B consecutive indices (32 or 64:
-// this file is compiled once per box size, fmm32.cu and fmm64.cu) (d_k and x_k of the same k always share
-// a box, the paper's first design point) and every box carries the interval
+// box holds B consecutive indices (32 or 64; this file is compiled once per
+// box size, fmm32.cu and fmm64.cu), so d_k and x_k of the same k always share
+// a box (the paper's first design point), and every box carries the interval
 // [d_{i0}, d_{i1}] of its points (the last box ends at d_{m-1}).  The index
 // split adapts the boxes to clustered spectra (second design point); whether
 // two boxes interact through expansions is decided geometrically: boxes S, T
@@ -14,14 +14,17 @@
 // list that are not admissible) and have any length (a wide box, e.g. in a
 // tail of the spectrum, is close to many boxes; its narrow children are not).
 // Only when the list pool is exhausted is a box marked "all near", with its
-// subtree: the targets of such leaves are summed directly over every source.  Only the last eigenvalue
-// lambda_{m-1} lies outside the tree (to the right of d_{m-1}): as a target it
-// is summed directly, as a source it is added directly to every target.
+// subtree: the targets of such leaves are summed directly over every source.
+// Only the last eigenvalue lambda_{m-1} lies outside the tree (to the right of
+// d_{m-1}): as a target its sums run over the tree (node weights of the boxes
+// far from it, direct sums over the leaf boxes next to it) or are spread over
+// the leaf boxes; as a source it is added directly to every target.
 //
 // Expansions.  Chebyshev interpolation with FMM_P first-kind nodes per box:
 // source moments M_n = sum_j w_j T_n(u_j) of the leaf boxes, node weights
 // W_q = sum_j w_j L_q(u_j) from the moments, parents' moments exactly from
-// the children's weights (T_n(alpha u + beta) has degree n < P; upward pass); every box
+// the children's weights (T_n(alpha u + beta) has degree n < P; upward
+// pass); every box
 // receives the kernel sums of its interaction list (children of its parent's
 // near list that are admissible to it) at its own Chebyshev nodes (M2L), the
 // parents' fields are interpolated down the tree (L2L), and on the leaves the
@@ -818,13 +821,14 @@ __global__ void __launch_bounds__(128) k_fmm_l2l(FmmDev pl, const int32_t *__res
 }
 
 // ---------------------------------------------------------------------------
-// Secular roots of the FMM problems, one warp per leaf box: a lane takes the
-// next root of the box when its root has converged (the box's roots share
-// the near list).  The near boxes' poles and weights (fixed during the
-// iteration) are staged in shared memory once per box; each sweep sums them
-// with shifted differences and evaluates the four far-field expansions at
-// x = d_K + y.  The last root of each problem (outside the tree) is solved
-// by k_secular_last.
+// Secular roots of the FMM problems, one warp per leaf box: with boxes of 64
+// a lane takes the next root of the box when its root has converged (the
+// box's roots share the near list).  The near boxes' poles and weights (fixed
+// during the iteration) are staged in shared memory once per box; each sweep
+// sums them with shifted differences and evaluates the four far-field
+// expansions at x = d_K + y.  Once no root is left to hand out and fewer than
+// TAIL_X lanes are busy, the box's stragglers go to k_secular_tail.  The last
+// root of each problem (outside the tree) is solved by k_secular_last.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(64)
 k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c, int max_iter,
