@@ -208,6 +208,7 @@ k_leaf_tri(int r, const int64_t *__restrict__ leaf_off, const int64_t *__restric
     extern __shared__ double sm[];
     __shared__ double dg[128], ee[128], hh[128];
     __shared__ double red[LEAF_T / 32];
+    __shared__ double s_ih;
     const int L = blockIdx.x;
     const int m = (int)leaf_m[L];
     const int lda = m | 1;
@@ -260,18 +261,19 @@ k_leaf_tri(int r, const int64_t *__restrict__ leaf_off, const int64_t *__restric
         const double g = (f >= 0.0) ? -sqrt(full) : sqrt(full);
         const double h = full - f * g;                       // = ||u||^2 / 2
         __syncthreads();
-        if (tid == 0) { ee[i] = g; hh[i] = h; A[i * lda + l] = f - g; }
+        if (tid == 0) { ee[i] = g; hh[i] = h; s_ih = 1.0 / h; A[i * lda + l] = f - g; }
         __syncthreads();
+        const double ih = s_ih;
         // p = A u / h on the leading (l+1) x (l+1) block, u = A[i][0..l]
         double up = 0;
         for (int j = tid; j <= l; j += LEAF_T) {
             double s = 0;
             for (int k = 0; k <= l; k++) s += A[j * lda + k] * A[i * lda + k];
-            const double pj = s / h;
+            const double pj = s * ih;
             dg[j] = pj;                                      // p kept in dg until the reduction ends
             up += A[i * lda + j] * pj;
         }
-        const double K = bsum(up) / (2.0 * h);
+        const double K = bsum(up) * (0.5 * ih);
         for (int j = tid; j <= l; j += LEAF_T) dg[j] -= K * A[i * lda + j];   // q = p - K u
         __syncthreads();
         for (int e2 = tid; e2 < (l + 1) * (l + 1); e2 += LEAF_T) {
@@ -279,7 +281,7 @@ k_leaf_tri(int r, const int64_t *__restrict__ leaf_off, const int64_t *__restric
             A[j * lda + k] -= A[i * lda + j] * dg[k] + dg[j] * A[i * lda + k];
         }
         __syncthreads();
-        for (int j = tid; j <= l; j += LEAF_T) A[j * lda + i] = A[i * lda + j] / h;   // u / h in column i
+        for (int j = tid; j <= l; j += LEAF_T) A[j * lda + i] = A[i * lda + j] * ih;  // u / h in column i
         __syncthreads();
     }
     // diagonal of the tridiagonal matrix, then the orthogonal factor in place
@@ -321,11 +323,30 @@ k_leaf_tri(int r, const int64_t *__restrict__ leaf_off, const int64_t *__restric
 // Newton steps y <- y + y (1 - q y^2) / 2 (relative error 2^-22 -> 2^-44 ->
 // below one ulp), which replaces a square root and a division in the chain of
 // dependent operations; elsewhere hypot and one division.
+// q^(-1/2) to about 2^-22 for a normal q > 0: the FP32 approximate reciprocal
+// square root of the leading mantissa bits (scaled into [1, 4) to make the
+// exponent even), the exponent halved by integer arithmetic; no conversion
+// between FP64 and FP32 in the chain of dependent steps
+__device__ __forceinline__ double rsqrt_seed(double q)
+{
+    const int hi = __double2hiint(q);
+    const unsigned lo = (unsigned)__double2loint(q);
+    const int e = ((hi >> 20) & 0x7FF) - 1023;
+    const int odd = e & 1;
+    const unsigned mb = (((unsigned)hi & 0xFFFFFu) << 3) | (lo >> 29);
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__uint_as_float(((unsigned)(127 + odd) << 23) | mb)));
+    const unsigned rb = __float_as_uint(r);                  // in (0.5, 1]
+    const int E = (int)(rb >> 23) - 127 - (e - odd) / 2 + 1023;
+    const unsigned rm = rb & 0x7FFFFFu;
+    return __hiloint2double((int)(((unsigned)E << 20) | (rm >> 3)), (int)(rm << 29));
+}
+
 __device__ __forceinline__ void ql_pair(double f, double g, double &c, double &s, double &rr)
 {
     const double q = fma(f, f, g * g);
     if (q > 1e-36 && q < 1e36) {
-        double y = (double)rsqrtf((float)q);
+        double y = rsqrt_seed(q);
         double e = fma(-q * y, y, 1.0);
         y = fma(0.5 * y, e, y);
         e = fma(-q * y, y, 1.0);
