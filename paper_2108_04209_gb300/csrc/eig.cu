@@ -49,52 +49,68 @@ cudaError_t dalloc(T **p, size_t n, std::vector<char *> *own)
 // ---------------------------------------------------------------------------
 __device__ void jacobi_small_maxeig(double *G, int r, double *out, double *V)
 {
-    // cyclic Jacobi on the r x r symmetric matrix G (column-major), one thread;
-    // V (r x r, may be NULL) accumulates the rotations; *out = largest eigenvalue,
-    // V's first column is overwritten with its eigenvector
+    // cyclic Jacobi on the r x r symmetric matrix G (column-major, shared
+    // memory), called by all 32 lanes of one warp (r <= 32): the rotation
+    // parameters are computed by every lane alike, the row, column and V
+    // updates one index per lane, the norms by lane 0 in the serial order, so
+    // every entry sees the same operations in the same order as in a one-thread
+    // sweep (a lone thread spent ~1 ms per node on these dependent chains).
+    // V (r x r, may be NULL) accumulates the rotations; *out = largest
+    // eigenvalue, V's first column is overwritten with its eigenvector
+    const unsigned FULL = 0xffffffffu;
+    const int k = threadIdx.x & 31;
     double fro = 0;
-    for (int i = 0; i < r * r; i++) fro += G[i] * G[i];
-    fro = sqrt(fro);
-    if (V) for (int i = 0; i < r * r; i++) V[i] = ((i % r) == (i / r)) ? 1.0 : 0.0;
+    if (k == 0) {
+        for (int i = 0; i < r * r; i++) fro += G[i] * G[i];
+        fro = sqrt(fro);
+    }
+    fro = __shfl_sync(FULL, fro, 0);
+    if (V && k < r)
+        for (int i = 0; i < r; i++) V[i + r * k] = (i == k) ? 1.0 : 0.0;
+    __syncwarp();
     for (int sw = 0; sw < 60; sw++) {
         double off = 0;
-        for (int j = 0; j < r; j++)
-            for (int i = 0; i < r; i++)
-                if (i != j) off += G[i + r * j] * G[i + r * j];
+        if (k == 0)
+            for (int j = 0; j < r; j++)
+                for (int i = 0; i < r; i++)
+                    if (i != j) off += G[i + r * j] * G[i + r * j];
+        off = __shfl_sync(FULL, off, 0);
         if (sqrt(off) <= SDC_EPS * fro) break;
         for (int p = 0; p < r - 1; p++)
             for (int q = p + 1; q < r; q++) {
-                double apq = G[p + r * q];
+                const double apq = G[p + r * q];
                 if (apq == 0.0) continue;
-                double app = G[p + r * p], aqq = G[q + r * q];
-                double zeta = (aqq - app) / (2.0 * apq);
-                double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                                                : ((zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)));
-                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                for (int k = 0; k < r; k++) {
-                    double gp = G[p + r * k], gq = G[q + r * k];
-                    G[p + r * k] = c * gp - s * gq;
-                    G[q + r * k] = s * gp + c * gq;
+                const double app = G[p + r * p], aqq = G[q + r * q];
+                const double zeta = (aqq - app) / (2.0 * apq);
+                const double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                                      : ((zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta)));
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                __syncwarp();
+                if (k < r) {
+                    const double gp = G[p + r * k], gq = G[q + r * k];
+                    G[p + r * k] = c * gp - sn * gq;
+                    G[q + r * k] = sn * gp + c * gq;
                 }
-                for (int k = 0; k < r; k++) {
-                    double gp = G[k + r * p], gq = G[k + r * q];
-                    G[k + r * p] = c * gp - s * gq;
-                    G[k + r * q] = s * gp + c * gq;
-                }
-                if (V)
-                    for (int k = 0; k < r; k++) {
-                        double vp = V[k + r * p], vq = V[k + r * q];
-                        V[k + r * p] = c * vp - s * vq;
-                        V[k + r * q] = s * vp + c * vq;
+                __syncwarp();
+                if (k < r) {
+                    const double gp = G[k + r * p], gq = G[k + r * q];
+                    G[k + r * p] = c * gp - sn * gq;
+                    G[k + r * q] = sn * gp + c * gq;
+                    if (V) {
+                        const double vp = V[k + r * p], vq = V[k + r * q];
+                        V[k + r * p] = c * vp - sn * vq;
+                        V[k + r * q] = sn * vp + c * vq;
                     }
+                }
+                __syncwarp();
             }
     }
     double mx = G[0];
     int im = 0;
     for (int i = 1; i < r; i++) if (G[i + r * i] > mx) { mx = G[i + r * i]; im = i; }
     *out = fmax(mx, 0.0);
-    if (V && im != 0)
-        for (int k = 0; k < r; k++) V[k] = V[k + r * im];
+    if (V && im != 0 && k < r) V[k] = V[k + r * im];
+    __syncwarp();
 }
 
 __global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, const int32_t *__restrict__ lch,
@@ -142,11 +158,13 @@ __global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, con
         G[e] = s;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double mx;
         jacobi_small_maxeig(G, r, &mx, Vg);
-        s_beta = sqrt(fmax(mx, 0.0));
-        if (!isfinite(s_beta)) sdc_latch(status, SUPERDC_DEV_NONFINITE);
+        if (threadIdx.x == 0) {
+            s_beta = sqrt(fmax(mx, 0.0));
+            if (!isfinite(s_beta)) sdc_latch(status, SUPERDC_DEV_NONFINITE);
+        }
     }
     __syncthreads();
     const double beta = s_beta;
