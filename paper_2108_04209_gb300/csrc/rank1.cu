@@ -497,6 +497,8 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
     __shared__ double sd[SEC_CHUNK];
     __shared__ double sw[SEC_CHUNK];
     __shared__ double red[SPLIT ? NW : 1][4][32];
+    __shared__ double s_dK[SPLIT ? 32 : 1], s_y[SPLIT ? 32 : 1];
+    __shared__ int s_ph[SPLIT ? 32 : 1], s_fin[SPLIT ? 32 : 1];
     __shared__ int s_unit;
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -558,27 +560,50 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
                     else    sweep<true>(sd, sw, j0, j1, c0, kk, kwlo, kwhi, R.dK, R.y, A);
                 }
             }
+            bool fin = false;
             if (SPLIT) {
+                // the warps hold the same roots: warp 0 alone reduces the partial
+                // sums (fixed order) and updates, the others take the new iterate
+                // (an FP64 instruction costs its pipe slot in every warp that runs it)
                 red[SPLIT ? warp : 0][0][lane] = A.psi;
                 red[SPLIT ? warp : 0][1][lane] = A.phi;
                 red[SPLIT ? warp : 0][2][lane] = A.dpsi;
                 red[SPLIT ? warp : 0][3][lane] = A.dphi;
                 __syncthreads();
-                Acc T = {0.0, 0.0, 0.0, 0.0};
+                if (warp == 0) {
+                    Acc T = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-                for (int w = 0; w < (SPLIT ? NW : 1); w++) {      // same order in every warp
-                    T.psi += red[w][0][lane];
-                    T.phi += red[w][1][lane];
-                    T.dpsi += red[w][2][lane];
-                    T.dphi += red[w][3][lane];
+                    for (int w = 0; w < (SPLIT ? NW : 1); w++) {
+                        T.psi += red[w][0][lane];
+                        T.phi += red[w][1][lane];
+                        T.dpsi += red[w][2][lane];
+                        T.dphi += red[w][3][lane];
+                    }
+                    if (act) {
+                        fin = R.update(T, tol, max_iter, o.status);
+                        if (fin) {
+                            o.org[b0 + k] = R.K;
+                            o.eta[b0 + k] = R.y;
+                            o.dorg[b0 + k] = R.dK;
+                            o.lamk[b0 + k] = R.dK + R.y;
+                            if (o.sweeps) o.sweeps[b0 + k] = R.nsw;
+                        }
+                    }
+                    s_dK[SPLIT ? lane : 0] = R.dK;
+                    s_y[SPLIT ? lane : 0] = R.y;
+                    s_ph[SPLIT ? lane : 0] = R.phase;
+                    s_fin[SPLIT ? lane : 0] = fin ? 1 : 0;
                 }
-                A = T;
                 __syncthreads();
-            }
-            bool fin = false;
-            if (act) {
+                if (warp != 0) {
+                    R.dK = s_dK[SPLIT ? lane : 0];
+                    R.y = s_y[SPLIT ? lane : 0];
+                    R.phase = s_ph[SPLIT ? lane : 0];
+                    fin = s_fin[SPLIT ? lane : 0] != 0;
+                }
+            } else if (act) {
                 fin = R.update(A, tol, max_iter, o.status);
-                if (fin && (!SPLIT || warp == 0)) {
+                if (fin) {
                     o.org[b0 + k] = R.K;
                     o.eta[b0 + k] = R.y;
                     o.dorg[b0 + k] = R.dK;
