@@ -100,25 +100,41 @@ static double geval(int m, const double *d, const double *w, int K, int k, doubl
     return 1.0 + p + q;
 }
 
-/* the root of a*y^2 + b*y + c = 0 lying strictly inside (lo, hi); if none,
- * the middle of the bracket */
-static double quad_in(double a, double b, double c, double lo, double hi)
+/* Rational model of Section 4.1.3 ("middle way", after Li): near the
+ * bracket (delta_k, delta_{k+1}) of root k, in the frame of origin K
+ * (delta_j = d_j - d_K), the secular function is modelled as
+ *     h(xi) = C + beta1 / (delta_k - xi) + beta2 / (delta_{k+1} - xi),
+ * which is strictly increasing between its two poles and therefore has
+ * exactly one zero there.  Written with the step s = xi - y from the current
+ * point y, p = delta_k - y < 0 < q = delta_{k+1} - y, the zero solves
+ *     C s^2 - (C (p + q) + beta1 + beta2) s + p q h(y) = 0
+ * (multiply h by (p - s)(q - s); the constant term C p q + beta1 q + beta2 p
+ * equals p q h(y), which the iteration passes as such: it tends to 0 with
+ * h(y) instead of cancelling).  model_step returns the zero lying in (p, q): both roots
+ * of the quadratic are formed without cancellation (the one of larger
+ * magnitude from the sign-matched sum, the other as the product over it),
+ * and the one between the poles is kept.  Returns 0 when rounding leaves no
+ * root strictly inside (p, q); the caller then bisects. */
+static int model_step(double C, double beta1, double beta2, double p, double q, double cst,
+                      double *s_out)
 {
-    double mid = 0.5 * (lo + hi);
-    if (a == 0.0) {
-        if (b == 0.0) return mid;
-        double y = -c / b;
-        return (y > lo && y < hi) ? y : mid;
+    double lin = -(C * (p + q) + beta1 + beta2);     /* coefficient of s   */
+    double r1, r2;
+    if (C == 0.0) {                                    /* linear model       */
+        if (lin == 0.0) return 0;
+        r1 = r2 = -cst / lin;
+    } else {
+        double disc = lin * lin - 4.0 * C * cst;
+        if (disc < 0.0) disc = 0.0;                    /* rounding only: one zero is between the poles */
+        double big = -0.5 * (lin + copysign(sqrt(disc), lin));
+        if (big == 0.0) { r1 = r2 = 0.0; }
+        else { r1 = big / C; r2 = cst / big; }
     }
-    double disc = b * b - 4.0 * a * c;
-    if (!(disc >= 0.0)) return mid;
-    double sq = sqrt(disc);
-    double q = -0.5 * (b + (b >= 0 ? sq : -sq));
-    double y1 = q / a;
-    double y2 = (q != 0.0) ? c / q : y1;
-    if (y1 > lo && y1 < hi) return y1;
-    if (y2 > lo && y2 < hi) return y2;
-    return mid;
+    int in1 = (r1 > p && r1 < q), in2 = (r2 > p && r2 < q);
+    if (in1 && in2) { *s_out = (fabs(r1) <= fabs(r2)) ? r1 : r2; return 1; }
+    if (in1) { *s_out = r1; return 1; }
+    if (in2) { *s_out = r2; return 1; }
+    return 0;
 }
 
 /* one root.  d, w: kept problem (m entries, d ascending, w = z^2 > 0).
@@ -133,26 +149,23 @@ int orc_secular_root(int m, const double *d, const double *w, int k, int mode,
     double W = 0;
     for (int j = 0; j < m; j++) W += w[j];
     int sweeps = 0;
-    double rest;      /* frozen non-adjacent part at the midpoint (initial guess) */
-    double fmid;
-    double ym;
+    double ymid, fmid;
     if (!last) {
-        double D = d[k + 1] - d[k];
-        double h = 0.5 * D;
-        fmid = geval(m, d, w, k, k, h, NULL, NULL, NULL, NULL);
+        /* origin (Section 4.2.1): the sign of f at the middle of (d_k, d_{k+1})
+         * says which pole the root is closer to */
+        ymid = 0.5 * (d[k + 1] - d[k]);
+        fmid = geval(m, d, w, k, k, ymid, NULL, NULL, NULL, NULL);
         sweeps++;
-        rest = fmid + w[k] / h - w[k + 1] / (D - h);
-        if (fmid >= 0.0) { K = k;     lo = 0.0; hi = h;  glo = -INFINITY; ghi = fmid; }
-        else             { K = k + 1; lo = -h;  hi = 0.0; glo = fmid;     ghi = INFINITY; }
-        (void)ym;
+        if (fmid >= 0.0) { K = k;     lo = 0.0;   hi = ymid; glo = -INFINITY; ghi = fmid; }
+        else             { K = k + 1; lo = -ymid; hi = 0.0;  glo = fmid;      ghi = INFINITY; }
     } else {
+        /* last root: lambda in (d_{m-1}, d_{m-1} + sum w); test the middle */
         K = k;
-        ym = 0.5 * W;
-        fmid = geval(m, d, w, K, k, ym, NULL, NULL, NULL, NULL);
+        ymid = 0.5 * W;
+        fmid = geval(m, d, w, K, k, ymid, NULL, NULL, NULL, NULL);
         sweeps++;
-        if (fmid >= 0.0) { lo = 0.0; hi = ym; glo = -INFINITY; ghi = fmid; }
-        else             { lo = ym;  hi = W;  glo = fmid;      ghi = geval(m, d, w, K, k, W, NULL, NULL, NULL, NULL); sweeps++; }
-        rest = fmid + w[k] / ym;
+        if (fmid >= 0.0) { lo = 0.0;  hi = ymid; glo = -INFINITY; ghi = fmid; }
+        else             { lo = ymid; hi = W;    glo = fmid;      ghi = geval(m, d, w, K, k, W, NULL, NULL, NULL, NULL); sweeps++; }
         /* g(W) >= 0 in exact arithmetic; widen if rounding says otherwise */
         int guard = 0;
         while (ghi < 0.0 && guard < 64) {
@@ -176,58 +189,69 @@ int orc_secular_root(int m, const double *d, const double *w, int k, int mode,
         return 0;
     }
 
-    /* mode 1: initial guess by freezing the non-adjacent terms (Li's scheme) */
+    /* mode 1.  Start (after Li): keep the poles next to the root exactly
+     * and freeze every other term at its value at the middle point,
+     *   h0(xi) = rest + w_k/(delta_k - xi) [+ w_{k+1}/(delta_{k+1} - xi)],
+     * with rest = f(ymid) minus the adjacent terms at ymid (evaluated in the
+     * frame of d_k, where f(ymid) was taken), and start from h0's zero. */
+    double dlo = d[k] - d[K];                          /* delta_k in the chosen frame     */
+    double dhi = last ? 0.0 : d[k + 1] - d[K];         /* delta_{k+1} in the chosen frame */
+    double rest;
+    if (!last) rest = fmid + w[k] / ymid - w[k + 1] / ((d[k + 1] - d[k]) - ymid);
+    else       rest = fmid + w[k] / ymid;
+    y = lo + 0.5 * (hi - lo);
     if (!last) {
-        double a = d[k] - d[K], b = d[k + 1] - d[K];
-        double A2 = rest;
-        double B2 = -(rest * (a + b) + w[k] + w[k + 1]);
-        double C2 = w[k] * b + w[k + 1] * a;
-        y = quad_in(A2, B2, C2, lo, hi);
-    } else {
-        y = (rest > 0.0) ? w[k] / rest : 0.5 * (lo + hi);
-        if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+        /* step from xi = 0; one of dlo, dhi is 0 (the origin pole), so the
+         * constant term is the limit w_k dhi + w_{k+1} dlo (+ rest dlo dhi = 0) */
+        double s0;
+        if (model_step(rest, w[k], w[k + 1], dlo, dhi, rest * dlo * dhi + w[k] * dhi + w[k + 1] * dlo, &s0)
+            && s0 > lo && s0 < hi)
+            y = s0;
+    } else if (rest > 0.0) {
+        /* one-pole model rest + w_k/(0 - xi) = 0 */
+        double x0 = w[k] / rest;
+        if (x0 > lo && x0 < hi) y = x0;
     }
-    double eps_tol = stop_c * (double)m * EPS;
+
+    double tol_c = stop_c * (double)m * EPS;
     for (int it = 0; it < max_iter; it++) {
         double psi, phi, dpsi, dphi;
         double f = geval(m, d, w, K, k, y, &psi, &phi, &dpsi, &dphi);
         sweeps++;
-        if (fabs(f) < eps_tol * (1.0 + fabs(psi) + fabs(phi))) {      /* eq. (4.12) */
+        /* stopping test, eq. (4.12) */
+        if (fabs(f) < tol_c * (1.0 + fabs(psi) + fabs(phi))) {
             *Kout = K; *etaout = y; if (iters) *iters = sweeps;
             return 0;
         }
-        if (f < 0.0) lo = y; else hi = y;
-        double ynew;
+        /* g_K increases on the bracket: shrink it to the side of the root */
+        if (f > 0.0) hi = y; else lo = y;
+        /* match value and slope of psi at y by alpha1 + beta1/(delta_k - xi)
+         * and of phi by alpha2 + beta2/(delta_{k+1} - xi) */
+        double p = dlo - y;
+        double beta1 = dpsi * p * p;
+        double alpha1 = psi - dpsi * p;
+        double xi;
+        int ok;
         if (!last) {
-            double Dk  = (d[k] - d[K]) - y;       /* d_k - x     */
-            double Dk1 = (d[k + 1] - d[K]) - y;   /* d_{k+1} - x */
-            double c = f - Dk * dpsi - Dk1 * dphi;
-            double A = (Dk + Dk1) * f - Dk * Dk1 * (dpsi + dphi);
-            double Bq = Dk * Dk1 * f;
-            double corr;
-            if (c == 0.0) {
-                corr = (A != 0.0) ? Bq / A : 0.0;
-            } else {
-                double disc = A * A - 4.0 * Bq * c;
-                if (disc < 0.0) disc = 0.0;
-                double s = sqrt(disc);
-                double den = A + (A >= 0 ? s : -s);
-                corr = (den != 0.0) ? 2.0 * Bq / den : 0.0;
-            }
-            ynew = y + corr;
+            double q = dhi - y;
+            double beta2 = dphi * q * q;
+            double alpha2 = phi - dphi * q;
+            double s;
+            ok = model_step(1.0 + alpha1 + alpha2, beta1, beta2, p, q, p * q * f, &s);
+            xi = y + s;
         } else {
-            double Dl = (d[k] - d[K]) - y;
-            double den = f - Dl * dpsi;
-            double corr = (den != 0.0) ? Dl + Dl * Dl * dpsi / den : 0.0;
-            ynew = y + corr;
+            /* no pole to the right: 1 + alpha1 + beta1/(delta_k - xi) = 0 */
+            double C = 1.0 + alpha1;
+            ok = (C != 0.0);
+            xi = ok ? dlo + beta1 / C : y;
         }
-        if (!(ynew > lo && ynew < hi)) ynew = lo + 0.5 * (hi - lo);
-        if (ynew == y || !(ynew > lo && ynew < hi)) {
-            /* bracket exhausted at double resolution */
+        if (!ok || !(xi > lo && xi < hi)) xi = lo + 0.5 * (hi - lo);   /* safeguard: bisect */
+        if (!(xi > lo && xi < hi) || xi == y) {
+            /* the bracket holds no other double */
             *Kout = K; *etaout = y; if (iters) *iters = sweeps;
             return 0;
         }
-        y = ynew;
+        y = xi;
     }
     *Kout = K; *etaout = y; if (iters) *iters = sweeps;
     return 1;
