@@ -200,7 +200,7 @@ superdc_status superdc_secular_batched_noalloc(int64_t nprob, const int64_t *off
  * Tree (HOST arrays): a postordered full binary tree with nnodes nodes, the
  * root is node nnodes-1; lchild/rchild are -1 at leaves; every leaf lies at
  * the same depth (perfect tree); leaf_size[i] = rows of leaf i (ignored for
- * non-leaves), 1 <= leaf_size <= 256; rank = r, the common HSS rank
+ * non-leaves), 1 <= leaf_size <= 128; rank = r, the common HSS rank
  * (1 <= r <= 32): every U_i is m_i x r, every R_i and B_i is r x r.
  *
  * Generators (DEVICE, FP64, column-major blocks, caller-owned, read only):
@@ -293,6 +293,8 @@ superdc_status superdc_eigfact_stats(const superdc_eigfact *f, int64_t *deflated
  * inspection access).  level: 0 (root) .. lmax-1; step: 0 .. r-1.  Fields of
  * length n (one entry per row of the level; node i owns its row range):
  *   "dk", "eta", "dorg", "vhat", "bnorm"  (double), "src", "pinv" (int32),
+ *   "din", "zin" (double: the step's input poles, ascending inside each
+ *   node, and its input column z, both before deflation),
  *   "P" (int32, the merge order of eq. (4.31); step ignored),
  *   "giv_cs" (double, 2n), "giv_ab" (int32, 2n);
  * per node of the level: "mk", "ngiv", "fmm" (int32; fmm = 1 where the

@@ -272,6 +272,39 @@ int orc_secular_all(int m, const double *d, const double *z, int mode, double st
     return bad;
 }
 
+/* the roots ks[0..nk-1] of a kept problem only (same per-root routine);
+ * returns the number of roots that failed */
+int orc_secular_some(int m, const double *d, const double *z, int nk, const int *ks, int mode,
+                     double stop_c, int max_iter, int *K, double *eta, int *iters)
+{
+    double *w = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
+    for (int j = 0; j < m; j++) w[j] = z[j] * z[j];
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 4) reduction(+:bad)
+    for (int t = 0; t < nk; t++)
+        bad += orc_secular_root(m, d, w, ks[t], mode, stop_c, max_iter, &K[t], &eta[t],
+                                iters ? &iters[t] : NULL);
+    free(w);
+    return bad;
+}
+
+/* f = g_K(y) and its triangular parts at given points: root ks[t] in the
+ * frame of origin Ks[t] at gap ys[t] (direct sums, the same evaluation as the
+ * iteration).  Outputs per point: f, psi, phi and f' = psi' + phi'. */
+void orc_secular_eval(int m, const double *d, const double *z, int nk, const int *ks, const int *Ks,
+                      const double *ys, double *f, double *psi, double *phi, double *df)
+{
+    double *w = (double *)malloc(sizeof(double) * (m > 0 ? m : 1));
+    for (int j = 0; j < m; j++) w[j] = z[j] * z[j];
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int t = 0; t < nk; t++) {
+        double p, q, dp, dq;
+        f[t] = geval(m, d, w, Ks[t], ks[t], ys[t], &p, &q, &dp, &dq);
+        psi[t] = p; phi[t] = q; df[t] = dp + dq;
+    }
+    free(w);
+}
+
 /* ------------------------------------------------------------------ */
 /* 3. Loewner's formula, eq. (4.23), paired as in Gu & Eisenstat         */
 /* ------------------------------------------------------------------ */

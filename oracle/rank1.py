@@ -64,6 +64,42 @@ def secular(dk, zk, mode=0, stop_c=8.0, max_iter=50):
     return K, eta, it, int(bad)
 
 
+def secular_some(dk, zk, ks, mode=0, stop_c=8.0, max_iter=50):
+    """Roots ks only of the kept problem (dk, zk); same per-root routine as
+    ``secular``.  Returns (K, eta, sweeps, number not converged) for ks."""
+    dk = np.ascontiguousarray(dk, np.float64)
+    zk = np.ascontiguousarray(zk, np.float64)
+    ks = np.ascontiguousarray(ks, np.int32)
+    m, nk = len(dk), len(ks)
+    assert nk == 0 or (ks.min() >= 0 and ks.max() < m)
+    K = np.zeros(nk, np.int32)
+    eta = np.zeros(nk)
+    it = np.zeros(nk, np.int32)
+    if nk == 0:
+        return K, eta, it, 0
+    bad = lib().orc_secular_some(ctypes.c_int(m), _d(dk), _d(zk), ctypes.c_int(nk), _i(ks), ctypes.c_int(mode),
+                                 ctypes.c_double(stop_c), ctypes.c_int(max_iter), _i(K), _d(eta), _i(it))
+    return K, eta, it, int(bad)
+
+
+def secular_eval(dk, zk, ks, Ks, ys):
+    """g_K(y) = 1 + psi + phi and f' at the given points (root ks[t], origin
+    Ks[t], gap ys[t]) by direct sums.  Returns (f, psi, phi, df)."""
+    dk = np.ascontiguousarray(dk, np.float64)
+    zk = np.ascontiguousarray(zk, np.float64)
+    ks = np.ascontiguousarray(ks, np.int32)
+    Ks = np.ascontiguousarray(Ks, np.int32)
+    ys = np.ascontiguousarray(ys, np.float64)
+    m, nk = len(dk), len(ks)
+    assert len(Ks) == nk and len(ys) == nk
+    assert nk == 0 or (ks.min() >= 0 and ks.max() < m and Ks.min() >= 0 and Ks.max() < m)
+    out = [np.zeros(nk) for _ in range(4)]
+    if nk:
+        lib().orc_secular_eval(ctypes.c_int(m), _d(dk), _d(zk), ctypes.c_int(nk), _i(ks), _i(Ks), _d(ys),
+                               *[_d(a) for a in out])
+    return tuple(out)
+
+
 def lowner(dk, zk, K, eta):
     m = len(dk)
     v = np.empty(m)

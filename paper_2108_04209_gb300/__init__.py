@@ -175,7 +175,7 @@ class EigFactor:
         n = self.n
         nn = 2 ** level
         spec = {"dk": (n, np.float64), "eta": (n, np.float64), "dorg": (n, np.float64), "vhat": (n, np.float64),
-                "bnorm": (n, np.float64), "src": (n, np.int32), "pinv": (n, np.int32), "P": (n, np.int32),
+                "bnorm": (n, np.float64), "din": (n, np.float64), "zin": (n, np.float64), "src": (n, np.int32), "pinv": (n, np.int32), "P": (n, np.int32),
                 "giv_cs": (2 * n, np.float64), "giv_ab": (2 * n, np.int32), "mk": (nn, np.int32),
                 "ngiv": (nn, np.int32), "fmm": (nn, np.int32)}
         cnt, dt = spec[field]

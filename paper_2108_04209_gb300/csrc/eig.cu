@@ -977,11 +977,12 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
         const int64_t np = (int64_t)h->lev_nodes[l].size();
         for (int j = 0; j < r; j++) {
             StepF &S = f->F[l][j];
-            // one slab per step: 7 double arrays (dk, eta, dorg, vhat, bnorm, giv_cs x2), int arrays
+            // one slab per step: 9 double arrays (dk, eta, dorg, vhat, bnorm, giv_cs x2, din, zin),
+            // int arrays
             double *dslab;
-            EIG_CHECK(dalloc(&dslab, 7 * n, &f->slabs));
+            EIG_CHECK(dalloc(&dslab, 9 * n, &f->slabs));
             S.dk = dslab; S.eta = dslab + n; S.dorg = dslab + 2 * n; S.vhat = dslab + 3 * n;
-            S.bnorm = dslab + 4 * n; S.giv_cs = dslab + 5 * n;
+            S.bnorm = dslab + 4 * n; S.giv_cs = dslab + 5 * n; S.din = dslab + 7 * n; S.zin = dslab + 8 * n;
             int32_t *islab;
             EIG_CHECK(dalloc(&islab, 5 * n + 3 * np, &f->slabs));
             S.src = islab; S.pinv = islab + n; S.giv_ab = islab + 2 * n; S.sweeps = islab + 4 * n;
@@ -1107,6 +1108,9 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
             if (T.on)
                 EIG_CHECK(cudaMemcpyAsync(T.WKb[l][j], WK + (int64_t)j * n, (size_t)n * (ctot - j) * sizeof(double),
                                           cudaMemcpyDeviceToDevice, st));
+            // the step's inputs (poles and z column), kept for inspection
+            EIG_CHECK(cudaMemcpyAsync(S.din, dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            EIG_CHECK(cudaMemcpyAsync(S.zin, WK + (int64_t)j * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
             // level-batched (default): every node of the level is one problem of
             // one launch sequence; unbatched baseline: one sequence per node
             const int nseg = opts->batching ? 1 : nl;
@@ -1263,6 +1267,8 @@ superdc_status superdc_eigfact_get(const superdc_eigfact *f, int32_t level, int3
     else if (fld == "dorg") { src = S.dorg; bytes = n * 8; }
     else if (fld == "vhat") { src = S.vhat; bytes = n * 8; }
     else if (fld == "bnorm") { src = S.bnorm; bytes = n * 8; }
+    else if (fld == "din") { src = S.din; bytes = n * 8; }
+    else if (fld == "zin") { src = S.zin; bytes = n * 8; }
     else if (fld == "src") { src = S.src; bytes = n * 4; }
     else if (fld == "pinv") { src = S.pinv; bytes = n * 4; }
     else if (fld == "P") { src = f->P[level]; bytes = n * 4; }

@@ -24,6 +24,7 @@ struct superdc_hss {
 
 struct StepF {   // stored factor of one rank-one step of one level
     double *dk, *eta, *dorg, *vhat, *bnorm, *giv_cs;
+    double *din, *zin;   // the step's input poles d and column z (before deflation)
     int32_t *src, *pinv, *giv_ab, *mk, *ngiv, *sweeps;
     int32_t *fmm;   // per node: 1 if the step took the FMM path
 };

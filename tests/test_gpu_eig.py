@@ -8,19 +8,38 @@ torch = pytest.importorskip("torch")
 import paper_2108_04209_gb300 as sdc  # noqa: E402
 from paper_2108_04209_gb300 import inputs  # noqa: E402
 from oracle import dense, superdc as osd  # noqa: E402
+from tests import parity as P  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-LAM_RTOL = 1e-10      # eigenvalue relative error bound
 METRIC_TOL = 1e-12    # residual and orthogonality (the paper's gamma, theta)
 
 
-def lam_close(lam, ref, anorm):
-    """|lambda - lambda_o| <= 1e-10 ||A||_2 for every eigenvalue.  The deflation
-    tolerance tau of Remark 4.1 is absolute, so the method fixes eigenvalues
-    to O(tau) in absolute terms: the relative error is measured against the
-    spectral radius, not against each (possibly tiny) eigenvalue."""
-    return np.all(np.abs(lam - ref) <= LAM_RTOL * anorm)
+def nsteps(F):
+    """Rank-one steps an eigenvalue passes through: tree levels x rank."""
+    return F.lmax * F.rank
+
+
+def decision_mismatches(F, O, t):
+    """(level, step, node) triples whose kept size or rotation count differs
+    between the GPU factor and the oracle's."""
+    bad = []
+    for lev in range(F.lmax):
+        nodes = sorted([i for i in range(t.nnodes) if t.level[i] == lev], key=lambda i: t.offset[i])
+        for j in range(F.rank):
+            mk, ng = F.get(lev, j, "mk"), F.get(lev, j, "ngiv")
+            for q, node in enumerate(nodes):
+                fo = O.fac[node][j]
+                if mk[q] != fo.mk or ng[q] != len(fo.giv[0]):
+                    bad.append((lev, j, node, int(mk[q]), fo.mk))
+    return bad
+
+
+def assert_lam(lam, ref, anorm, F, tau=1e-10, differ=False, what=""):
+    ok, info = P.lam_check(lam, ref, anorm, nsteps(F), tau=tau, decisions_differ=differ)
+    print(what, info)
+    assert ok, info
+    return info
 
 
 def gpu_eig(h, tau=1e-10):
@@ -40,8 +59,10 @@ def test_small_hss_vs_oracle_and_dense():
     H, lam, F = gpu_eig(h)
     O = osd.superdc(h, tau=1e-10, mode=0)
     an = np.linalg.norm(A, 2)
-    assert lam_close(lam, O.eigenvalues, an), np.abs(lam - O.eigenvalues).max()
-    assert lam_close(lam, np.linalg.eigvalsh(A), an)
+    assert not decision_mismatches(F, O, h.tree)
+    info = assert_lam(lam, O.eigenvalues, an, F, what="n=512 vs oracle")
+    assert info["n_deflation"] == 0
+    assert_lam(lam, np.linalg.eigvalsh(A), an, F, what="n=512 vs eigh")
     Q, QT = dense_Q(F, h.tree.n)
     assert np.abs(QT - Q.T).max() < 1e-13
     assert dense.gamma(A, lam, Q) <= METRIC_TOL
@@ -80,7 +101,8 @@ def test_per_node_deflation_and_permutations_vs_oracle():
                     pairs = ab[2 * o:2 * o + 2 * ng[q]].reshape(-1, 2)
                     assert np.array_equal(pairs[:, 0], fo.giv[0]) and np.array_equal(pairs[:, 1], fo.giv[1])
     an = np.abs(O.eigenvalues).max()
-    assert lam_close(lam, O.eigenvalues, an)
+    info = assert_lam(lam, O.eigenvalues, an, F, what="n=1024 clustered vs oracle")
+    assert info["n_deflation"] == 0
 
 
 def test_tridiagonal_closed_form_gpu():
@@ -97,13 +119,22 @@ def test_tridiagonal_closed_form_gpu():
 
 
 def test_clustered_16384_vs_oracle_probes():
-    """Clustered leaf spectra at n=16384 (leaf 64, rank 8): eigenvalues against
-    the oracle; residual and orthogonality through 64 probe columns."""
+    """Clustered leaf spectra at n=16384 (leaf 64, rank 8): every eigenvalue
+    against the oracle's bisection mode; residual and orthogonality through
+    64 probe columns."""
     h = inputs.cfg_clustered_16384()
     H, lam, F = gpu_eig(h)
-    O = osd.superdc(h, tau=1e-10, mode=1)
+    O = osd.superdc(h, tau=1e-10, mode=0)
     an = max(np.abs(O.eigenvalues).max(), 1.0)
-    assert lam_close(lam, O.eigenvalues, an), np.abs(lam - O.eigenvalues).max()
+    # The two sides form Zhat by different routes (W route / superdcmv), so a
+    # step's inputs differ by rounding and a deflation test that sits within
+    # rounding of tau can flip (the clustered spectra put many |z| near tau);
+    # test_every_step_deflation_bitexact_16384 checks the decisions on equal
+    # inputs.  Here the flips are counted and their O(tau) effect is allowed.
+    mism = decision_mismatches(F, O, h.tree)
+    print("node-steps whose deflation differs (level, step, node, gpu mk, oracle mk):", mism[:10], len(mism),
+          "of", F.lmax * F.rank * (2 ** F.lmax - 1) // F.lmax)
+    assert_lam(lam, O.eigenvalues, an, F, differ=bool(mism), what="n=16384 clustered vs oracle (bisection)")
     n = h.tree.n
     Xn = inputs.normal_block(n, 64, seed=102)
     X = torch.from_numpy(Xn).cuda()
@@ -117,11 +148,71 @@ def test_clustered_16384_vs_oracle_probes():
     assert st["deflated"] > 0
 
 
-def test_full_size_131072_invariants_and_probes():
-    """n=131072, leaf 128, rank 10: trace and Frobenius invariants from the
-    generators, residual and orthogonality on a 131072 x 64 N(0,1) block."""
+def test_every_step_deflation_bitexact_16384():
+    """Every rank-one step of every node of the clustered n=16384 problem:
+    the oracle's deflation (Remark 4.1) run on the step's own inputs (the
+    poles and z column the GPU stored) reproduces the GPU's kept set, rotated
+    poles, rotation pairs and (c, s) bit for bit."""
+    h = inputs.cfg_clustered_16384()
+    H, lam, F = gpu_eig(h)
+    t = h.tree
+    from oracle import rank1 as r1
+    nrot = nsteps_checked = 0
+    for lev in range(F.lmax):
+        nodes = sorted([i for i in range(t.nnodes) if t.level[i] == lev], key=lambda i: t.offset[i])
+        for j in range(F.rank):
+            din, zin = F.get(lev, j, "din"), F.get(lev, j, "zin")
+            src, dk = F.get(lev, j, "src"), F.get(lev, j, "dk")
+            mk, ng = F.get(lev, j, "mk"), F.get(lev, j, "ngiv")
+            ab, cs = F.get(lev, j, "giv_ab"), F.get(lev, j, "giv_cs")
+            for q, node in enumerate(nodes):
+                o, m = int(t.offset[node]), int(t.leaf_size[node])
+                dd, zz, kept, giv = r1.deflate(din[o:o + m], zin[o:o + m], 1e-10)
+                kidx = np.nonzero(kept)[0]
+                assert mk[q] == len(kidx), (lev, j, node)
+                assert np.array_equal(src[o:o + mk[q]], kidx)
+                assert np.array_equal(dk[o:o + mk[q]], dd[kidx])
+                assert ng[q] == len(giv[0])
+                if ng[q]:
+                    pr = ab[2 * o:2 * o + 2 * ng[q]].reshape(-1, 2)
+                    c = cs[2 * o:2 * o + 2 * ng[q]].reshape(-1, 2)
+                    assert np.array_equal(pr[:, 0], giv[0]) and np.array_equal(pr[:, 1], giv[1])
+                    assert np.array_equal(c[:, 0], giv[2]) and np.array_equal(c[:, 1], giv[3])
+                nrot += int(ng[q])
+                nsteps_checked += 1
+    print("node-steps checked", nsteps_checked, "rotations", nrot)
+    assert nrot > 0
+
+
+def test_tridiagonal_131072_closed_form_every_eigenvalue():
+    """Section 5, Example 1 at n = 131072 (leaf 128, rank 2, tau = 1e-10):
+    every eigenvalue against 3 - 2 cos(k pi/(n+1)), per entry."""
+    n = 131072
+    h = inputs.hss_tridiag(n, 128)
+    H, lam, F = gpu_eig(h)
+    k = np.arange(1, n + 1)
+    exact = np.sort(3.0 - 2.0 * np.cos(k * np.pi / (n + 1)))
+    rel = np.abs(lam - exact) / np.abs(exact)
+    print("tridiagonal n=131072: max relative error", rel.max(), F.stats())
+    assert rel.max() <= 1e-10
+    X = torch.from_numpy(inputs.normal_block(n, 4, seed=6)).cuda()
+    back = F.apply_Q(F.apply_Q(X), trans=True)
+    orth = (torch.linalg.norm(back - X) / torch.linalg.norm(X)).item()
+    print("tridiagonal n=131072: probe orthogonality", orth)
+    assert orth <= 1e-12 * np.sqrt(n)
+
+
+@pytest.fixture(scope="module")
+def large_131072():
     h = inputs.cfg_large_131072()
     H, lam, F = gpu_eig(h)
+    return h, H, lam, F
+
+
+def test_full_size_131072_invariants_and_probes(large_131072):
+    """n=131072, leaf 128, rank 10: trace and Frobenius invariants from the
+    generators, residual and orthogonality on a 131072 x 64 N(0,1) block."""
+    h, H, lam, F = large_131072
     tr = dense.trace_from_generators(h)
     fro2 = dense.fro2_from_generators(h)
     assert np.all(np.diff(lam) >= 0)
@@ -137,6 +228,25 @@ def test_full_size_131072_invariants_and_probes():
     orth = F.apply_Q(torch.from_numpy(QX).cuda(), trans=True).cpu().numpy() - Xn
     assert res < 1e-12 * np.sqrt(n)
     assert np.linalg.norm(orth) / np.linalg.norm(Xn) < 1e-12 * np.sqrt(n)
+
+
+@pytest.mark.parametrize("step", [0, 9])
+def test_root_node_step_131072_vs_oracle(large_131072, step):
+    """The largest rank-one steps of n=131072 (leaf 128, rank 10): the root
+    node's step (m = 131072, triangular FMM path) fed with the GPU's own
+    inputs (poles and z column of that step) to the oracle: deflation bit for
+    bit, every gap, zhat and b per entry against the oracle's middle-way mode,
+    512 sampled gaps against its bisection to adjacent doubles, and the new
+    eigenvalues per entry (the next step's poles, or the final eigenvalues)."""
+    h, H, lam, F = large_131072
+    n = h.tree.n
+    din = F.get(0, step, "din")
+    zin = F.get(0, step, "zin")
+    nxt = F.get(0, step + 1, "din") if step + 1 < F.rank else lam
+    assert F.get(0, step, "fmm")[0] == 1
+    g = P.eigfact_problem(F, 0, step, 0, 0, n, nxt_din=nxt)
+    st = P.compare_stored_step(g, din, zin, 1e-10, mode=1, n_exact=512, seed=step)
+    print("root step", step, st)
 
 
 def test_unbatched_per_node_path_matches_level_batched():
