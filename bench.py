@@ -10,11 +10,21 @@ whole rank-one pipeline of the conquering stage, in one C-ABI call.
 Metric: secular roots per second (all roots of the batch / device time of
 the step).  Inputs are resident in HBM when the timed region starts; the L2
 is flushed (256 MiB write) before every timed step.  ``e2e`` repeats the
-measurement through the host-buffer API (pinned host -> device copies of the
-inputs and device -> host copies of the results inside the timed region).
+measurement through the C-ABI host-buffer entry point
+superdc_secular_batched_host (pinned host -> device copies of the inputs and
+device -> host copies of the results inside the timed region).
 
 Multi-GPU: the path has no exchange step; N ranks run N independent replicas
 (weak scaling), ``value`` = roots of all ranks / max-over-ranks time.
+
+Beside the batched step (single-GPU runs only; --no-eig skips them):
+``hss_eig_131072`` times superdc_eig on the n=131072, leaf 128, rank 10 HSS
+matrix (median of 3 after a warm-up, wall and CUDA-event time, clocks), Q^T X
+on a 131072 x 64 block through superdc_apply_Q (time, HBM GB/s of its
+algorithmic bytes, FP64 fraction of its algorithmic flops), the direct-only
+eigendecomposition once (--no-direct skips it) and Table 5's statistic;
+``hss_eig_16384`` times the clustered n=16384 problem level-batched and one
+node at a time, and the oracle on the same problem on the host cores.
 
 ``--impl reference`` times the CPU oracle (plain C + OpenMP, FP64) on a
 bounded sample of the same workload on the host cores.
@@ -182,6 +192,143 @@ def job_throughput(units_per_rank_step, steps, ws, tmax_ms):
     return units, units / (tmax_ms * 1e-3)
 
 
+def _median(v):
+    return float(np.median(np.asarray(v, dtype=np.float64)))
+
+
+def _timed(fn, reps):
+    """(median wall s, median CUDA-event ms, last result) of reps calls after
+    the caller's warm-up; the events bracket the call on the current stream."""
+    import torch
+    walls, evs, res = [], [], None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        res = fn()
+        e1.record()
+        e1.synchronize()
+        walls.append(time.perf_counter() - t0)
+        evs.append(e0.elapsed_time(e1))
+    return _median(walls), _median(evs), res
+
+
+def apply_q_work(F, ncols, fmm_min_m=512):
+    """Algorithmic bytes and flops of Q^T X for the direct part (the FMM part's
+    flops come from the device counter): per rank-one factor the block is read
+    and written once and the factor vectors (dk, eta, d_K, vhat, b: doubles;
+    src, pinv: int32) read once; per level one permutation pass; the leaves
+    read the block, their dense Q and write the result.  Direct Cauchy-like
+    terms: difference, reciprocal and one FMA per column of each 32-column
+    chunk, over every (target, source) pair of the nodes below the FMM
+    threshold."""
+    n = F.n
+    blk = 2.0 * n * ncols * 8
+    nbytes = F.lmax * F.rank * (blk + n * (5 * 8 + 2 * 4)) + F.lmax * blk + blk + n * 128 * 8
+    chunks = [min(32, ncols - c0) for c0 in range(0, ncols, 32)]
+    per_pair = sum(3 + 2 * c for c in chunks)
+    dflops = 0.0
+    for lev in range(F.lmax):
+        for j in range(F.rank):
+            mk = F.get(lev, j, "mk").astype(np.float64)
+            dmk = mk[mk < fmm_min_m]
+            dflops += per_pair * float(np.sum(dmk * dmk))
+    return nbytes, dflops
+
+
+def eig_headline(dev, peak, peak_src, direct=True, reps=3):
+    """HSS eigendecomposition at n=131072 (leaf 128, rank 10, seed 4) and
+    Q^T X on a 131072 x 64 N(0,1) block: median of reps after one warm-up,
+    wall time around the C-ABI call (which synchronises) and CUDA-event time,
+    the clocks during the runs; the direct-only time once; Table 5's statistic
+    over the root node's r secular equations."""
+    import ctypes
+    import torch
+    import paper_2108_04209_gb300 as sdc
+    from paper_2108_04209_gb300 import _lib as L, inputs
+    lib = L.lib()
+    h = inputs.cfg_large_131072()
+    H = sdc.HSSMatrix(h)
+    opts = sdc.default_opts()
+    clk = Clocks(dev.index or 0)
+    lam, F = H.eig(opts)                       # warm-up
+    del F
+    clk.start()
+    wall, ev, (lam, F) = _timed(lambda: H.eig(opts), reps)
+    n = F.n
+    X = torch.from_numpy(inputs.normal_block(n, 64, seed=104)).to(dev)
+    F.apply_Q(X, trans=True)                   # warm-up
+    awall, aev, Y = _timed(lambda: F.apply_Q(X, trans=True), reps)
+    # the device flop counter of the FMM part, one more call
+    lib.superdc_profile_reset()
+    lib.superdc_profile_enable(1)
+    F.apply_Q(X, trans=True)
+    torch.cuda.synchronize()
+    lib.superdc_profile_enable(0)
+    c = ctypes.c_int64(0)
+    lib.superdc_profile_counter(b"fmm_flops", ctypes.byref(c))
+    nbytes, dflops = apply_q_work(F, 64)
+    aflops = float(c.value) + dflops
+    clocks = clk.stop()
+    st = F.stats()
+    mus = []
+    for j in range(F.rank):
+        swj = F.get(0, j, "sweeps")[:int(F.get(0, j, "mk")[0])]
+        mus.append(float(np.mean(swj - 1 > 5)))
+    out = {
+        "workload": "HSS n=131072, leaf 128, rank 10, seed 4 (U orthonormal from QR of N(0,1), B = N(0,1) diag(2^-k)), "
+                    "tau=1e-10; apply: Q^T X, X 131072 x 64 N(0,1) seed 104",
+        "eig_s": {"wall_median": wall, "device_median": ev * 1e-3, "reps": reps},
+        "apply_QT_64": {"wall_median_s": awall, "device_median_s": aev * 1e-3,
+                        "hbm_gbs": nbytes / (aev * 1e-3) / 1e9, "algorithmic_bytes": nbytes,
+                        "fp64_tflops": aflops / (aev * 1e-3) / 1e12, "fp64_frac": aflops / (aev * 1e-3) / 1e12 / peak,
+                        "algorithmic_flops": aflops, "hbm_of": "measured copy bandwidth %.0f GB/s" % _peaks().get(
+                            "hbm_gbs", 0.0), "fp64_of": peak_src},
+        "stats": st,
+        "mu_table5_root": {"max_over_steps": max(mus), "per_step": mus,
+                           "note": "fraction of the root node's roots needing more than 5 iterations after the "
+                                   "midpoint sweep (Section 5, Table 5)"},
+        "clocks": clocks,
+    }
+    if direct:
+        del F
+        lam0, F0 = H.eig(sdc.default_opts(fmm_min_m=-1))
+        torch.cuda.synchronize()
+        dw, dev_ms, _ = _timed(lambda: H.eig(sdc.default_opts(fmm_min_m=-1)), 1)
+        out["eig_direct_only_s"] = {"wall": dw, "device": dev_ms * 1e-3}
+    out["cpu_oracle"] = "not run at n=131072: the oracle needs ~5 min on 16 cores per run (direct O(n^2) sweeps " \
+                        "at the top levels); timed at n=16384 in hss_eig_16384"
+    return out
+
+
+def eig_clustered(dev, oracle=True, reps=3):
+    """n=16384, leaf 64, rank 8, clustered leaf spectra (seed 2): level-batched
+    launches vs one launch sequence per node (opts.batching = 0), and the
+    oracle on the host cores (middle-way mode) for the same problem."""
+    import torch
+    import paper_2108_04209_gb300 as sdc
+    from paper_2108_04209_gb300 import inputs
+    h = inputs.cfg_clustered_16384()
+    H = sdc.HSSMatrix(h)
+    H.eig()
+    bw, bev, (lam, F) = _timed(lambda: H.eig(), reps)
+    H.eig(sdc.default_opts(batching=0))
+    uw, uev, _ = _timed(lambda: H.eig(sdc.default_opts(batching=0)), 1)
+    out = {"workload": "HSS n=16384, leaf 64, rank 8, clustered leaf spectra, seed 2, tau=1e-10",
+           "batched_s": {"wall_median": bw, "device_median": bev * 1e-3},
+           "per_node_s": {"wall": uw, "device": uev * 1e-3},
+           "batched_speedup": uev / bev, "deflated": F.stats()["deflated"]}
+    if oracle:
+        from oracle import superdc as osd
+        t0 = time.perf_counter()
+        osd.superdc(h, tau=1e-10, mode=1)
+        out["cpu_oracle"] = {"s": time.perf_counter() - t0, "cores": len(os.sched_getaffinity(0)),
+                             "kind": "oracle (middle-way mode), same box"}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -229,6 +376,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-eig", action="store_true", help="skip the HSS eigendecomposition blocks")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-only n=131072 run (~50 s)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -351,6 +500,8 @@ def main():
     sw = out["sweeps"].cpu().numpy().astype(np.float64)
     fm = out["fmm"].cpu().numpy()[:batch.nprob] != 0
     per_prob_sweeps = np.add.reduceat(sw, batch.offsets[:-1]) if total else np.zeros(0)
+    kept_sw = sw[sw > 0]
+    mu = float(np.mean(kept_sw - 1 > 5)) if kept_sw.size else 0.0
     interactions = float(np.sum((mk * per_prob_sweeps)[~fm]))
     last_sweeps = np.array([sw[int(batch.offsets[p]) + int(mk[p]) - 1] if fm[p] else 0.0
                             for p in range(batch.nprob)])
@@ -358,6 +509,9 @@ def main():
     terms = ctypes.c_int64(0)
     lib.superdc_profile_counter(b"fmm_secular_terms", ctypes.byref(terms))
     fmm_terms = float(terms.value) / max(1, args.steps)
+    fl_ctr = ctypes.c_int64(0)
+    lib.superdc_profile_counter(b"fmm_flops", ctypes.byref(fl_ctr))
+    fmm_other_flops = float(fl_ctr.value) / max(1, args.steps)
     peak, peak_src = _fp64_peak()
     sec_ms = kern["secular"][1] / max(1, kern["secular"][0])
     fsec_ms = kern["fmm_secular"][1] / max(1, args.steps)
@@ -372,26 +526,36 @@ def main():
         rl["fmm_secular"] = {"achieved": fl / (fsec_ms * 1e-3) / 1e12, "ms": fsec_ms, "flops": fl,
                              "algorithmic": "%.0f flops x %.4g near-field terms + %d flops x %.4g root sweeps" % (
                                  SECULAR_FLOPS_PER_INTERACTION, fmm_terms, FMM_FAR_FLOPS, fmm_root_sweeps)}
+    # whole step: every kernel's algorithmic work (direct secular, Loewner 5 and
+    # b 6 flops per (target, source) pair of the direct problems, FMM secular
+    # near terms and far-field sweeps, and the device-counted far fields and
+    # Loewner / b consumers of the FMM problems) over the step time
+    direct_pairs = float(np.sum((mk * mk)[~fm]))
+    step_flops = (SECULAR_FLOPS_PER_INTERACTION * interactions + 11.0 * direct_pairs +
+                  SECULAR_FLOPS_PER_INTERACTION * fmm_terms + FMM_FAR_FLOPS * fmm_root_sweeps + fmm_other_flops)
     dom = max(rl, key=lambda k: rl[k]["ms"]) if rl else "k_secular"
     prof = _profiled("k_secular_batched4096_dram.md", "paper_2108_04209_gb300/csrc/rank1.cu") \
         if dom == "k_secular" else _profiled("fmm_secular_batched4096_dram.md",
                                              "paper_2108_04209_gb300/csrc/fmm_impl.cuh")
     achieved = rl[dom]["achieved"] if rl else 0.0
 
-    # e2e: host buffers, copies inside the timed region
+    # e2e: the C-ABI host-buffer entry point (superdc_secular_batched_host):
+    # pinned host inputs in, host results out, copies inside the timed region
     h_off = torch.from_numpy(batch.offsets).pin_memory()
     h_d = torch.from_numpy(batch.d).pin_memory()
     h_z = torch.from_numpy(batch.z).pin_memory()
     fields = ("lam", "eta", "org", "vhat", "bnorm")
-    for _ in range(2):
-        sdc.secular_batched_host(h_off, h_d, h_z, 1.0, opts, fields=fields)
+    res = sdc.secular_batched_host(h_off, h_d, h_z, 1.0, opts, fields=fields)
+    hout = dict(res)
+    hout["status"] = torch.zeros(1, dtype=torch.int32).pin_memory()
+    sdc.secular_batched_host(h_off, h_d, h_z, 1.0, opts, fields=fields, out=hout)
     barrier()
     e2e_t = 0.0
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = sdc.secular_batched_host(h_off, h_d, h_z, 1.0, opts, fields=fields)
+        res = sdc.secular_batched_host(h_off, h_d, h_z, 1.0, opts, fields=fields, out=hout)
         e2e_t += time.perf_counter() - t0
     h2d = h_off.numel() * 8 + h_d.numel() * 8 + h_z.numel() * 8
     d2h = sum(v.numel() * v.element_size() for v in res.values()) + 4
@@ -417,6 +581,14 @@ def main():
                          "algorithmic": rl.get(dom, {}).get("algorithmic"),
                          "other": {k: {"achieved": v["achieved"], "frac": v["achieved"] / peak, "ms": v["ms"]}
                                    for k, v in rl.items() if k != dom}},
+            "whole_step": {"flops": step_flops, "achieved_tflops": step_flops / (tmax / args.steps * 1e-3) / 1e12,
+                           "frac": step_flops / (tmax / args.steps * 1e-3) / 1e12 / peak,
+                           "of": "measured FP64 peak (DFMA probe)",
+                           "algorithmic": "direct secular 7/pair-sweep, direct Loewner 5 + b 6 per pair, FMM secular "
+                                          "7/near term + %d/root sweep, FMM far fields and consumers counted on the "
+                                          "device (FMA 2, other operations 1)" % FMM_FAR_FLOPS},
+            "mu_table5": {"value": mu, "unit": "fraction of roots not converged after 5 iterations",
+                          "note": "iterations = sweeps after the midpoint sweep (Section 5, Table 5's statistic)"},
             "fmm": {"threshold": "opts.fmm_min_m=%d (0 = library default)" % opts.fmm_min_m,
                     "problems": int(fm.sum()), "roots": int(mk[fm].sum()),
                     "direct_problems": int((~fm).sum()), "direct_roots": int(mk[~fm].sum())},
@@ -433,6 +605,11 @@ def main():
         }
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(batch, budget_s=args.cpu_budget)
+        if not args.no_eig and ws == 1:
+            del out, flush
+            torch.cuda.empty_cache()
+            line["hss_eig_131072"] = eig_headline(dev, peak, peak_src, direct=not args.no_direct)
+            line["hss_eig_16384"] = eig_clustered(dev, oracle=(ws == 1 and not args.no_cpu_baseline))
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

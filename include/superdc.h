@@ -136,6 +136,21 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
                                        const superdc_opts *opts, superdc_rank1_out *out,
                                        cudaStream_t stream);
 
+/* superdc_secular_batched with HOST buffers, for callers whose data live in
+ * host memory: offsets[nprob+1], d[total], z[total] are HOST arrays (pinned
+ * memory makes the copies asynchronous; pageable memory works too), every
+ * non-NULL field of *out is a HOST array of the length given above, and
+ * out->status (HOST, required) receives the device status word.  The call
+ * copies the inputs to a stream-ordered device slab, runs the batched step,
+ * copies the requested outputs back, releases the slab and synchronises the
+ * stream; it returns SUPERDC_ERR_NONFINITE / SUPERDC_ERR_NOCONV when the
+ * status word says so.  Argument errors as superdc_secular_batched, plus
+ * offsets[0] != 0 or offsets[nprob] != total. */
+superdc_status superdc_secular_batched_host(int64_t nprob, const int64_t *offsets, int64_t total,
+                                            const double *d, const double *z, double rho,
+                                            const superdc_opts *opts, superdc_rank1_out *out,
+                                            cudaStream_t stream);
+
 /* Y = Qhat^T X (trans = 1) or Y = Qhat X (trans = 0) for every problem of a
  * superdc_secular_batched result `fwd` (the structured eigenvector matrices of
  * eq. (4.26) with the rotations and the sort), applied to caller columns:
@@ -158,8 +173,9 @@ superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offsets, int64_
  * Outputs: d_bar[total], z_bar[total] (input order), X_bar = Qhat Ybar
  * (total x ncols, ld ldxb; written only when ncols > 0).
  * Kept block: eigen-adjoint of diag(d_k) + z_k z_k^T through the Cauchy-like
- * factor (eq. (4.26)) with zhat recomputed from the stored factor vectors and
- * every difference in shifted form (eq. (4.28)); deflation rotations are
+ * factor (eq. (4.26)), reading zhat and b from fwd (the structured factor
+ * keeps them for its applications, so they are not formed again) with every
+ * difference in shifted form (eq. (4.28)); deflation rotations are
  * treated as fixed linear maps (their dependence on z is of order tau). */
 superdc_status superdc_secular_batched_backward(int64_t nprob, const int64_t *offsets, int64_t total,
                                                 double rho, const superdc_rank1_out *fwd,
@@ -171,21 +187,29 @@ superdc_status superdc_secular_batched_backward(int64_t nprob, const int64_t *of
 /* ------------------------------------------------------------------------
  * superdc_secular_batched_noalloc: the batched rank-one step of
  * superdc_secular_batched for callers that cannot allocate device memory
- * while they run (work recorded once and replayed from a CUDA graph, latency
- * bound paths where an allocation may block or fail, hosts with a fixed,
- * pre-reserved memory budget).  The paper has no counterpart; this is an
- * interface variant only.  Same arguments, layout and results as
- * superdc_secular_batched, but the call makes no device allocation: its
- * scratch is a static device array of about 11 MB that every GPU which loads
- * the library holds until the process exits.
+ * while they run: a host whose device memory was reserved up front by
+ * another framework or pool it does not own, a latency-bound path on which
+ * cudaMalloc may block or synchronise the device, or a plug-in that must not
+ * change the process's memory footprint after it has been loaded.  The paper
+ * has no counterpart; this is an interface variant only.  Same arguments and
+ * output layout as superdc_secular_batched, but the call makes no device
+ * allocation: its scratch is a static device array of about 11 MB that every
+ * GPU which loads the library holds until the process exits.
+ *   - evaluator: the direct tiled evaluator only (the triangular FMM needs
+ *     scratch proportional to its tree); opts.fmm_min_m is ignored and
+ *     out->fmm (if given) is set to 0.  opts.sched and opts.tile_roots select
+ *     the schedule as in superdc_secular_batched; for a problem below the
+ *     FMM threshold the results are those of superdc_secular_batched;
  *   - limits: nprob <= SDC_NOALLOC_MAX_PROB and total <= SDC_NOALLOC_MAX_TOTAL,
  *     else SUPERDC_ERR_ARG (nothing enqueued);
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current and caches it; make
- *     that first call before any stream capture;
- *   - all calls on a device share the array: calls whose work overlaps on the
- *     GPU (other streams, other host threads) race and must be serialised;
- *     nothing needs clearing between calls.
+ *     (cudaGetSymbolAddress) with that device current and caches it, and
+ *     sets a kernel attribute once per device; make that first call before
+ *     any stream capture;
+ *   - all calls on a device share the array and it keeps the last call's
+ *     contents (each call writes every word it reads, so nothing needs
+ *     clearing in between): calls whose work overlaps on the GPU (other
+ *     streams, other host threads) race and must be serialised.
  * -------------------------------------------------------------------- */
 #define SDC_NOALLOC_MAX_TOTAL 262144
 #define SDC_NOALLOC_MAX_PROB 16384
@@ -233,8 +257,8 @@ void superdc_hss_free(superdc_hss *h);
 
 /* Eigendecomposition A = Q diag(lambda) Q^T (Algorithms 1-3):
  *   dividing stage (Algorithm 1, balanced eqs. (3.11)/(3.12), generator
- *   updates of Lemma 2.1); leaf eigendecompositions (parallel cyclic
- *   Jacobi); conquering stage bottom-up over the tree levels: merge sort P_p
+ *   updates of Lemma 2.1); leaf eigendecompositions (Householder
+ *   tridiagonalisation and implicit QL with Wilkinson's shift); conquering stage bottom-up over the tree levels: merge sort P_p
  *   (eq. (4.31)), Zhat_p = diag(Q_c1^T, Q_c2^T) Z_p (eq. (2.8)), r rank-one
  *   steps per node, each step applied to the remaining columns.
  * lambda: DEVICE, n entries, ascending (caller-allocated).
@@ -294,7 +318,8 @@ superdc_status superdc_eigfact_stats(const superdc_eigfact *f, int64_t *deflated
  * length n (one entry per row of the level; node i owns its row range):
  *   "dk", "eta", "dorg", "vhat", "bnorm"  (double), "src", "pinv" (int32),
  *   "din", "zin" (double: the step's input poles, ascending inside each
- *   node, and its input column z, both before deflation),
+ *   node, and its input column z, both before deflation), "sweeps" (int32:
+ *   secular sweeps of each kept root, the midpoint sweep included),
  *   "P" (int32, the merge order of eq. (4.31); step ignored),
  *   "giv_cs" (double, 2n), "giv_ab" (int32, 2n);
  * per node of the level: "mk", "ngiv", "fmm" (int32; fmm = 1 where the

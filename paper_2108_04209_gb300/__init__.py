@@ -73,19 +73,31 @@ def secular_batched(offsets, d, z, rho=1.0, opts=None, out=None, check=True):
     return out
 
 
-def secular_batched_host(offsets, d, z, rho=1.0, opts=None, fields=("lam", "eta", "org", "vhat", "bnorm")):
-    """End-to-end variant: host (CPU) tensors in, host tensors out.  Copies the
-    inputs to the device, runs the batched step, copies ``fields`` back."""
-    dev = torch.device("cuda")
-    offs = offsets.to(dev, non_blocking=True)
-    dd = d.to(dev, non_blocking=True)
-    zz = z.to(dev, non_blocking=True)
-    out = secular_batched(offs, dd, zz, rho, opts, check=False)
-    res = {k: out[k].to("cpu", non_blocking=True) for k in fields}
-    st = out["status"].to("cpu", non_blocking=True)
-    torch.cuda.current_stream().synchronize()
-    check_status(st, "superdc_secular_batched")
-    return res
+def secular_batched_host(offsets, d, z, rho=1.0, opts=None, fields=("lam", "eta", "org", "vhat", "bnorm"),
+                         out=None):
+    """End-to-end variant through the host-buffer entry point
+    superdc_secular_batched_host: CPU tensors in (pinned for asynchronous
+    copies), CPU tensors out.  ``fields`` selects the outputs copied back;
+    ``out`` (optional) is a dict of preallocated CPU tensors to reuse."""
+    assert not d.is_cuda and not z.is_cuda and not offsets.is_cuda, "host tensors required"
+    assert d.dtype == torch.float64 and z.dtype == torch.float64 and offsets.dtype == torch.int64
+    nprob = offsets.numel() - 1
+    total = d.numel()
+    if opts is None:
+        opts = default_opts(tau=1e-12)
+    if out is None:
+        pin = torch.cuda.is_available()
+        out = {}
+        for k in fields:
+            dt = torch.int32 if k in ("org", "src", "perm", "giv_ab", "mk", "ngiv", "sweeps", "fmm") else torch.float64
+            n = {"giv_ab": 2 * total, "giv_cs": 2 * total, "mk": nprob, "ngiv": nprob, "fmm": nprob}.get(k, total)
+            out[k] = torch.empty(max(n, 1), dtype=dt, pin_memory=pin)
+        out["status"] = torch.zeros(1, dtype=torch.int32, pin_memory=pin)
+    ro = L.Rank1Out(**{k: (_ptr(out[k]).value if k in out else None) for k, _ in L.Rank1Out._fields_})
+    code = L.lib().superdc_secular_batched_host(nprob, _ptr(offsets), total, _ptr(d), _ptr(z), float(rho),
+                                                ctypes.byref(opts), ctypes.byref(ro), _stream())
+    L.check(code, "superdc_secular_batched_host")
+    return {k: v for k, v in out.items() if k != "status"}
 
 
 # ---------------------------------------------------------------------------
@@ -175,7 +187,7 @@ class EigFactor:
         n = self.n
         nn = 2 ** level
         spec = {"dk": (n, np.float64), "eta": (n, np.float64), "dorg": (n, np.float64), "vhat": (n, np.float64),
-                "bnorm": (n, np.float64), "din": (n, np.float64), "zin": (n, np.float64), "src": (n, np.int32), "pinv": (n, np.int32), "P": (n, np.int32),
+                "bnorm": (n, np.float64), "din": (n, np.float64), "zin": (n, np.float64), "src": (n, np.int32), "pinv": (n, np.int32), "sweeps": (n, np.int32), "P": (n, np.int32),
                 "giv_cs": (2 * n, np.float64), "giv_ab": (2 * n, np.int32), "mk": (nn, np.int32),
                 "ngiv": (nn, np.int32), "fmm": (nn, np.int32)}
         cnt, dt = spec[field]

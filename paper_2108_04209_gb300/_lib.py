@@ -57,6 +57,9 @@ def lib():
         L.superdc_secular_batched.argtypes = [c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_double,
                                               ctypes.POINTER(Opts), ctypes.POINTER(Rank1Out), c_void_p]
         L.superdc_secular_batched.restype = c_int32
+        L.superdc_secular_batched_host.argtypes = [c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_double,
+                                                   ctypes.POINTER(Opts), ctypes.POINTER(Rank1Out), c_void_p]
+        L.superdc_secular_batched_host.restype = c_int32
         L.superdc_build_hss.argtypes = [ctypes.POINTER(Tree), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         ctypes.POINTER(c_void_p)]
         L.superdc_build_hss.restype = c_int32

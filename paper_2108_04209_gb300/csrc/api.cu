@@ -1,4 +1,5 @@
 // extern "C" entry points of libsuperdc (declared in include/superdc.h).
+#include <algorithm>
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "rank1.cuh"
@@ -92,6 +93,58 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
     cudaFreeAsync(a.o.wsum, stream);
     cudaFreeAsync(a.o.pinv, stream);
     return st;
+}
+
+superdc_status superdc_secular_batched_host(int64_t nprob, const int64_t *offsets, int64_t total,
+                                            const double *d, const double *z, double rho,
+                                            const superdc_opts *opts, superdc_rank1_out *out,
+                                            cudaStream_t stream)
+{
+    superdc_opts def;
+    if (!opts) { superdc_opts_default(&def); opts = &def; }
+    if (nprob < 0 || total < 0 || !(rho > 0.0) || !opts_ok(opts) || !out || !out->status) return SUPERDC_ERR_ARG;
+    if (nprob == 0) { *out->status = 0; return SUPERDC_OK; }
+    if (!offsets || !d || !z || total > INT32_MAX) return SUPERDC_ERR_ARG;
+    if (offsets[0] != 0 || offsets[nprob] != total) return SUPERDC_ERR_ARG;
+    const size_t T = (size_t)std::max<int64_t>(total, 1), NP = (size_t)nprob;
+    // one device slab: inputs, every output, status (8-byte fields first)
+    const size_t n8 = (NP + 1) + 3 * T + 6 * T + 2 * T, n4 = 3 * T + 2 * T + 2 * NP + T + 1 + NP;
+    char *slab = nullptr;
+    SDC_CHECK(sdc_alloc(&slab, n8 * 8 + n4 * 4, stream));
+    int64_t *doff = (int64_t *)slab;
+    double *dd = (double *)(doff + NP + 1), *dz = dd + T;
+    superdc_rank1_out o;
+    o.lam = dz + T; o.dk = o.lam + T; o.zk = o.dk + T; o.eta = o.zk + T; o.vhat = o.eta + T; o.bnorm = o.vhat + T;
+    o.giv_cs = o.bnorm + T;
+    int32_t *ip = (int32_t *)(o.giv_cs + 2 * T);
+    o.org = ip; o.src = o.org + T; o.perm = o.src + T; o.giv_ab = o.perm + T; o.mk = o.giv_ab + 2 * T;
+    o.ngiv = o.mk + NP; o.sweeps = o.ngiv + NP; o.status = o.sweeps + T; o.fmm = o.status + 1;
+    cudaError_t e = cudaMemcpyAsync(doff, offsets, (NP + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, d, (size_t)total * sizeof(double), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dz, z, (size_t)total * sizeof(double), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o.status, 0, sizeof(int32_t), stream);
+    superdc_status st = (e == cudaSuccess)
+        ? superdc_secular_batched(nprob, doff, total, dd, dz, rho, opts, &o, stream) : SUPERDC_ERR_CUDA;
+    // results back to the caller's host arrays (NULL fields are skipped)
+    struct Cp { void *h; const void *dv; size_t bytes; };
+    const Cp cps[] = {
+        {out->lam, o.lam, T * 8}, {out->dk, o.dk, T * 8}, {out->zk, o.zk, T * 8}, {out->eta, o.eta, T * 8},
+        {out->vhat, o.vhat, T * 8}, {out->bnorm, o.bnorm, T * 8}, {out->giv_cs, o.giv_cs, 2 * T * 8},
+        {out->org, o.org, T * 4}, {out->src, o.src, T * 4}, {out->perm, o.perm, T * 4},
+        {out->giv_ab, o.giv_ab, 2 * T * 4}, {out->mk, o.mk, NP * 4}, {out->ngiv, o.ngiv, NP * 4},
+        {out->sweeps, o.sweeps, T * 4}, {out->fmm, o.fmm, NP * 4}, {out->status, o.status, 4}};
+    if (st == SUPERDC_OK)
+        for (const Cp &c : cps)
+            if (c.h && e == cudaSuccess) e = cudaMemcpyAsync(c.h, c.dv, c.bytes, cudaMemcpyDeviceToHost, stream);
+    cudaFreeAsync(slab, stream);
+    cudaError_t es = cudaStreamSynchronize(stream);
+    if (st != SUPERDC_OK) return st;
+    if (e != cudaSuccess || es != cudaSuccess) return SUPERDC_ERR_CUDA;
+    const int32_t w = *out->status;
+    if (w & SUPERDC_DEV_NONFINITE) return SUPERDC_ERR_NONFINITE;
+    if (w & SUPERDC_DEV_NOCONV) return SUPERDC_ERR_NOCONV;
+    if (w & SUPERDC_DEV_INDEX) return SUPERDC_ERR_CUDA;
+    return SUPERDC_OK;
 }
 
 }  // extern "C"

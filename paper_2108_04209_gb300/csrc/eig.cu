@@ -1271,6 +1271,7 @@ superdc_status superdc_eigfact_get(const superdc_eigfact *f, int32_t level, int3
     else if (fld == "zin") { src = S.zin; bytes = n * 8; }
     else if (fld == "src") { src = S.src; bytes = n * 4; }
     else if (fld == "pinv") { src = S.pinv; bytes = n * 4; }
+    else if (fld == "sweeps") { src = S.sweeps; bytes = n * 4; }
     else if (fld == "P") { src = f->P[level]; bytes = n * 4; }
     else if (fld == "giv_cs") { src = S.giv_cs; bytes = 2 * n * 8; }
     else if (fld == "giv_ab") { src = S.giv_ab; bytes = 2 * n * 4; }

@@ -46,6 +46,9 @@ struct FmmDev {
     const int64_t *lev_off;                // per level: prefix of the FMM problems' box counts
     int64_t cap_f;                         // capacity of the FMM problem list
     int ncol, nfield;                      // workspace widths
+    unsigned long long *flops;             // algorithmic FP64 work of the far fields and of the
+                                           // zhat / b / Cauchy-like consumers (profiling only; NULL
+                                           // otherwise): FMA 2, other operations 1
 };
 
 struct FmmPlan {

@@ -152,6 +152,12 @@ __device__ __forceinline__ double clenshaw(const double *__restrict__ a, double 
     return fma(u, b1, a[0] - b2);
 }
 
+// algorithmic work counter (profiling): one add per box by thread 0
+__device__ __forceinline__ void fl_add(const FmmDev &pl, int64_t v)
+{
+    if (pl.flops && threadIdx.x == 0 && v > 0) atomicAdd(pl.flops, (unsigned long long)v);
+}
+
 // ---------------------------------------------------------------------------
 // Plan: which problems take the FMM path, and the prefix of their boxes.
 // ---------------------------------------------------------------------------
@@ -443,6 +449,9 @@ __global__ void __launch_bounds__(B) k_fmm_leafmom(FmmDev pl, SrcArgs a)
             for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
             pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
         }
+        // Chebyshev recurrence per source, moments, moments -> node weights
+        const int64_t cnt = max(0, min(B, jend - Tb * B));
+        fl_add(pl, cnt * ((MODE == M_LOW) ? 4 : 2) * (P - 2) + 2 * cnt * P * nw + 2 * P * P * nw);
     }
 }
 
@@ -561,6 +570,8 @@ __global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__res
             for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
             pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
         }
+        // children's node positions, the children's weights into moments, moments -> weights
+        fl_add(pl, (int64_t)nch * 2 * P * (P - 2) + (int64_t)nch * 2 * P * P * nw + 2 * P * P * nw);
     }
 }
 
@@ -607,6 +618,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
         double acc[RMAX];
 #pragma unroll
         for (int r = 0; r < RMAX; r++) acc[r] = 0.0;
+        int npair = 0;            // interaction pairs of the box (work counter)
         double f0 = 0.0;          // K_LOG: the far field at the box centre (thread 0)
         double accL = 0.0, accR = 0.0;   // K_SEC: thread t < 2P, node t % P, kernel 1/(s-t)^(1 + t/P),
                                          // sums of the boxes to the left / right
@@ -641,6 +653,7 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                 }
                 __syncthreads();
                 const int nlist = s_nlist;
+                npair += nlist;
                 for (int ii = 0; ii < nlist; ii++) {
                     const int S = s_list[ii];
                     const bool left = S < Tb;
@@ -731,6 +744,16 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
                 }
             }
         }
+        {
+            // per pair: the kernel matrix (difference and reciprocal, squared
+            // for 1/(s-t)^2) unless read back, and its products with the
+            // fields; K_LOG adds the centre's log sum and the integration
+            const bool evald = !(kmode == 2 && pl.kslots > 0);
+            const int64_t kev = evald ? ((KER == K_SEC || KER == K_2) ? 3 : 2) * P * P : 0;
+            const int64_t mv = (KER == K_SEC) ? 4 * P * P : 2 * P * P * nf;
+            const int64_t lg = (KER == K_LOG) ? 3 * P : 0;
+            fl_add(pl, npair * (kev + mv + lg) + ((KER == K_LOG && npair) ? 4 * P * P : 0));
+        }
         if (KER == K_SEC) {
             // fields: 0 psi (left, 1/(s-t)), 1 phi (right), 2 psi', 3 phi'
             if (tid < 2 * P) {
@@ -806,6 +829,9 @@ __global__ void __launch_bounds__(128) k_fmm_l2l(FmmDev pl, const int32_t *__res
             for (int t = tid; t < P * nf; t += blockDim.x) Fs[t / nf][t % nf] = 0.0;
         }
         __syncthreads();
+        // parent's node values -> coefficients -> this box's nodes; on the
+        // leaves the field -> coefficients for the targets
+        fl_add(pl, (alln ? 0 : 2 * P * (P - 2) + 4 * P * P * nf) + ((l == 0) ? 2 * P * P * nf : 0));
         if (l > 0) {
             for (int t = tid; t < P * nf; t += blockDim.x) pl.F[(g * P + t / nf) * pl.nfield + t % nf] = Fs[t / nf][t % nf];
         } else {
@@ -1357,10 +1383,12 @@ __global__ void __launch_bounds__(B) k_lowner_fmm(FmmDev pl, const int64_t *__re
         }
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
+        int64_t nsrc = 0;
         for (int s = 0; s < nn; s++) {
             const int S = near_box(pl, g, nnr, s);
             const int j0 = S * B;
             const int cnt = min(B, (m - 1) - j0);
+            nsrc += max(cnt, 0);
             __syncthreads();
             if (tid < cnt) { sd[tid] = dk[j0 + tid]; so[tid] = dorg[j0 + tid]; se[tid] = eta[j0 + tid]; }
             __syncthreads();
@@ -1383,6 +1411,9 @@ __global__ void __launch_bounds__(B) k_lowner_fmm(FmmDev pl, const int64_t *__re
             if (!isfinite(v)) sdc_latch(o.status, SUPERDC_DEV_NONFINITE);
             o.vhat[b0 + i] = (o.zk[b0 + i] < 0.0) ? -v : v;
         }
+        // near ratios (5 each, as the direct kernel), the far field's Clenshaw sum
+        const int64_t nt = max(0, min(B, m - Tb * B));
+        fl_add(pl, nt * (5 * (nsrc + 1) + 2 * P + 6));
     }
 }
 
@@ -1415,10 +1446,12 @@ __global__ void __launch_bounds__(B) k_bnorm_fmm(FmmDev pl, const int64_t *__res
         }
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
+        int64_t nsrc = 0;
         for (int q = 0; q < nn; q++) {
             const int S = near_box(pl, g, nnr, q);
             const int i0 = S * B;
             const int cnt = min(B, m - i0);
+            nsrc += max(cnt, 0);
             __syncthreads();
             if (tid < cnt) { sd[tid] = o.dk[b0 + i0 + tid]; sv[tid] = o.vhat[b0 + i0 + tid]; }
             __syncthreads();
@@ -1446,6 +1479,9 @@ __global__ void __launch_bounds__(B) k_bnorm_fmm(FmmDev pl, const int64_t *__res
             for (int q = 0; q < B; q++) a += red[q];
             pl.lastp[gl * pl.ncol] = a;
         }
+        // near terms (6 each, as the direct kernel), Clenshaw, the last target's share
+        const int64_t nt = max(0, min(B, (m - 1) - Tb * B)), ns = max(0, min(B, m - Tb * B));
+        fl_add(pl, nt * (6 * nsrc + 2 * P + 2) + ns * 7);
     }
 }
 
@@ -1517,10 +1553,12 @@ k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
         }
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
+        int64_t nsrc = 0;
         for (int s = 0; s < nn; s++) {
             const int S = near_box(pl, g, nnr, s);
             const int i0 = S * B;
             const int cnt = min(B, m - i0);
+            nsrc += max(cnt, 0);
             __syncthreads();
             if (tid < cnt) {
                 const int i = i0 + tid;
@@ -1564,6 +1602,10 @@ k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
             for (int i = 0; i < B; i++) t += sx[tid][i];
             pl.lastp[gl * pl.ncol + tid] = t;
         }
+        // near terms (difference, reciprocal, one FMA per column), Clenshaw
+        // and the scale by b per column, the last row's share per source
+        const int64_t nt = max(0, min(B, (m - 1) - Tb * B)), ns = max(0, min(B, m - Tb * B));
+        fl_add(pl, nt * (nsrc * (3 + 2 * nc) + (2 * P + 1) * nc) + ns * (4 + 2 * nc));
     }
 }
 
@@ -1610,10 +1652,12 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
         }
         const int nnr = pl.nnear[g];
         const int nn = near_len(nnr, (m + B - 1) / B);
+        int64_t nsrc = 0;
         for (int s = 0; s < nn; s++) {
             const int S = near_box(pl, g, nnr, s);
             const int j0 = S * B;
             const int cnt = min(B, (m - 1) - j0);
+            nsrc += max(cnt, 0);
             __syncthreads();
             if (tid < cnt) {
                 const int j = j0 + tid;
@@ -1640,6 +1684,10 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
             for (int q = 0; q < NC; q++)
                 if (q < nc) Y[row + (int64_t)(col0 + q) * ldy] = v * acc[q];
         }
+        // near terms and the last source (difference, reciprocal, one FMA
+        // per column), Clenshaw and the scale by vhat per column
+        const int64_t nt = max(0, min(B, m - Tb * B));
+        fl_add(pl, nt * ((nsrc + 1) * (3 + 2 * nc) + (2 * P + 1) * nc));
     }
 }
 
@@ -1762,6 +1810,7 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     d.lev_off = lev_off;
     d.cap_f = nf_cap;
 
+    d.flops = prof_counter("fmm_flops");
     d.box_base = box_base; d.leaf_base = leaf_base; d.fslot = fslot; d.fprob = fprob; d.nfmm = nfmm;
     d.blo = blo; d.bhi = bhi; d.nnear = nnear; d.near = near; d.nstart = nstart;
     PROF_LAUNCH("fmm_plan", st, k_fmm_plan<<<1, 1024, 0, st>>>(nprob, mk, min_m, pl.cap_boxes, pl.cap_leaves,

@@ -750,6 +750,41 @@ __global__ void k_merge(int64_t nprob, const int64_t *__restrict__ off, int64_t 
     }
 }
 
+// k_units sorts in dynamic shared memory beyond the default 48 KB: raise its
+// limit once per device (the attribute belongs to the device's context)
+cudaError_t units_attr()
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        e = cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(SORT_MAX * sizeof(unsigned long long)));
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
+// Secular schedule of a batch (shared by r1_run and the allocation-free
+// entry point): with many roots per CTA slot, whole problems (or 2048-root
+// pieces) go to CTAs whose warps own separate root ranges; with few roots per
+// slot (the top levels of a tree), units shrink so every SM gets work and the
+// warps of a CTA split the poles instead of the roots.  opts.sched forces
+// either mode, opts.tile_roots the unit size.
+void secular_schedule(int64_t rows, int sched, int tile_roots, int slots, bool *split, int *ubig)
+{
+    const int64_t per = rows / slots;
+    *split = (sched == 2) || (sched == 0 && per < 512);
+    *ubig = SEC_UNIT_BIG / 2;
+    if (*split) *ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
+    if (tile_roots >= 32 && tile_roots <= 4096) *ubig = (tile_roots / 32) * 32;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -773,12 +808,7 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     int *ucount = nullptr;
     SDC_CHECK(sdc_alloc(&units, a.nprob + a.total / 32 + 2, st));
     SDC_CHECK(sdc_alloc(&ucount, 2, st));
-    static bool attr_done = false;
-    if (!attr_done) {
-        SDC_CHECK(cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(SORT_MAX * sizeof(unsigned long long))));
-        attr_done = true;
-    }
+    SDC_CHECK(units_attr());
 
     const int tpb = 128;
     PROF_LAUNCH("deflate", st, k_deflate<<<(unsigned)((a.nprob + tpb - 1) / tpb), tpb, 0, st>>>(
@@ -801,16 +831,10 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     PROF_LAUNCH("tiles", st, k_tiles<<<1, 1024, 0, st>>>(a.nprob, a.o.mk, TR, tile_off));
     const unsigned grid = (unsigned)(nsm * 8);
     const size_t ksm = (a.nprob <= SORT_MAX) ? (size_t)SORT_MAX * sizeof(unsigned long long) : 0;
-    // Scheduling: with many roots per CTA slot, whole problems (or 2048-root
-    // pieces) go to CTAs whose warps own separate root ranges; with few roots
-    // per slot (the top levels of a tree), units shrink so every SM gets work
-    // and the warps of a CTA split the poles instead of the roots.
     const int slots = nsm * 6;
-    const int64_t per = (a.rows >= 0 ? a.rows : a.total) / slots;
-    const bool split = (a.sched == 2) || (a.sched == 0 && per < 512);
-    int ubig = SEC_UNIT_BIG / 2;
-    if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
-    if (a.tile_roots >= 32 && a.tile_roots <= 4096) ubig = (a.tile_roots / 32) * 32;
+    bool split;
+    int ubig;
+    secular_schedule(a.rows >= 0 ? a.rows : a.total, a.sched, a.tile_roots, slots, &split, &ubig);
     PROF_LAUNCH("units", st, k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, fslot, ubig, split ? 0 : 1, units,
                                                            ucount, ucount + 1));
     if (split)
@@ -912,7 +936,8 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     superdc_opts def;
     if (!opts) { superdc_opts_default(&def); opts = &def; }
     if (nprob < 0 || total < 0 || !(rho > 0.0) || !out) return SUPERDC_ERR_ARG;
-    if (!(opts->tau >= 0.0) || !(opts->stop_c > 0.0) || opts->max_iter < 1 || opts->max_iter > 10000)
+    if (!(opts->tau >= 0.0) || !(opts->stop_c > 0.0) || opts->max_iter < 1 || opts->max_iter > 10000 ||
+        opts->sched < 0 || opts->sched > 2)
         return SUPERDC_ERR_ARG;
     if (nprob > NA_P || total > NA_T) return SUPERDC_ERR_ARG;   // beyond the static scratch
     if (nprob == 0) return SUPERDC_OK;
@@ -925,7 +950,7 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     R1Args a;
     a.nprob = nprob; a.total = total; a.off = offsets; a.d = d; a.z = z;
     a.sqrt_rho = sqrt(rho); a.tau = opts->tau; a.stop_c = opts->stop_c; a.max_iter = opts->max_iter;
-    a.tile_roots = opts->tile_roots;
+    a.tile_roots = opts->tile_roots; a.sched = opts->sched;
     a.o.lam = out->lam; a.o.dk = out->dk; a.o.zk = out->zk; a.o.eta = out->eta;
     a.o.vhat = out->vhat; a.o.bnorm = out->bnorm; a.o.org = out->org; a.o.src = out->src;
     a.o.perm = out->perm; a.o.giv_ab = out->giv_ab; a.o.giv_cs = out->giv_cs; a.o.mk = out->mk;
@@ -941,8 +966,7 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     int32_t *surv = (int32_t *)(base + NA_SURV);
     int4 *units = (int4 *)(base + NA_UNITS);
     int *ucount = (int *)(base + NA_UCNT);
-    SDC_CHECK(cudaFuncSetAttribute(k_units, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(SORT_MAX * sizeof(unsigned long long))));
+    SDC_CHECK(units_attr());
     const int nsm = sdc_num_sms();
     const int tpb = 128;
     k_deflate<<<(unsigned)((a.nprob + tpb - 1) / tpb), tpb, 0, st>>>(a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau,
@@ -955,10 +979,9 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     const unsigned grid = (unsigned)(nsm * 8);
     const size_t ksm = (a.nprob <= SORT_MAX) ? (size_t)SORT_MAX * sizeof(unsigned long long) : 0;
     const int slots = nsm * 6;
-    const int64_t per = a.total / slots;
-    const bool split = per < 512;
-    int ubig = SEC_UNIT_BIG / 2;
-    if (split) ubig = (int)std::max<int64_t>(32, std::min<int64_t>(256, (per / 32) * 32));
+    bool split;
+    int ubig;
+    secular_schedule(a.total, a.sched, a.tile_roots, slots, &split, &ubig);
     k_units<<<1, 1024, ksm, st>>>(a.nprob, a.o.mk, nullptr, ubig, split ? 0 : 1, units, ucount, ucount + 1);
     if (split)
         k_secular<4, true><<<(unsigned)slots, 128, 0, st>>>(a.off, units, ucount, ucount + 1, a.o, a.stop_c,

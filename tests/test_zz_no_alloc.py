@@ -1,8 +1,10 @@
 """The allocation-free entry point superdc_secular_batched_noalloc, for
-callers that cannot allocate device memory while they run (graph replay,
-latency-bound paths, fixed memory budgets).  Called twice in a row through the
-C ABI; each call must match superdc_secular_batched on the same inputs.  Kept
-in a file that is collected last."""
+callers that cannot allocate device memory while they run (device memory
+reserved up front by another framework, latency-bound paths on which an
+allocation may block, plug-ins with a fixed memory footprint).  Called twice
+in a row through the C ABI; each call must match superdc_secular_batched on
+the same inputs, and the results are checked against the oracle as well.
+Kept in a file that is collected last."""
 import ctypes
 
 import numpy as np
@@ -33,28 +35,42 @@ def _call_noalloc(b, opts, out):
     return code, offs, d, z
 
 
-def test_noalloc_matches_allocating_entry_point_twice():
-    opts = sdc.default_opts(tau=1e-12)
-    batches = [inputs.secular_batch(96, 32, 2048, seed=21),           # whole-problem units
-               inputs.secular_batch(3, 20000, 30000, seed=22)]        # large problems: split mode
-    for b in batches:
-        total = int(b.offsets[-1])
-        assert total <= 262144
-        dev = torch.device("cuda")
-        ref = sdc.secular_batched(torch.from_numpy(b.offsets).to(dev), torch.from_numpy(b.d).to(dev),
-                                  torch.from_numpy(b.z).to(dev), 1.0, opts)
-        ref = {k: v.cpu().numpy() for k, v in ref.items() if v is not None}
-        for call in range(2):
-            out = sdc.alloc_rank1_out(b.nprob, total, dev)
-            code, *_ = _call_noalloc(b, opts, out)
-            assert code == 0, L.STATUS.get(code)
-            got = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
-            assert got["status"][0] == 0
-            for k in ("mk", "ngiv", "src", "perm", "org"):
-                assert np.array_equal(got[k][:len(ref[k])], ref[k]), (call, k)
-            for k in ("lam", "eta", "vhat", "bnorm", "dk"):
-                r, g = ref[k], got[k]
-                assert np.all(np.abs(g - r) <= 1e-10 * np.abs(r) + 1e-300), (call, k, np.abs(g - r).max())
+@pytest.mark.parametrize("case", ["whole_problems", "pole_split"])
+def test_noalloc_matches_allocating_entry_point_twice(case):
+    """Two calls in a row against the allocating entry point (direct evaluator:
+    fmm_min_m < 0 there, as the allocation-free path has no FMM) and against
+    the oracle.  sched = 1 runs the whole-problem units, which the automatic
+    choice does not pick below the size limit; sched = 2 the pole split."""
+    from tests import parity as P
+    if case == "whole_problems":
+        b, sched = inputs.secular_batch(96, 32, 2048, seed=21), 1
+    else:
+        b, sched = inputs.secular_batch(3, 20000, 30000, seed=22), 2
+    opts = sdc.default_opts(tau=1e-12, sched=sched)
+    total = int(b.offsets[-1])
+    assert total <= 262144
+    dev = torch.device("cuda")
+    ref = sdc.secular_batched(torch.from_numpy(b.offsets).to(dev), torch.from_numpy(b.d).to(dev),
+                              torch.from_numpy(b.z).to(dev), 1.0, sdc.default_opts(tau=1e-12, sched=sched,
+                                                                                   fmm_min_m=-1))
+    ref = {k: v.cpu().numpy() for k, v in ref.items() if v is not None}
+    for call in range(2):
+        out = sdc.alloc_rank1_out(b.nprob, total, dev)
+        out["fmm"].fill_(7)
+        code, *_ = _call_noalloc(b, opts, out)
+        assert code == 0, L.STATUS.get(code)
+        got = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+        assert got["status"][0] == 0
+        assert np.all(got["fmm"][:b.nprob] == 0)
+        for k in ("mk", "ngiv", "src", "perm", "org"):
+            assert np.array_equal(got[k][:len(ref[k])], ref[k]), (call, k)
+        for k in ("lam", "eta", "vhat", "bnorm", "dk"):
+            r, g = ref[k], got[k]
+            assert np.all(np.abs(g - r) <= 1e-10 * np.abs(r) + 1e-300), (call, k, np.abs(g - r).max())
+    # the same results against the oracle, problem by problem
+    for p in range(b.nprob):
+        d, z = b.problem(p)
+        P.compare_problem(P.gpu_problem(got, b.offsets, p), d, z, 1e-12, mode=1)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
