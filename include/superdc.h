@@ -68,6 +68,13 @@ typedef struct {
  * tile_roots = 0 (automatic), batching = 1, sched = 0, tape = 0, fmm_min_m = 0 (default crossover). */
 superdc_status superdc_opts_default(superdc_opts *opts);
 
+/* Test hook (no counterpart in the paper): from now on every device
+ * allocation the library makes that is larger than max_bytes fails as if the
+ * device were out of memory, so the SUPERDC_ERR_OOM paths can be exercised
+ * without exhausting a GPU; 0 removes the limit.  Process-wide; not meant
+ * for production use.  Negative values: SUPERDC_ERR_ARG. */
+superdc_status superdc_debug_alloc_limit(int64_t max_bytes);
+
 /* Human-readable name of a status code (static string). */
 const char *superdc_status_string(superdc_status s);
 

@@ -52,6 +52,8 @@ def lib():
         L = ctypes.CDLL(path)
         L.superdc_opts_default.argtypes = [ctypes.POINTER(Opts)]
         L.superdc_opts_default.restype = c_int32
+        L.superdc_debug_alloc_limit.argtypes = [c_int64]
+        L.superdc_debug_alloc_limit.restype = c_int32
         L.superdc_status_string.argtypes = [c_int32]
         L.superdc_status_string.restype = ctypes.c_char_p
         L.superdc_secular_batched.argtypes = [c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_double,

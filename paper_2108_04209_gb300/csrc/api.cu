@@ -1,9 +1,20 @@
 // extern "C" entry points of libsuperdc (declared in include/superdc.h).
 #include <algorithm>
+#include <atomic>
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "rank1.cuh"
 #include "fmm.cuh"
+
+namespace {
+std::atomic<int64_t> g_alloc_limit{0};
+}
+
+bool sdc_alloc_denied(size_t bytes)
+{
+    const int64_t lim = g_alloc_limit.load(std::memory_order_relaxed);
+    return lim > 0 && (int64_t)bytes > lim;
+}
 
 int sdc_num_sms()
 {
@@ -19,6 +30,13 @@ int sdc_num_sms()
 }
 
 extern "C" {
+
+superdc_status superdc_debug_alloc_limit(int64_t max_bytes)
+{
+    if (max_bytes < 0) return SUPERDC_ERR_ARG;
+    g_alloc_limit.store(max_bytes, std::memory_order_relaxed);
+    return SUPERDC_OK;
+}
 
 superdc_status superdc_opts_default(superdc_opts *opts)
 {
@@ -85,14 +103,11 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
     a.o.vhat = out->vhat; a.o.bnorm = out->bnorm; a.o.org = out->org; a.o.src = out->src;
     a.o.perm = out->perm; a.o.giv_ab = out->giv_ab; a.o.giv_cs = out->giv_cs; a.o.mk = out->mk;
     a.o.ngiv = out->ngiv; a.o.sweeps = out->sweeps; a.o.status = out->status; a.o.fmm_used = out->fmm;
-    SDC_CHECK(sdc_alloc(&a.o.dorg, total, stream));
-    SDC_CHECK(sdc_alloc(&a.o.wsum, nprob, stream));
-    SDC_CHECK(sdc_alloc(&a.o.pinv, total, stream));
-    superdc_status st = r1_run(a, stream);
-    cudaFreeAsync(a.o.dorg, stream);
-    cudaFreeAsync(a.o.wsum, stream);
-    cudaFreeAsync(a.o.pinv, stream);
-    return st;
+    SdcScratch sc(stream);
+    SDC_CHECK(sc.get(&a.o.dorg, total));
+    SDC_CHECK(sc.get(&a.o.wsum, nprob));
+    SDC_CHECK(sc.get(&a.o.pinv, total));
+    return r1_run(a, stream);
 }
 
 superdc_status superdc_secular_batched_host(int64_t nprob, const int64_t *offsets, int64_t total,

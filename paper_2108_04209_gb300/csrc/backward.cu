@@ -242,19 +242,20 @@ superdc_status r1_backward_fv(const FactorView &f, int64_t total, const double *
     const int nsm = sdc_num_sms();
     double *u = nullptr, *g = nullptr, *dbs = nullptr, *zbs = nullptr, *Y = nullptr, *Xw = nullptr;
     int64_t *tile_off = nullptr;
-    SDC_CHECK(sdc_alloc(&u, total, st));
-    SDC_CHECK(sdc_alloc(&g, total, st));
-    SDC_CHECK(sdc_alloc(&dbs, total, st));
-    SDC_CHECK(sdc_alloc(&zbs, total, st));
-    SDC_CHECK(sdc_alloc(&tile_off, f.nprob + 1, st));
+    SdcScratch sc(st);
+    SDC_CHECK(sc.get(&u, total));
+    SDC_CHECK(sc.get(&g, total));
+    SDC_CHECK(sc.get(&dbs, total));
+    SDC_CHECK(sc.get(&zbs, total));
+    SDC_CHECK(sc.get(&tile_off, f.nprob + 1));
     SDC_CHECK(cudaMemsetAsync(u, 0, total * sizeof(double), st));
     SDC_CHECK(cudaMemsetAsync(g, 0, total * sizeof(double), st));
     k_tiles_b<<<1, 1024, 0, st>>>(f.nprob, f.mk, TB, tile_off);
     superdc_status s = SUPERDC_OK;
     if (ncols > 0) {
         // Y = Qhat^T X is recomputed (the rotations act on a copy of X)
-        SDC_CHECK(sdc_alloc(&Y, (size_t)total * ncols, st));
-        SDC_CHECK(sdc_alloc(&Xw, (size_t)total * ncols, st));
+        SDC_CHECK(sc.get(&Y, (size_t)total * ncols));
+        SDC_CHECK(sc.get(&Xw, (size_t)total * ncols));
         SDC_CHECK(cudaMemcpy2DAsync(Xw, total * sizeof(double), X, ldx * sizeof(double), total * sizeof(double),
                                     ncols, cudaMemcpyDeviceToDevice, st));
         s = cauchy_apply_T(f, total, Xw, total, Y, total, ncols, st);
@@ -271,10 +272,6 @@ superdc_status r1_backward_fv(const FactorView &f, int64_t total, const double *
                                                                     f.giv_ab, f.giv_cs, lam_bar, dbs, zbs, sqrt_rho,
                                                                     d_bar, z_bar);
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(u, st); cudaFreeAsync(g, st);
-    cudaFreeAsync(dbs, st); cudaFreeAsync(zbs, st); cudaFreeAsync(tile_off, st);
-    if (Y) cudaFreeAsync(Y, st);
-    if (Xw) cudaFreeAsync(Xw, st);
     if (s != SUPERDC_OK) return s;
     return e == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
 }
@@ -293,19 +290,16 @@ extern "C" superdc_status superdc_secular_batched_backward(
     const int nsm = sdc_num_sms();
     int32_t *pinv = nullptr;
     double *dorg = nullptr;
-    SDC_CHECK(sdc_alloc(&pinv, total, st));
-    SDC_CHECK(sdc_alloc(&dorg, total, st));
+    SdcScratch sc(st);
+    SDC_CHECK(sc.get(&pinv, total));
+    SDC_CHECK(sc.get(&dorg, total));
     k_prep<<<(unsigned)(nsm * 8), 256, 0, st>>>(nprob, offsets, total, fwd->mk, fwd->perm, fwd->org, fwd->dk, pinv,
                                                  dorg);
     FactorView f;
     f.nprob = nprob; f.off = offsets; f.mk = fwd->mk; f.ngiv = fwd->ngiv; f.dk = fwd->dk; f.eta = fwd->eta;
     f.dorg = dorg; f.vhat = fwd->vhat; f.bnorm = fwd->bnorm; f.src = fwd->src; f.perm = fwd->perm; f.pinv = pinv;
     f.giv_ab = fwd->giv_ab; f.giv_cs = fwd->giv_cs;
-    superdc_status s = r1_backward_fv(f, total, lam_bar, (int)ncols, X, ldx, Ybar, ldy, d_bar, z_bar, X_bar, ldxb,
-                                      sqrt(rho), st);
-    cudaFreeAsync(pinv, st);
-    cudaFreeAsync(dorg, st);
-    return s;
+    return r1_backward_fv(f, total, lam_bar, (int)ncols, X, ldx, Ybar, ldy, d_bar, z_bar, X_bar, ldxb, sqrt(rho), st);
 }
 
 extern "C" superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offsets, int64_t total,
@@ -324,8 +318,9 @@ extern "C" superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offs
     const int nsm = sdc_num_sms();
     int32_t *pinv = nullptr;
     double *dorg = nullptr, *Xw = nullptr;
-    SDC_CHECK(sdc_alloc(&pinv, total, st));
-    SDC_CHECK(sdc_alloc(&dorg, total, st));
+    SdcScratch sc(st);
+    SDC_CHECK(sc.get(&pinv, total));
+    SDC_CHECK(sc.get(&dorg, total));
     k_prep<<<(unsigned)(nsm * 8), 256, 0, st>>>(nprob, offsets, total, fwd->mk, fwd->perm, fwd->org, fwd->dk, pinv,
                                                  dorg);
     FactorView f;
@@ -335,7 +330,7 @@ extern "C" superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offs
     f.fmm_min_m = fmm_resolve(opts->fmm_min_m);
     superdc_status s;
     if (trans) {
-        SDC_CHECK(sdc_alloc(&Xw, (size_t)total * ncols, st));
+        SDC_CHECK(sc.get(&Xw, (size_t)total * ncols));
         SDC_CHECK(cudaMemcpy2DAsync(Xw, total * sizeof(double), X, ldx * sizeof(double), total * sizeof(double),
                                     ncols, cudaMemcpyDeviceToDevice, st));
         s = cauchy_apply_T(f, total, Xw, total, Y, ldy, (int)ncols, st);
@@ -343,9 +338,6 @@ extern "C" superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offs
         s = cauchy_apply_N(f, total, X, ldx, Y, ldy, (int)ncols, st);
     }
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(pinv, st);
-    cudaFreeAsync(dorg, st);
-    if (Xw) cudaFreeAsync(Xw, st);
     if (s != SUPERDC_OK) return s;
     return e == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
 }

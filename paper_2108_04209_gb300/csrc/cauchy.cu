@@ -279,7 +279,8 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
     if (ncols <= 0 || total <= 0) return SUPERDC_OK;
     const int nsm = sdc_num_sms();
     int64_t *tile_off = nullptr;
-    SDC_CHECK(sdc_alloc(&tile_off, f.nprob + 1, st));
+    SdcScratch sc(st);
+    SDC_CHECK(sc.get(&tile_off, f.nprob + 1));
     k_tiles_c<<<1, 1024, 0, st>>>(f.nprob, f.mk, TJ, tile_off);
     const int gthreads = 128;
     if (trans)
@@ -296,7 +297,7 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
         // (P^2 per column and box pair) dominate and boxes of 64 halve those
         superdc_status fs = fmm_plan(fp, f.nprob, f.off, total, f.max_m, f.mk, f.dk, f.fmm_min_m, w, w, nullptr,
                                      box, 0, st);
-        if (fs != SUPERDC_OK) { fmm_free(fp, st); cudaFreeAsync(tile_off, st); return fs; }
+        if (fs != SUPERDC_OK) { fmm_free(fp, st); return fs; }
     }
     const FmmPlan &pl = use_shared ? *shared : fp;
     const int32_t *fslot = pl.on ? pl.dv.fslot : nullptr;
@@ -312,9 +313,9 @@ superdc_status run(const FactorView &f, int64_t total, double *Xmut, const doubl
                                                                                   trans ? 1 : 0));
     if (!trans)
         PROF_LAUNCH("givens", st, k_givens<<<(unsigned)(nsm * 8), gthreads, 0, st>>>(f, total, Y, ldy, ncols, 1));
-    SDC_CHECK(cudaGetLastError());
-    SDC_CHECK(cudaFreeAsync(tile_off, st));
+    const cudaError_t le = cudaGetLastError();
     fmm_free(fp, st);
+    if (le != cudaSuccess) return SUPERDC_ERR_CUDA;
     return fs;
 }
 

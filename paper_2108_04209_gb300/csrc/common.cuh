@@ -33,10 +33,45 @@ __device__ __forceinline__ int64_t sdc_upper_index(const T *__restrict__ a, int6
 // Number of SMs of the current device (cached per device by the caller).
 int sdc_num_sms();
 
+// Test hook of superdc_debug_alloc_limit: true when an allocation of this
+// many bytes must fail as if the device were out of memory.
+bool sdc_alloc_denied(size_t bytes);
+
 // Stream-ordered scratch allocation helpers.
 template <typename T>
 static inline cudaError_t sdc_alloc(T **p, size_t count, cudaStream_t st)
 {
     if (count == 0) count = 1;
+    if (sdc_alloc_denied(count * sizeof(T))) return cudaErrorMemoryAllocation;
     return cudaMallocAsync((void **)p, count * sizeof(T), st);
 }
+
+// Synchronous allocation (handles that outlive the call).
+template <typename T>
+static inline cudaError_t sdc_malloc(T **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 1;
+    if (sdc_alloc_denied(bytes)) return cudaErrorMemoryAllocation;
+    return cudaMalloc((void **)p, bytes);
+}
+
+// Stream-ordered scratch of one call: every buffer taken through get() is
+// released on the stream (cudaFreeAsync) when the holder goes out of scope,
+// on the error paths as on the normal one.
+struct SdcScratch {
+    cudaStream_t st;
+    void *p[16];
+    int n = 0;
+    explicit SdcScratch(cudaStream_t s) : st(s) {}
+    template <typename T>
+    cudaError_t get(T **ptr, size_t count)
+    {
+        if (n >= 16) return cudaErrorInvalidValue;
+        cudaError_t e = sdc_alloc(ptr, count, st);
+        if (e == cudaSuccess) p[n++] = (void *)*ptr;
+        return e;
+    }
+    ~SdcScratch() { for (int i = 0; i < n; i++) cudaFreeAsync(p[i], st); }
+    SdcScratch(const SdcScratch &) = delete;
+    SdcScratch &operator=(const SdcScratch &) = delete;
+};

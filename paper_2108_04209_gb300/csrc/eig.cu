@@ -33,7 +33,7 @@ namespace {
 template <typename T>
 cudaError_t dalloc(T **p, size_t n, std::vector<char *> *own)
 {
-    cudaError_t e = cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+    cudaError_t e = sdc_malloc(p, std::max<size_t>(n, 1) * sizeof(T));
     if (e == cudaSuccess && own) own->push_back((char *)*p);
     return e;
 }
@@ -879,18 +879,18 @@ superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, cons
     const int rr = r * r;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
-    chk(cudaMalloc(&h->D, dsz * sizeof(double)));
-    chk(cudaMalloc(&h->U, usz * sizeof(double)));
-    chk(cudaMalloc(&h->R, (size_t)nn * rr * sizeof(double)));
-    chk(cudaMalloc(&h->B, (size_t)nn * rr * sizeof(double)));
-    chk(cudaMalloc(&h->d_lch, nn * sizeof(int32_t)));
-    chk(cudaMalloc(&h->d_rch, nn * sizeof(int32_t)));
-    chk(cudaMalloc(&h->d_size, nn * sizeof(int64_t)));
-    chk(cudaMalloc(&h->d_leaf_off, h->nleaves * sizeof(int64_t)));
-    chk(cudaMalloc(&h->d_leaf_m, h->nleaves * sizeof(int64_t)));
-    chk(cudaMalloc(&h->d_leaf_doff, h->nleaves * sizeof(int64_t)));
-    chk(cudaMalloc(&h->d_leaf_uoff, h->nleaves * sizeof(int64_t)));
-    chk(cudaMalloc(&h->d_leaf_id, h->nleaves * sizeof(int32_t)));
+    chk(sdc_malloc(&h->D, dsz * sizeof(double)));
+    chk(sdc_malloc(&h->U, usz * sizeof(double)));
+    chk(sdc_malloc(&h->R, (size_t)nn * rr * sizeof(double)));
+    chk(sdc_malloc(&h->B, (size_t)nn * rr * sizeof(double)));
+    chk(sdc_malloc(&h->d_lch, nn * sizeof(int32_t)));
+    chk(sdc_malloc(&h->d_rch, nn * sizeof(int32_t)));
+    chk(sdc_malloc(&h->d_size, nn * sizeof(int64_t)));
+    chk(sdc_malloc(&h->d_leaf_off, h->nleaves * sizeof(int64_t)));
+    chk(sdc_malloc(&h->d_leaf_m, h->nleaves * sizeof(int64_t)));
+    chk(sdc_malloc(&h->d_leaf_doff, h->nleaves * sizeof(int64_t)));
+    chk(sdc_malloc(&h->d_leaf_uoff, h->nleaves * sizeof(int64_t)));
+    chk(sdc_malloc(&h->d_leaf_id, h->nleaves * sizeof(int32_t)));
     if (e != cudaSuccess) { superdc_hss_free(h); return e == cudaErrorMemoryAllocation ? SUPERDC_ERR_OOM : SUPERDC_ERR_CUDA; }
     chk(cudaMemcpyAsync(h->D, D, dsz * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     chk(cudaMemcpyAsync(h->U, U, usz * sizeof(double), cudaMemcpyDeviceToDevice, stream));
@@ -911,8 +911,8 @@ superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, cons
         std::vector<int64_t> lo;
         for (int i : h->lev_nodes[l]) lo.push_back(h->off[i]);
         lo.push_back(h->n);
-        chk(cudaMalloc(&h->d_lev_off[l], lo.size() * sizeof(int64_t)));
-        chk(cudaMalloc(&h->d_lev_nodes[l], h->lev_nodes[l].size() * sizeof(int32_t)));
+        chk(sdc_malloc(&h->d_lev_off[l], lo.size() * sizeof(int64_t)));
+        chk(sdc_malloc(&h->d_lev_nodes[l], h->lev_nodes[l].size() * sizeof(int32_t)));
         if (e != cudaSuccess) break;
         chk(cudaMemcpyAsync(h->d_lev_off[l], lo.data(), lo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
         chk(cudaMemcpyAsync(h->d_lev_nodes[l], h->lev_nodes[l].data(), h->lev_nodes[l].size() * sizeof(int32_t),
@@ -1178,8 +1178,9 @@ superdc_status superdc_apply_Q(const superdc_eigfact *f, int32_t trans, int64_t 
     const int nc = (int)ncols;
     const int nsm = sdc_num_sms();
     double *B0 = nullptr, *B1 = nullptr;
-    SDC_CHECK(sdc_alloc(&B0, (size_t)n * nc, st));
-    SDC_CHECK(sdc_alloc(&B1, (size_t)n * nc, st));
+    SdcScratch sc(st);
+    SDC_CHECK(sc.get(&B0, (size_t)n * nc));
+    SDC_CHECK(sc.get(&B1, (size_t)n * nc));
     const unsigned g = (unsigned)(nsm * 8);
     superdc_status s = SUPERDC_OK;
     if (trans) {
@@ -1212,8 +1213,6 @@ superdc_status superdc_apply_Q(const superdc_eigfact *f, int32_t trans, int64_t 
             n, h->d_leaf_off, h->d_leaf_m, f->Qleaf, f->d_qoff, B0, n, Y, ldy, nc, 0));
     }
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(B0, st);
-    cudaFreeAsync(B1, st);
     if (s != SUPERDC_OK) return s;
     return e == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
 }

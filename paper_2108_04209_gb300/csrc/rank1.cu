@@ -797,17 +797,18 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     double *wd = nullptr, *wz = nullptr;
     int8_t *kept = nullptr;
     int64_t *tile_off = nullptr;
-    SDC_CHECK(sdc_alloc(&wd, a.total, st));
-    SDC_CHECK(sdc_alloc(&wz, a.total, st));
-    SDC_CHECK(sdc_alloc(&kept, a.total, st));
-    SDC_CHECK(sdc_alloc(&tile_off, a.nprob + 1, st));
+    SdcScratch sc(st);
+    SDC_CHECK(sc.get(&wd, a.total));
+    SDC_CHECK(sc.get(&wz, a.total));
+    SDC_CHECK(sc.get(&kept, a.total));
+    SDC_CHECK(sc.get(&tile_off, a.nprob + 1));
     int32_t *surv = nullptr;
-    SDC_CHECK(sdc_alloc(&surv, a.total, st));
-    SDC_CHECK(sdc_alloc(&a.o.lamk, a.total, st));
+    SDC_CHECK(sc.get(&surv, a.total));
+    SDC_CHECK(sc.get(&a.o.lamk, a.total));
     int4 *units = nullptr;
     int *ucount = nullptr;
-    SDC_CHECK(sdc_alloc(&units, a.nprob + a.total / 32 + 2, st));
-    SDC_CHECK(sdc_alloc(&ucount, 2, st));
+    SDC_CHECK(sc.get(&units, a.nprob + a.total / 32 + 2));
+    SDC_CHECK(sc.get(&ucount, 2));
     SDC_CHECK(units_attr());
 
     const int tpb = 128;
@@ -849,16 +850,8 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     PROF_LAUNCH("bnorm", st, k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, fslot));
     if (fs == SUPERDC_OK) fs = fmm_bnorm(fp, a.off, a.o, st);
     PROF_LAUNCH("merge", st, k_merge<<<(unsigned)(nsm * 8), 256, 0, st>>>(a.nprob, a.off, a.total, a.o));
-    SDC_CHECK(cudaGetLastError());
-
-    SDC_CHECK(cudaFreeAsync(wd, st));
-    SDC_CHECK(cudaFreeAsync(wz, st));
-    SDC_CHECK(cudaFreeAsync(kept, st));
-    SDC_CHECK(cudaFreeAsync(tile_off, st));
-    SDC_CHECK(cudaFreeAsync(units, st));
-    SDC_CHECK(cudaFreeAsync(surv, st));
-    SDC_CHECK(cudaFreeAsync(a.o.lamk, st));
-    SDC_CHECK(cudaFreeAsync(ucount, st));
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) { fmm_free(fp, st); return SUPERDC_ERR_CUDA; }
     if (a.keep && fs == SUPERDC_OK) *a.keep = fp;
     else fmm_free(fp, st);
     return fs;
