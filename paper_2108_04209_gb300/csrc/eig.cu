@@ -380,6 +380,54 @@ __device__ __forceinline__ void ql_pair(double f, double g, double &c, double &s
     }
 }
 
+// One implicit QL sweep on the unreduced block [l, h] of a symmetric
+// tridiagonal matrix (diagonal a[i * S], off-diagonal b[i * S] coupling i and
+// i + 1): the implicit symmetric QR step with Wilkinson's shift of Golub and
+// Van Loan (Section 8.3), in its QL orientation.  The shift mu is the
+// eigenvalue of the leading 2 x 2 block nearer to a_l; the first rotation, in
+// plane (h-1, h), has its second column along the last column of T - mu I
+// restricted to rows h-1, h, i.e. along (b_{h-1}, a_h - mu); every later
+// rotation, in plane (i, i+1), removes the bulge at (i, i+2) that the
+// previous one left, against the entry b_{i+1}.  A rotation G with G(i,i) =
+// G(i+1,i+1) = c, G(i,i+1) = s, G(i+1,i) = -s acts as T <- G^T T G:
+//   a_i     <- c^2 a_i - 2 c s b_i + s^2 a_{i+1}
+//   a_{i+1} <- s^2 a_i + 2 c s b_i + c^2 a_{i+1}
+//   b_i     <- c s (a_i - a_{i+1}) + (c^2 - s^2) b_i
+//   b_{i-1} <- c b_{i-1}, and the new bulge at (i-1, i+1) is s b_{i-1}.
+// rec(q, c, s) records rotation q (plane (h-1-q, h-q)): the eigenvectors are
+// Q <- Q G, i.e. columns (x_i, x_{i+1}) <- (c x_i - s x_{i+1}, s x_i + c x_{i+1}).
+// Returns the number of rotations (h - l).
+template <int S, typename Rec>
+__device__ __forceinline__ int ql_sweep_tri(double *a, double *b, int l, int h, Rec rec)
+{
+    const double al = a[l * S], bl = b[l * S];
+    const double del = 0.5 * (a[(l + 1) * S] - al);
+    const double mu = al - bl * bl / (del + copysign(hypot(del, bl), del));
+    double x = a[h * S] - mu, z = b[(h - 1) * S];
+    int q = 0;
+    for (int i = h - 1; i >= l; i--, q++) {
+        double c, s, r;
+        ql_pair(z, x, c, s, r);                 // c = x / r, s = z / r
+        if (!(r > 0.0)) { c = 1.0; s = 0.0; r = x; }
+        if (i < h - 1) b[(i + 1) * S] = r;      // the bulge is gone
+        const double ai = a[i * S], ai1 = a[(i + 1) * S], bi = b[i * S];
+        const double cc = c * c, ss = s * s, cs = c * s;
+        const double t2 = 2.0 * cs * bi;
+        a[i * S] = fma(cc, ai, fma(ss, ai1, -t2));
+        a[(i + 1) * S] = fma(ss, ai, fma(cc, ai1, t2));
+        const double bn = fma(cs, ai - ai1, (cc - ss) * bi);
+        b[i * S] = bn;
+        rec(q, c, s);
+        if (i > l) {
+            const double bm = b[(i - 1) * S];
+            z = s * bm;                         // bulge at (i-1, i+1)
+            b[(i - 1) * S] = c * bm;
+            x = bn;
+        }
+    }
+    return q;
+}
+
 // Implicit QL on the tridiagonal (d, e) of every leaf, one lane per leaf; d
 // and e staged in shared memory ([index][lane]).  Sweep t of leaf L records
 // its first column and count in hdr[L * caps + t] and its rotations (c, s) in
@@ -413,28 +461,12 @@ k_leaf_ql(int nleaves, int mmax, const int64_t *__restrict__ leaf_off, const int
             }
             if (mm == l) break;
             if (iter >= 64 || nsweep >= caps || nrot + (mm - l) > cap) { bad = true; break; }
-            double g = (sd[(l + 1) * 32 + lane] - sd[l * 32 + lane]) / (2.0 * se[l * 32 + lane]);
-            double rr = hypot(g, 1.0);
-            g = sd[mm * 32 + lane] - sd[l * 32 + lane] + se[l * 32 + lane] / (g + ((g >= 0.0) ? rr : -rr));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int cnt = 0;
-            bool under = false;
-            for (int i = mm - 1; i >= l; i--) {
-                const double ei = se[i * 32 + lane];
-                const double f = s * ei, bb = c * ei;
-                ql_pair(f, g, c, s, rr);
-                se[(i + 1) * 32 + lane] = rr;
-                if (rr == 0.0) { sd[(i + 1) * 32 + lane] -= p; se[mm * 32 + lane] = 0.0; under = true; break; }
-                g = sd[(i + 1) * 32 + lane] - p;
-                rr = (sd[i * 32 + lane] - g) * s + 2.0 * c * bb;
-                p = s * rr;
-                sd[(i + 1) * 32 + lane] = g + p;
-                g = c * rr - bb;
-                R[nrot + cnt] = make_double2(c, s);
-                cnt++;
-            }
-            if (!under) { sd[l * 32 + lane] -= p; se[l * 32 + lane] = g; se[mm * 32 + lane] = 0.0; }
-            if (cnt > 0) { Hd[nsweep] = make_int2(mm - 1, cnt); nsweep++; nrot += cnt; }
+            double2 *Rs = R + nrot;
+            const int cnt = ql_sweep_tri<32>(sd + lane, se + lane, l, mm,
+                                             [&](int q, double c, double s) { Rs[q] = make_double2(c, s); });
+            Hd[nsweep] = make_int2(mm - 1, cnt);
+            nsweep++;
+            nrot += cnt;
         }
     }
     if (act) {
@@ -591,27 +623,7 @@ k_leaf_qlcta(int r, int64_t n, const int64_t *__restrict__ leaf_off, const int64
                 continue;
             }
             ql_iter++;
-            double g = (dg[l + 1] - dg[l]) / (2.0 * ee[l]);
-            double rr = hypot(g, 1.0);
-            g = dg[mm] - dg[l] + ee[l] / (g + ((g >= 0.0) ? rr : -rr));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int cnt = 0;
-            bool under = false;
-            for (int i = mm - 1; i >= l; i--) {
-                const double f = s * ee[i], bb = c * ee[i];
-                ql_pair(f, g, c, s, rr);
-                ee[i + 1] = rr;
-                if (rr == 0.0) { dg[i + 1] -= p; ee[mm] = 0.0; under = true; break; }
-                g = dg[i + 1] - p;
-                rr = (dg[i] - g) * s + 2.0 * c * bb;
-                p = s * rr;
-                dg[i + 1] = g + p;
-                g = c * rr - bb;
-                bc[cnt] = c;
-                bs[cnt] = s;
-                cnt++;
-            }
-            if (!under) { dg[l] -= p; ee[l] = g; ee[mm] = 0.0; }
+            const int cnt = ql_sweep_tri<1>(dg, ee, l, mm, [&](int q, double c, double s) { bc[q] = c; bs[q] = s; });
             s_first_b[b] = mm - 1;
             return cnt;
         }
