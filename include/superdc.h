@@ -262,6 +262,26 @@ superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, cons
                                  superdc_hss **out);
 void superdc_hss_free(superdc_hss *h);
 
+/* Complex Hermitian HSS matrix (the extension the paper notes in Section 1:
+ * its real symmetric treatment carries over to the Hermitian case).  Same
+ * tree and packing as superdc_build_hss, but every generator entry is
+ * complex, stored as an (re, im) pair of doubles (column-major blocks of
+ * pairs): D_i Hermitian, A(i, j) = U_i B_i U_j^H for a left child i and its
+ * sibling j, nested U_p = [U_i R_i; U_j R_j].  The handle holds the real form
+ * of A: every complex block M becomes [[Re M, -Im M], [Im M, Re M]] and the
+ * rows of every leaf are ordered [Re rows; Im rows], which keeps the tree and
+ * gives a real symmetric HSS matrix of order 2n, leaves 2m_i, rank 2r (so
+ * 2 m_i <= 128 and 2r <= 32).  Its eigenvalues are those of A, each twice
+ * (superdc_eig returns 2n values, pairs equal up to rounding); for a real
+ * function f, superdc_apply_function applies f(A) to complex columns in the
+ * same real layout ([Re x_leaf; Im x_leaf] per leaf), and column 2k of the
+ * real Q read as x = (first half of each leaf's rows) + i (second half) is
+ * a unit eigenvector of A for the k-th eigenvalue when that eigenvalue is
+ * simple. */
+superdc_status superdc_build_hss_hermitian(const superdc_tree *tree, const double *D, const double *U,
+                                           const double *R, const double *B, cudaStream_t stream,
+                                           superdc_hss **out);
+
 /* Eigendecomposition A = Q diag(lambda) Q^T (Algorithms 1-3):
  *   dividing stage (Algorithm 1, balanced eqs. (3.11)/(3.12), generator
  *   updates of Lemma 2.1); leaf eigendecompositions (Householder
@@ -304,6 +324,18 @@ superdc_status superdc_eig_backward(const superdc_hss *h, const superdc_eigfact 
                                     const double *lambda_bar, int64_t k, const double *V, int64_t ldv,
                                     const double *Ybar, int64_t ldy, double *gD, double *gU, double *gR,
                                     double *gB, double *gV, int64_t ldgv, cudaStream_t stream);
+
+/* Matrix function of A applied to a block (the use of the structured
+ * eigendecomposition the paper's introduction motivates, Section 1):
+ * Y = Q diag(fvals) Q^T X, i.e. f(A) X when fvals[i] = f(lambda_i) for the
+ * eigenvalues in the ascending order superdc_eig returned them.  fvals: DEVICE,
+ * n entries (any real function values: exp(-t lambda), 1/(lambda - sigma),
+ * a spectral window, ...).  X, Y: DEVICE, n x ncols column-major, ld >= n,
+ * not overlapping.  Two Algorithm 4 sweeps (Q^T, then Q) and a row scaling;
+ * work buffers from the stream-ordered allocator. */
+superdc_status superdc_apply_function(const superdc_eigfact *f, const double *fvals, int64_t ncols,
+                                      const double *X, int64_t ldx, double *Y, int64_t ldy,
+                                      cudaStream_t stream);
 
 /* FMM threshold of later superdc_apply_Q calls on this factor (same meaning
  * as superdc_opts.fmm_min_m; superdc_eig sets it from its options).  The

@@ -27,6 +27,31 @@ def dense_from_hss(h) -> np.ndarray:
     return A
 
 
+def dense_from_hss_hermitian(h) -> np.ndarray:
+    """Complex Hermitian HSS matrix from complex generators: A(i, j) =
+    U_i B_i U_j^H for a left child i and its sibling j, the conjugate
+    transpose below the diagonal, nested U_p = [U_i R_i; U_j R_j]."""
+    t = h.tree
+    n = t.n
+    A = np.zeros((n, n), np.complex128)
+    Ubig = {}
+    for i in range(t.nnodes):
+        o, m = int(t.offset[i]), int(t.leaf_size[i])
+        if t.lchild[i] < 0:
+            A[o:o + m, o:o + m] = h.leaf_D(i)
+            Ubig[i] = h.leaf_U(i).copy()
+            continue
+        a, b = int(t.lchild[i]), int(t.rchild[i])
+        oa, ma = int(t.offset[a]), int(t.leaf_size[a])
+        ob, mb = int(t.offset[b]), int(t.leaf_size[b])
+        blk = Ubig[a] @ h.B[a] @ Ubig[b].conj().T
+        A[oa:oa + ma, ob:ob + mb] = blk
+        A[ob:ob + mb, oa:oa + ma] = blk.conj().T
+        if i != t.root:
+            Ubig[i] = np.vstack([Ubig[a] @ h.R[a], Ubig[b] @ h.R[b]])
+    return A
+
+
 def gamma(A, lam, Q):
     """max_k ||A q_k - lam_k q_k|| / (n ||A||_2)"""
     n = A.shape[0]

@@ -109,26 +109,29 @@ class HSSMatrix:
     ``h`` is an ``inputs.HSS`` (tree + generators); the generators are copied
     to the GPU and then into the library handle."""
 
-    def __init__(self, h, device=None, tensors=None):
+    def __init__(self, h, device=None, tensors=None, hermitian=False):
+        """``hermitian``: ``h`` holds complex Hermitian generators; the handle
+        is the real form of order 2n (superdc_build_hss_hermitian)."""
         import numpy as np
         dev = torch.device(device or "cuda")
         t = h.tree if hasattr(h, "tree") else h
-        self.n, self.rank = int(t.n), int(t.rank)
+        self.hermitian = bool(hermitian)
+        self.n, self.rank = int(t.n) * (2 if hermitian else 1), int(t.rank) * (2 if hermitian else 1)
         self.tree = t
         self._lch = np.ascontiguousarray(t.lchild, np.int32)
         self._rch = np.ascontiguousarray(t.rchild, np.int32)
         self._sz = np.ascontiguousarray(t.leaf_size, np.int64)
-        tree = L.Tree(self.n, int(t.nnodes), self._lch.ctypes.data, self._rch.ctypes.data,
-                      self._sz.ctypes.data, self.rank)
+        tree = L.Tree(int(t.n), int(t.nnodes), self._lch.ctypes.data, self._rch.ctypes.data,
+                      self._sz.ctypes.data, int(t.rank))
         if tensors is not None:
             D, U, R, B = (x.detach().contiguous() for x in tensors)
         else:
             D, U, R, B = (torch.from_numpy(x).to(dev) for x in h.packed())
         self.sizes = (D.numel(), U.numel(), R.numel(), B.numel())
         self._h = ctypes.c_void_p()
-        code = L.lib().superdc_build_hss(ctypes.byref(tree), _ptr(D), _ptr(U), _ptr(R), _ptr(B), _stream(),
-                                         ctypes.byref(self._h))
-        L.check(code, "superdc_build_hss")
+        build = L.lib().superdc_build_hss_hermitian if hermitian else L.lib().superdc_build_hss
+        code = build(ctypes.byref(tree), _ptr(D), _ptr(U), _ptr(R), _ptr(B), _stream(), ctypes.byref(self._h))
+        L.check(code, "superdc_build_hss_hermitian" if hermitian else "superdc_build_hss")
 
     def eig(self, opts=None):
         """Eigendecomposition; returns (lambda [n] device tensor ascending, EigFactor)."""
@@ -171,6 +174,21 @@ class EigFactor:
         code = L.lib().superdc_apply_Q(self._f, 1 if trans else 0, k, _ptr(Xf), ldx, _ptr(Y),
                                        self.n, _stream())
         L.check(code, "superdc_apply_Q")
+        return Y.reshape(-1) if vec else Y
+
+    def apply_function(self, fvals, X):
+        """f(A) X = Q diag(fvals) Q^T X (superdc_apply_function); fvals: float64
+        CUDA tensor of f(lambda_i) for the ascending eigenvalues; X: n or n x k."""
+        vec = X.dim() == 1
+        Xc = X.reshape(self.n, -1)
+        Xf = Xc.t().contiguous().t() if not Xc.t().is_contiguous() else Xc
+        k = Xf.shape[1]
+        fv = fvals.contiguous()
+        assert fv.numel() == self.n and fv.dtype == torch.float64 and fv.is_cuda
+        Y = torch.empty((k, self.n), dtype=torch.float64, device=X.device).t()
+        ldx = Xf.stride(1) if k > 1 else self.n
+        code = L.lib().superdc_apply_function(self._f, _ptr(fv), k, _ptr(Xf), ldx, _ptr(Y), self.n, _stream())
+        L.check(code, "superdc_apply_function")
         return Y.reshape(-1) if vec else Y
 
     def set_fmm_min_m(self, fmm_min_m):

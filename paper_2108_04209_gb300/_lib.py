@@ -65,6 +65,9 @@ def lib():
         L.superdc_build_hss.argtypes = [ctypes.POINTER(Tree), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         ctypes.POINTER(c_void_p)]
         L.superdc_build_hss.restype = c_int32
+        L.superdc_build_hss_hermitian.argtypes = [ctypes.POINTER(Tree), c_void_p, c_void_p, c_void_p, c_void_p,
+                                                  c_void_p, ctypes.POINTER(c_void_p)]
+        L.superdc_build_hss_hermitian.restype = c_int32
         L.superdc_hss_free.argtypes = [c_void_p]
         L.superdc_hss_free.restype = None
         L.superdc_eig.argtypes = [c_void_p, ctypes.POINTER(Opts), c_void_p, c_void_p, ctypes.POINTER(c_void_p)]
@@ -73,6 +76,9 @@ def lib():
         L.superdc_eigfact_free.restype = None
         L.superdc_apply_Q.argtypes = [c_void_p, c_int32, c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p]
         L.superdc_apply_Q.restype = c_int32
+        L.superdc_apply_function.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int64,
+                                             c_void_p]
+        L.superdc_apply_function.restype = c_int32
         L.superdc_eigfact_set_fmm_min_m.argtypes = [c_void_p, c_int32]
         L.superdc_eigfact_set_fmm_min_m.restype = c_int32
         L.superdc_sync_status.argtypes = [c_void_p]

@@ -761,6 +761,17 @@ __global__ void k_copy_cols(int64_t n, int ncols, const double *__restrict__ X, 
     }
 }
 
+// Y(:, col) = fv .* Y(:, col) (rows scaled by the function values)
+__global__ void k_scale_rows(int64_t n, int ncols, const double *__restrict__ fv, double *__restrict__ Y, int64_t ldy)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * ncols;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = t % n;
+        const int col = (int)(t / n);
+        Y[x + ldy * col] *= fv[x];
+    }
+}
+
 __global__ void k_stats(int64_t nprob, const int64_t *__restrict__ off, const int32_t *__restrict__ mk,
                         const int32_t *__restrict__ sweeps, unsigned long long *acc)
 {
@@ -815,6 +826,32 @@ FactorView view(const superdc_eigfact *f, int l, int j)
 }  // namespace
 
 extern "C" {
+
+// Real form of complex blocks: a complex rows x cols block M (column-major,
+// entries as (re, im) pairs) becomes the real 2rows x 2cols block
+// [[Re M, -Im M], [Im M, Re M]] (column-major).  One launch covers nblk
+// blocks; block b starts at in + 2 ioff[b], out + ooff[b], with rows[b] rows
+// and cols columns (cols = 0: square, cols = rows[b]).
+__global__ void k_realify(int nblk, const int64_t *__restrict__ ioff, const int64_t *__restrict__ ooff,
+                          const int32_t *__restrict__ rows, int cols_in, const double *__restrict__ in,
+                          double *__restrict__ out)
+{
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int m = rows[b];
+        const int cols = cols_in > 0 ? cols_in : m;
+        const double *M = in + 2 * ioff[b];
+        double *Rm = out + ooff[b];
+        const int64_t ld = 2 * (int64_t)m;
+        for (int t = threadIdx.x; t < m * cols; t += blockDim.x) {
+            const int i = t % m, j = t / m;
+            const double re = M[2 * (i + (int64_t)m * j)], im = M[2 * (i + (int64_t)m * j) + 1];
+            Rm[i + ld * j] = re;
+            Rm[(i + m) + ld * j] = im;
+            Rm[i + ld * (j + cols)] = -im;
+            Rm[(i + m) + ld * (j + cols)] = re;
+        }
+    }
+}
 
 superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, const double *U, const double *R,
                                  const double *B, cudaStream_t stream, superdc_hss **out)
@@ -935,6 +972,70 @@ superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, cons
     if (e != cudaSuccess) { superdc_hss_free(h); return e == cudaErrorMemoryAllocation ? SUPERDC_ERR_OOM : SUPERDC_ERR_CUDA; }
     *out = h;
     return SUPERDC_OK;
+}
+
+superdc_status superdc_build_hss_hermitian(const superdc_tree *tree, const double *D, const double *U,
+                                           const double *R, const double *B, cudaStream_t stream,
+                                           superdc_hss **out)
+{
+    if (!tree || !out || !D || !U || !B || !tree->lchild || !tree->rchild || !tree->leaf_size) return SUPERDC_ERR_ARG;
+    const int nn = tree->nnodes, r = tree->rank;
+    if (nn < 1 || (nn % 2) == 0 || r < 1 || 2 * r > 32 || tree->n < 1) return SUPERDC_ERR_ARG;
+    if (nn > 1 && !R) return SUPERDC_ERR_ARG;
+    // leaves in postorder, their sizes doubled; block offsets (complex entries
+    // in, real entries out)
+    std::vector<int64_t> sz2(nn);
+    std::vector<int64_t> dio, doo, uio, uoo, rio, roo;
+    std::vector<int32_t> drow, urow, rrow;
+    int64_t di = 0, dr = 0, ui = 0, ur = 0, n2 = 0;
+    for (int i = 0; i < nn; i++) {
+        const bool leaf = tree->lchild[i] < 0;
+        const int64_t m = leaf ? tree->leaf_size[i] : 0;
+        if (leaf && (m < 1 || 2 * m > 128)) return SUPERDC_ERR_ARG;
+        sz2[i] = 2 * m;
+        if (leaf) {
+            dio.push_back(di); doo.push_back(dr); drow.push_back((int32_t)m);
+            uio.push_back(ui); uoo.push_back(ur); urow.push_back((int32_t)m);
+            di += m * m; dr += 4 * m * m; ui += m * r; ur += 4 * m * r; n2 += 2 * m;
+        }
+        rio.push_back((int64_t)i * r * r); roo.push_back((int64_t)i * 4 * r * r); rrow.push_back(r);
+    }
+    if (n2 != 2 * tree->n) return SUPERDC_ERR_ARG;
+    const int nl = (int)dio.size();
+    // one device slab: the real generators and the block tables
+    const size_t nd = (size_t)dr + ur + 2 * (size_t)nn * 4 * r * r;
+    const size_t ni = dio.size() * 4 + rio.size() * 2, n32 = drow.size() * 2 + rrow.size();
+    char *slab = nullptr;
+    SDC_CHECK(sdc_alloc(&slab, nd * 8 + ni * 8 + n32 * 4, stream));
+    double *RD = (double *)slab, *RU = RD + dr, *RR = RU + ur, *RB = RR + (size_t)nn * 4 * r * r;
+    int64_t *tab = (int64_t *)(RB + (size_t)nn * 4 * r * r);
+    int32_t *rows = (int32_t *)(tab + ni);
+    std::vector<int64_t> htab;
+    for (auto *v : {&dio, &doo, &uio, &uoo, &rio, &roo}) htab.insert(htab.end(), v->begin(), v->end());
+    std::vector<int32_t> hrows;
+    for (auto *v : {&drow, &urow, &rrow}) hrows.insert(hrows.end(), v->begin(), v->end());
+    cudaError_t e = cudaMemcpyAsync(tab, htab.data(), htab.size() * 8, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rows, hrows.data(), hrows.size() * 4, cudaMemcpyHostToDevice, stream);
+    const unsigned g = (unsigned)(sdc_num_sms() * 4);
+    superdc_status st = SUPERDC_OK;
+    if (e == cudaSuccess) {
+        k_realify<<<g, 256, 0, stream>>>(nl, tab, tab + nl, rows, 0, D, RD);           // square leaf blocks
+        k_realify<<<g, 256, 0, stream>>>(nl, tab + 2 * nl, tab + 3 * nl, rows + nl, r, U, RU);
+        if (R) k_realify<<<g, 256, 0, stream>>>(nn, tab + 4 * nl, tab + 4 * nl + nn, rows + 2 * nl, r, R, RR);
+        else e = cudaMemsetAsync(RR, 0, (size_t)nn * 4 * r * r * sizeof(double), stream);
+        k_realify<<<g, 256, 0, stream>>>(nn, tab + 4 * nl, tab + 4 * nl + nn, rows + 2 * nl, r, B, RB);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        superdc_tree t2 = *tree;
+        t2.n = 2 * tree->n;
+        t2.rank = 2 * r;
+        t2.leaf_size = sz2.data();
+        st = superdc_build_hss(&t2, RD, RU, RR, RB, stream, out);   // synchronises the stream
+    }
+    cudaFreeAsync(slab, stream);
+    if (e != cudaSuccess) return SUPERDC_ERR_CUDA;
+    return st;
 }
 
 void superdc_hss_free(superdc_hss *h)
@@ -1227,6 +1328,22 @@ superdc_status superdc_apply_Q(const superdc_eigfact *f, int32_t trans, int64_t 
     cudaError_t e = cudaGetLastError();
     if (s != SUPERDC_OK) return s;
     return e == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+}
+
+superdc_status superdc_apply_function(const superdc_eigfact *f, const double *fvals, int64_t ncols,
+                                      const double *X, int64_t ldx, double *Y, int64_t ldy, cudaStream_t st)
+{
+    if (!f || !fvals || !X || !Y || ncols < 0 || ncols > INT32_MAX) return SUPERDC_ERR_ARG;
+    const int64_t n = f->n;
+    if (ldx < n || ldy < n) return SUPERDC_ERR_ARG;
+    if (ncols == 0) return SUPERDC_OK;
+    double *T = nullptr;
+    SdcScratch sc(st);
+    SDC_CHECK(sc.get(&T, (size_t)n * ncols));
+    superdc_status s = superdc_apply_Q(f, 1, ncols, X, ldx, T, n, st);
+    if (s != SUPERDC_OK) return s;
+    PROF_LAUNCH("scale", st, k_scale_rows<<<(unsigned)(sdc_num_sms() * 8), 256, 0, st>>>(n, (int)ncols, fvals, T, n));
+    return superdc_apply_Q(f, 0, ncols, T, n, Y, ldy, st);
 }
 
 superdc_status superdc_eigfact_set_fmm_min_m(superdc_eigfact *f, int32_t fmm_min_m)

@@ -77,7 +77,10 @@ class HSS:
         r = self.tree.rank
         Rp = np.ascontiguousarray(np.transpose(self.R, (0, 2, 1))).reshape(-1)
         Bp = np.ascontiguousarray(np.transpose(self.B, (0, 2, 1))).reshape(-1)
-        return (np.ascontiguousarray(self.D), np.ascontiguousarray(self.U), Rp, Bp)
+        out = (np.ascontiguousarray(self.D), np.ascontiguousarray(self.U), Rp, Bp)
+        if np.iscomplexobj(self.D):     # (re, im) pairs
+            out = tuple(np.ascontiguousarray(x, np.complex128).view(np.float64) for x in out)
+        return out
 
 
 def perfect_tree(n: int, leaf: int, rank: int) -> Tree:
@@ -197,6 +200,64 @@ def hss_random(n: int, leaf: int, rank: int, seed: int, bscale: float = 1.0,
                 R[c2] = q[rank:]
             B[c1] = rng.standard_normal((rank, rank)) * colscale[None, :] * bscale
     return h
+
+
+def hss_random_hermitian(n: int, leaf: int, rank: int, seed: int) -> HSS:
+    """Random complex Hermitian HSS matrix, the complex analogue of
+    ``hss_random``: leaf D = (G + G^H)/2 and B = G diag(2^-k) with
+    G = N(0,1) + i N(0,1); leaf U and the stacked [R_c1; R_c2] are the
+    Q-factors of complex Gaussian matrices (orthonormal columns).  Arrays are
+    complex128 in the same layout as ``hss_random`` (``packed`` then yields the
+    (re, im) pairs that superdc_build_hss_hermitian reads).  Draw order as
+    ``hss_random``, each complex matrix drawn as its real part then its
+    imaginary part."""
+    tree = perfect_tree(n, leaf, rank)
+    rng = np.random.default_rng(seed)
+    D, U, R, B, d_off, u_off = _alloc(tree)
+    D, U, R, B = (x.astype(np.complex128) for x in (D, U, R, B))
+    h = HSS(tree, D, U, R, B, d_off, u_off)
+    colscale = 2.0 ** (-np.arange(rank, dtype=np.float64))
+
+    def cg(shape):
+        re = rng.standard_normal(shape)
+        return re + 1j * rng.standard_normal(shape)
+
+    for i in range(tree.nnodes):
+        m = int(tree.leaf_size[i])
+        if tree.lchild[i] < 0:
+            G = cg((m, m))
+            h.leaf_D(i)[:, :] = 0.5 * (G + G.conj().T)
+            h.leaf_U(i)[:, :] = _qfactor(cg((m, rank)))
+        else:
+            c1, c2 = int(tree.lchild[i]), int(tree.rchild[i])
+            if i != tree.root:
+                q = _qfactor(cg((2 * rank, rank)))
+                R[c1] = q[:rank]
+                R[c2] = q[rank:]
+            B[c1] = cg((rank, rank)) * colscale[None, :]
+    return h
+
+
+def real_layout(h: HSS, X: np.ndarray) -> np.ndarray:
+    """Complex n x k block -> the 2n x k real block of a Hermitian HSS
+    handle's layout: each leaf's rows as [Re rows; Im rows]."""
+    X = np.asarray(X).reshape(h.tree.n, -1)
+    out = np.empty((2 * h.tree.n, X.shape[1]))
+    for i in h.tree.leaves:
+        o, m = int(h.tree.offset[i]), int(h.tree.leaf_size[i])
+        out[2 * o:2 * o + m] = X[o:o + m].real
+        out[2 * o + m:2 * o + 2 * m] = X[o:o + m].imag
+    return out
+
+
+def complex_layout(h: HSS, Y: np.ndarray) -> np.ndarray:
+    """Inverse of ``real_layout``."""
+    Y = np.asarray(Y).reshape(2 * h.tree.n, -1)
+    out = np.empty((h.tree.n, Y.shape[1]), np.complex128)
+    for i in h.tree.leaves:
+        o, m = int(h.tree.offset[i]), int(h.tree.leaf_size[i])
+        out[o:o + m] = Y[2 * o:2 * o + m] + 1j * Y[2 * o + m:2 * o + 2 * m]
+    return out
 
 
 def hss_tridiag(n: int, leaf: int, diag: float = 3.0, off: float = -1.0) -> HSS:
