@@ -293,9 +293,25 @@ superdc_status superdc_build_hss_hermitian(const superdc_tree *tree, const doubl
  * (Lemma 4.1, eq. (4.34)): dense leaf blocks, the permutations and, for every
  * node and step, the factor vectors of eq. (4.30) plus the deflation
  * rotations.  Device-detected errors are latched in the handle; the call
- * synchronises the stream once at the end and returns them. */
+ * synchronises the stream once at the end and returns them (it is
+ * superdc_eig_plan + superdc_eig_run + that synchronisation). */
 superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaStream_t stream,
                            double *lambda, superdc_eigfact **fact);
+
+/* superdc_eig in two parts, for callers that record the work once into a CUDA
+ * graph and replay it (the level-batched launch sequence as one graph):
+ *   superdc_eig_plan allocates the handle with every buffer the
+ *   factorisation needs and sets the kernels' attributes (synchronous, no
+ *   work enqueued);
+ *   superdc_eig_run enqueues the whole factorisation on the stream: no host
+ *   synchronisation, no host memory read, only device work and the
+ *   stream-ordered (cudaMallocAsync) scratch of its steps, so the call can be
+ *   captured; each replay recomputes the factor in place and writes lambda
+ *   (DEVICE, n).  Device-detected errors are latched in the handle's status
+ *   word (cleared at the start of every run) and read by superdc_sync_status.
+ * The handle's options are those given to the plan. */
+superdc_status superdc_eig_plan(const superdc_hss *h, const superdc_opts *opts, superdc_eigfact **fact);
+superdc_status superdc_eig_run(superdc_eigfact *fact, cudaStream_t stream, double *lambda);
 void superdc_eigfact_free(superdc_eigfact *f);
 
 /* Y = Q X (trans = 0) or Y = Q^T X (trans = 1), Algorithm 4 applied at the

@@ -144,6 +144,15 @@ class HSSMatrix:
         L.check(code, "superdc_eig")
         return lam, fac
 
+    def eig_plan(self, opts=None):
+        """superdc_eig_plan: a factor handle with every buffer allocated; run it
+        with EigFactor.run (which can be captured into a CUDA graph)."""
+        if opts is None:
+            opts = default_opts()
+        f = ctypes.c_void_p()
+        L.check(L.lib().superdc_eig_plan(self._h, ctypes.byref(opts), ctypes.byref(f)), "superdc_eig_plan")
+        return EigFactor(f, self)
+
     def __del__(self):
         try:
             if self._h and self._h.value:
@@ -175,6 +184,17 @@ class EigFactor:
                                        self.n, _stream())
         L.check(code, "superdc_apply_Q")
         return Y.reshape(-1) if vec else Y
+
+    def run(self, lam):
+        """superdc_eig_run on the current stream into lam (float64 CUDA, n):
+        enqueue only, no synchronisation; errors via sync_status()."""
+        assert lam.is_cuda and lam.dtype == torch.float64 and lam.numel() == self.n
+        L.check(L.lib().superdc_eig_run(self._f, _stream(), _ptr(lam)), "superdc_eig_run")
+        return lam
+
+    def sync_status(self):
+        """Raise if the handle's device status word holds an error (synchronises)."""
+        L.check(L.lib().superdc_sync_status(self._f), "superdc_sync_status")
 
     def apply_function(self, fvals, X):
         """f(A) X = Q diag(fvals) Q^T X (superdc_apply_function); fvals: float64

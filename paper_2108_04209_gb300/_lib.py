@@ -72,6 +72,10 @@ def lib():
         L.superdc_hss_free.restype = None
         L.superdc_eig.argtypes = [c_void_p, ctypes.POINTER(Opts), c_void_p, c_void_p, ctypes.POINTER(c_void_p)]
         L.superdc_eig.restype = c_int32
+        L.superdc_eig_plan.argtypes = [c_void_p, ctypes.POINTER(Opts), ctypes.POINTER(c_void_p)]
+        L.superdc_eig_plan.restype = c_int32
+        L.superdc_eig_run.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.superdc_eig_run.restype = c_int32
         L.superdc_eigfact_free.argtypes = [c_void_p]
         L.superdc_eigfact_free.restype = None
         L.superdc_apply_Q.argtypes = [c_void_p, c_int32, c_int64, c_void_p, c_int64, c_void_p, c_int64, c_void_p]

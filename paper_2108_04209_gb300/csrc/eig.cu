@@ -26,6 +26,7 @@
 #include "fmm.cuh"
 #include "prof.cuh"
 
+#include <mutex>
 #include "handles.cuh"
 
 namespace {
@@ -1057,32 +1058,58 @@ void superdc_eigfact_free(superdc_eigfact *f)
     delete f;
 }
 
-superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaStream_t st, double *lambda,
-                           superdc_eigfact **fact)
+// The leaf kernels' dynamic shared-memory limits, raised once per device to
+// what the largest leaf (128 rows) and rank (32) need; a launch uses only what
+// its own leaves need.
+cudaError_t leaf_attrs()
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    const size_t mm = 128, rmax = 32;
+    const struct { const void *fn; size_t bytes; } at[] = {
+        {(const void *)k_leaf_tri, (mm * (mm | 1) + std::max(mm * rmax, mm)) * sizeof(double)},
+        {(const void *)k_leaf_ql, 2 * mm * 32 * sizeof(double)},
+        {(const void *)k_leaf_out, mm * (mm | 1) * sizeof(double)},
+        {(const void *)k_leaf_qlcta, (mm * (mm | 1) + 4 * mm) * sizeof(double)}};
+    for (const auto &a : at) {
+        e = cudaFuncSetAttribute(a.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.bytes);
+        if (e != cudaSuccess) return e;
+    }
+    done[dev] = true;
+    return cudaSuccess;
+}
+
+superdc_status superdc_eig_plan(const superdc_hss *h, const superdc_opts *opts, superdc_eigfact **fact)
 {
     superdc_opts def;
     if (!opts) { superdc_opts_default(&def); opts = &def; }
-    if (!h || !lambda || !fact || !(opts->tau >= 0) || !(opts->stop_c > 0) || opts->max_iter < 1 ||
-        opts->sched < 0 || opts->sched > 2)
+    if (!h || !fact || !(opts->tau >= 0) || !(opts->stop_c > 0) || opts->max_iter < 1 || opts->sched < 0 ||
+        opts->sched > 2)
         return SUPERDC_ERR_ARG;
     const int64_t n = h->n;
     const int r = h->r, lmax = h->lmax, rr = r * r, nn = h->nnodes;
     superdc_eigfact *f = new superdc_eigfact();
     f->h = h; f->n = n; f->r = r; f->lmax = lmax;
+    f->opts = *opts;
     f->fmm_min_m = fmm_resolve(opts->fmm_min_m);
     auto fail = [&](cudaError_t e) {
         superdc_eigfact_free(f);
         return e == cudaErrorMemoryAllocation ? SUPERDC_ERR_OOM : SUPERDC_ERR_CUDA;
     };
 #define EIG_CHECK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return fail(e_); } while (0)
-    // ---- persistent storage of the handle
+    // ---- storage of the structured Q
     std::vector<int64_t> qoff(h->nleaves + 1, 0);
     for (int k = 0; k < h->nleaves; k++) qoff[k + 1] = qoff[k] + h->size[h->leaves[k]] * h->size[h->leaves[k]];
     EIG_CHECK(dalloc(&f->Qleaf, qoff.back(), &f->slabs));
     EIG_CHECK(dalloc(&f->d_qoff, qoff.size(), &f->slabs));
     EIG_CHECK(dalloc(&f->status, 1, &f->slabs));
-    EIG_CHECK(cudaMemsetAsync(f->status, 0, sizeof(int32_t), st));
-    EIG_CHECK(cudaMemcpyAsync(f->d_qoff, qoff.data(), qoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    EIG_CHECK(cudaMemcpy(f->d_qoff, qoff.data(), qoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     f->P.assign(lmax, nullptr);
     f->F.assign(lmax, std::vector<StepF>(r));
     for (int l = 0; l < lmax; l++) {
@@ -1102,25 +1129,20 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
             S.mk = islab + 5 * n; S.ngiv = islab + 5 * n + np; S.fmm = islab + 5 * n + 2 * np;
         }
     }
-    // ---- work buffers (released at the end of the call)
-    double *H, *Bts, *sqb, *lamA, *lamB, *Wp, *WK, *WK2, *zk, *wsum;
-    int32_t *org, *perm;
-    std::vector<char *> tmp;
-    auto talloc = [&](auto **p, size_t cnt) { return dalloc(p, cnt, &tmp); };
-    auto free_tmp = [&]() { for (auto p : tmp) cudaFree(p); tmp.clear(); };
-#undef EIG_CHECK
-#define EIG_CHECK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { free_tmp(); return fail(e_); } } while (0)
+    // ---- work buffers of the run (kept with the handle so that a run
+    // allocates nothing but the stream-ordered scratch of its steps)
+    EigWork &w = f->work;
     Tape &T = f->tape;
     T.on = opts->tape != 0;
+    EIG_CHECK(dalloc(&w.H, (size_t)nn * rr, &f->slabs));
+    EIG_CHECK(dalloc(&w.Bts, (size_t)nn * rr, &f->slabs));
+    EIG_CHECK(dalloc(&w.sqb, nn, &f->slabs));
     if (T.on) {
-        EIG_CHECK(dalloc(&H, (size_t)nn * rr, &f->slabs));
-        EIG_CHECK(dalloc(&Bts, (size_t)nn * rr, &f->slabs));
-        EIG_CHECK(dalloc(&sqb, nn, &f->slabs));
         EIG_CHECK(dalloc(&T.Bt, (size_t)nn * rr, &f->slabs));
         EIG_CHECK(dalloc(&T.beta, nn, &f->slabs));
         EIG_CHECK(dalloc(&T.u1, (size_t)nn * r, &f->slabs));
         EIG_CHECK(dalloc(&T.v1, (size_t)nn * r, &f->slabs));
-        T.H = H; T.Bts = Bts; T.sqb = sqb;
+        T.H = w.H; T.Bts = w.Bts; T.sqb = w.sqb;
         T.lam_prev.assign(lmax, nullptr);
         T.Wprev.assign(lmax, nullptr);
         T.WKb.assign(lmax, std::vector<double *>(r, nullptr));
@@ -1130,78 +1152,95 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
             EIG_CHECK(dalloc(&T.Wprev[l], (size_t)n * r, &f->slabs));
             for (int j = 0; j < r; j++) EIG_CHECK(dalloc(&T.WKb[l][j], (size_t)n * (ctot - j), &f->slabs));
         }
-        EIG_CHECK(cudaMemsetAsync(T.Bt, 0, (size_t)nn * rr * sizeof(double), st));
-        EIG_CHECK(cudaMemsetAsync(T.beta, 0, nn * sizeof(double), st));
-    } else {
-        EIG_CHECK(talloc(&H, (size_t)nn * rr));
-        EIG_CHECK(talloc(&Bts, (size_t)nn * rr));
-        EIG_CHECK(talloc(&sqb, nn));
     }
-    EIG_CHECK(talloc(&lamA, n));
-    EIG_CHECK(talloc(&lamB, n));
-    EIG_CHECK(talloc(&Wp, (size_t)n * r));
-    EIG_CHECK(talloc(&WK, (size_t)n * 2 * r));
-    EIG_CHECK(talloc(&WK2, (size_t)n * 2 * r));
-    EIG_CHECK(talloc(&zk, n));
-    EIG_CHECK(talloc(&wsum, nn));
-    EIG_CHECK(talloc(&org, n));
-    EIG_CHECK(talloc(&perm, n));
-    EIG_CHECK(cudaMemsetAsync(H, 0, (size_t)nn * rr * sizeof(double), st));
+    EIG_CHECK(dalloc(&w.lamA, n, &f->slabs));
+    EIG_CHECK(dalloc(&w.lamB, n, &f->slabs));
+    EIG_CHECK(dalloc(&w.Wp, (size_t)n * r, &f->slabs));
+    EIG_CHECK(dalloc(&w.WK, (size_t)n * 2 * r, &f->slabs));
+    EIG_CHECK(dalloc(&w.WK2, (size_t)n * 2 * r, &f->slabs));
+    EIG_CHECK(dalloc(&w.zk, n, &f->slabs));
+    EIG_CHECK(dalloc(&w.wsum, nn, &f->slabs));
+    EIG_CHECK(dalloc(&w.org, n, &f->slabs));
+    EIG_CHECK(dalloc(&w.perm, n, &f->slabs));
+    EIG_CHECK(dalloc(&w.dq, n, &f->slabs));
+    EIG_CHECK(dalloc(&w.eq, n, &f->slabs));
+    // leaf eigensolver layout and kernel attributes (set here, not in the run)
+    const size_t mm = (size_t)h->mmax;
+    w.leaf_batched = mm >= 96;
+    w.smem1 = (mm * (mm | 1) + std::max(mm * (size_t)r, mm)) * sizeof(double);
+    w.smem2 = 2 * mm * 32 * sizeof(double);
+    w.smem3 = mm * (mm | 1) * sizeof(double);
+    w.smem4 = (mm * (mm | 1) + 4 * mm) * sizeof(double);
+    w.smem5 = (size_t)LEAF_R * (mm | 1) * sizeof(double);
+    w.cap = 3 * (int64_t)mm * mm;
+    w.caps = 16 * (int64_t)mm;
+    if (w.leaf_batched) {
+        EIG_CHECK(dalloc(&w.rot, (size_t)h->nleaves * w.cap, &f->slabs));
+        EIG_CHECK(dalloc(&w.hdr, (size_t)h->nleaves * w.caps, &f->slabs));
+        EIG_CHECK(dalloc(&w.nsw, h->nleaves, &f->slabs));
+    }
+    EIG_CHECK(leaf_attrs());
+    EIG_CHECK(r1_prepare());
+#undef EIG_CHECK
+    *fact = f;
+    return SUPERDC_OK;
+}
+
+superdc_status superdc_eig_run(superdc_eigfact *f, cudaStream_t st, double *lambda)
+{
+    if (!f || !lambda) return SUPERDC_ERR_ARG;
+    const superdc_hss *h = f->h;
+    const superdc_opts *opts = &f->opts;
+    const int64_t n = f->n;
+    const int r = f->r, lmax = f->lmax, rr = r * r, nn = h->nnodes;
+    EigWork &w = f->work;
+    Tape &T = f->tape;
+    double *H = w.H, *Bts = w.Bts, *sqb = w.sqb;
+    double *Wp = w.Wp, *WK = w.WK, *WK2 = w.WK2, *zk = w.zk, *wsum = w.wsum;
+    int32_t *org = w.org, *perm = w.perm;
+#define RUN_CHECK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) \
+        return e_ == cudaErrorMemoryAllocation ? SUPERDC_ERR_OOM : SUPERDC_ERR_CUDA; } while (0)
+    RUN_CHECK(cudaMemsetAsync(f->status, 0, sizeof(int32_t), st));
+    RUN_CHECK(cudaMemsetAsync(H, 0, (size_t)nn * rr * sizeof(double), st));
+    if (T.on) {
+        RUN_CHECK(cudaMemsetAsync(T.Bt, 0, (size_t)nn * rr * sizeof(double), st));
+        RUN_CHECK(cudaMemsetAsync(T.beta, 0, nn * sizeof(double), st));
+    }
     const int nsm = sdc_num_sms();
     // ---- 1. dividing stage, top-down
     for (int l = 0; l < lmax; l++) {
-        std::vector<int> nodes;
-        for (int i : h->lev_nodes[l]) if (h->lch[i] >= 0) nodes.push_back(i);
-        if (nodes.empty()) continue;
-        PROF_LAUNCH("divide", st, k_divide<<<(unsigned)nodes.size(), 128, 8 * rr * sizeof(double), st>>>(
+        int nnodes_l = 0;
+        for (int i : h->lev_nodes[l]) if (h->lch[i] >= 0) nnodes_l++;
+        if (nnodes_l == 0) continue;
+        PROF_LAUNCH("divide", st, k_divide<<<(unsigned)nnodes_l, 128, 8 * rr * sizeof(double), st>>>(
             h->d_lev_nodes[l], nn - 1, r, h->d_lch, h->d_rch, h->R, h->B, H, Bts, sqb, f->status,
             T.on ? T.Bt : nullptr, T.beta, T.u1, T.v1));
     }
-    // ---- 2. leaves
+    // ---- 2. leaves: large leaves (one CTA per SM) batch the QL chases one
+    // lane per leaf; small leaves chase inside each leaf's CTA, several CTAs per SM
     {
-        const size_t mm = (size_t)h->mmax;
-        const size_t smem1 = (mm * (mm | 1) + std::max(mm * (size_t)r, mm)) * sizeof(double);
-        const size_t smem2 = 2 * mm * 32 * sizeof(double);
-        const size_t smem3 = mm * (mm | 1) * sizeof(double);
-        const int64_t cap = 3 * (int64_t)mm * mm, caps = 16 * (int64_t)mm;
-        // large leaves (one CTA per SM): QL chases batched one lane per leaf;
-        // small leaves: the chase inside each leaf's CTA, several CTAs per SM
-        const bool batched = mm >= 96;
-        double *dq, *eq;
-        EIG_CHECK(talloc(&dq, n));
-        EIG_CHECK(talloc(&eq, n));
-        EIG_CHECK(cudaFuncSetAttribute(k_leaf_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
-        PROF_LAUNCH("leaf", st, k_leaf_tri<<<(unsigned)h->nleaves, LEAF_T, smem1, st>>>(
+        const int mm = h->mmax;
+        PROF_LAUNCH("leaf", st, k_leaf_tri<<<(unsigned)h->nleaves, LEAF_T, w.smem1, st>>>(
             r, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H, f->Qleaf,
-            f->d_qoff, dq, eq));
-        if (batched) {
-            double2 *rot;
-            int2 *hdr;
-            int32_t *nsw;
-            EIG_CHECK(talloc(&rot, (size_t)h->nleaves * cap));
-            EIG_CHECK(talloc(&hdr, (size_t)h->nleaves * caps));
-            EIG_CHECK(talloc(&nsw, h->nleaves));
-            EIG_CHECK(cudaFuncSetAttribute(k_leaf_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-            EIG_CHECK(cudaFuncSetAttribute(k_leaf_out, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
-            PROF_LAUNCH("leaf", st, k_leaf_ql<<<(unsigned)((h->nleaves + 31) / 32), 32, smem2, st>>>(
-                h->nleaves, (int)mm, h->d_leaf_off, h->d_leaf_m, dq, eq, rot, hdr, nsw, cap, (int)caps, f->status));
-            const size_t smem5 = (size_t)LEAF_R * (mm | 1) * sizeof(double);
+            f->d_qoff, w.dq, w.eq));
+        if (w.leaf_batched) {
+            PROF_LAUNCH("leaf", st, k_leaf_ql<<<(unsigned)((h->nleaves + 31) / 32), 32, w.smem2, st>>>(
+                h->nleaves, mm, h->d_leaf_off, h->d_leaf_m, w.dq, w.eq, w.rot, w.hdr, w.nsw, w.cap, (int)w.caps,
+                f->status));
             PROF_LAUNCH("leaf", st, k_leaf_rot<<<dim3((unsigned)h->nleaves, (unsigned)((mm + LEAF_R - 1) / LEAF_R)),
-                                                 LEAF_R, smem5, st>>>(h->d_leaf_m, f->Qleaf, f->d_qoff, rot, hdr, nsw,
-                                                                      cap, (int)caps));
-            PROF_LAUNCH("leaf", st, k_leaf_out<<<(unsigned)h->nleaves, LEAF_T, smem3, st>>>(
-                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, dq, lamA, Wp,
+                                                 LEAF_R, w.smem5, st>>>(h->d_leaf_m, f->Qleaf, f->d_qoff, w.rot, w.hdr,
+                                                                        w.nsw, w.cap, (int)w.caps));
+            PROF_LAUNCH("leaf", st, k_leaf_out<<<(unsigned)h->nleaves, LEAF_T, w.smem3, st>>>(
+                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, w.dq, w.lamA, Wp,
                 f->status));
         } else {
-            const size_t smem4 = (mm * (mm | 1) + 4 * mm) * sizeof(double);
-            EIG_CHECK(cudaFuncSetAttribute(k_leaf_qlcta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4));
-            PROF_LAUNCH("leaf", st, k_leaf_qlcta<<<(unsigned)h->nleaves, LEAF_T, smem4, st>>>(
-                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, dq, eq, lamA, Wp,
+            PROF_LAUNCH("leaf", st, k_leaf_qlcta<<<(unsigned)h->nleaves, LEAF_T, w.smem4, st>>>(
+                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, w.dq, w.eq, w.lamA, Wp,
                 f->status));
         }
     }
     // ---- 3. conquering stage, bottom-up over levels
-    double *dcur = lamA, *dnxt = lamB;
+    double *dcur = w.lamA, *dnxt = w.lamB;
     for (int l = lmax - 1; l >= 0; l--) {
         const int nl = (int)h->lev_nodes[l].size();
         const bool root = (l == 0);
@@ -1209,8 +1248,8 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
         int64_t lev_max = 0;
         for (int i : h->lev_nodes[l]) lev_max = std::max<int64_t>(lev_max, h->size[i]);
         if (T.on) {
-            EIG_CHECK(cudaMemcpyAsync(T.lam_prev[l], dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            EIG_CHECK(cudaMemcpyAsync(T.Wprev[l], Wp, (size_t)n * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            RUN_CHECK(cudaMemcpyAsync(T.lam_prev[l], dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            RUN_CHECK(cudaMemcpyAsync(T.Wprev[l], Wp, (size_t)n * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
         }
         PROF_LAUNCH("build", st, k_build<<<(unsigned)(nsm * 4), 256, 0, st>>>(
             n, r, nl, h->d_lev_off[l], h->d_lev_nodes[l], nn - 1, h->d_lch, h->d_rch, h->d_size, h->R, Bts, sqb,
@@ -1219,11 +1258,11 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
         for (int j = 0; j < r; j++) {
             StepF &S = f->F[l][j];
             if (T.on)
-                EIG_CHECK(cudaMemcpyAsync(T.WKb[l][j], WK + (int64_t)j * n, (size_t)n * (ctot - j) * sizeof(double),
+                RUN_CHECK(cudaMemcpyAsync(T.WKb[l][j], WK + (int64_t)j * n, (size_t)n * (ctot - j) * sizeof(double),
                                           cudaMemcpyDeviceToDevice, st));
             // the step's inputs (poles and z column), kept for inspection
-            EIG_CHECK(cudaMemcpyAsync(S.din, dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            EIG_CHECK(cudaMemcpyAsync(S.zin, WK + (int64_t)j * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            RUN_CHECK(cudaMemcpyAsync(S.din, dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            RUN_CHECK(cudaMemcpyAsync(S.zin, WK + (int64_t)j * n, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
             // level-batched (default): every node of the level is one problem of
             // one launch sequence; unbatched baseline: one sequence per node
             const int nseg = opts->batching ? 1 : nl;
@@ -1248,7 +1287,7 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
                 FmmPlan keep;
                 if (opts->batching && c > 0 && c <= 24) { a.keep = &keep; a.keep_width = c; }
                 superdc_status s1 = r1_run(a, st);
-                if (s1 != SUPERDC_OK) { fmm_free(keep, st); free_tmp(); superdc_eigfact_free(f); return s1; }
+                if (s1 != SUPERDC_OK) { fmm_free(keep, st); return s1; }
                 if (c > 0) {
                     FactorView v = view(f, l, j);
                     if (!opts->batching) {
@@ -1258,24 +1297,41 @@ superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaS
                     superdc_status s2 = cauchy_apply_T(v, n, WK + (int64_t)(j + 1) * n, n,
                                                        WK2 + (int64_t)(j + 1) * n, n, c, st,
                                                        a.keep ? &keep : nullptr);
-                    if (s2 != SUPERDC_OK) { fmm_free(keep, st); free_tmp(); superdc_eigfact_free(f); return s2; }
+                    if (s2 != SUPERDC_OK) { fmm_free(keep, st); return s2; }
                 }
                 fmm_free(keep, st);
             }
             if (ctot - (j + 1) > 0) std::swap(WK, WK2);
             std::swap(dcur, dnxt);
         }
-        if (!root) EIG_CHECK(cudaMemcpyAsync(Wp, WK + (int64_t)r * n, (size_t)n * r * sizeof(double),
+        if (!root) RUN_CHECK(cudaMemcpyAsync(Wp, WK + (int64_t)r * n, (size_t)n * r * sizeof(double),
                                              cudaMemcpyDeviceToDevice, st));
     }
-    EIG_CHECK(cudaMemcpyAsync(lambda, dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    EIG_CHECK(cudaGetLastError());
-    int32_t word = 0;
-    EIG_CHECK(cudaMemcpyAsync(&word, f->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    EIG_CHECK(cudaStreamSynchronize(st));
-    free_tmp();
-#undef EIG_CHECK
+    RUN_CHECK(cudaMemcpyAsync(lambda, dcur, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    RUN_CHECK(cudaGetLastError());
+#undef RUN_CHECK
     f->last_stream = st;
+    f->ran = true;
+    return SUPERDC_OK;
+}
+
+superdc_status superdc_eig(const superdc_hss *h, const superdc_opts *opts, cudaStream_t st, double *lambda,
+                           superdc_eigfact **fact)
+{
+    if (!h || !lambda || !fact) return SUPERDC_ERR_ARG;
+    superdc_eigfact *f = nullptr;
+    superdc_status s = superdc_eig_plan(h, opts, &f);
+    if (s != SUPERDC_OK) return s;
+    s = superdc_eig_run(f, st, lambda);
+    if (s != SUPERDC_OK) {
+        cudaStreamSynchronize(st);
+        superdc_eigfact_free(f);
+        return s;
+    }
+    int32_t word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, f->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { superdc_eigfact_free(f); return SUPERDC_ERR_CUDA; }
     *fact = f;
     return status_from_word(word);
 }

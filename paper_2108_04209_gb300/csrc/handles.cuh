@@ -38,6 +38,18 @@ struct Tape {
     double *H = nullptr, *Bt = nullptr, *Bts = nullptr, *beta = nullptr, *sqb = nullptr, *u1 = nullptr, *v1 = nullptr;
 };
 
+// Work buffers of superdc_eig_run, allocated by superdc_eig_plan.
+struct EigWork {
+    double *H = nullptr, *Bts = nullptr, *sqb = nullptr, *lamA = nullptr, *lamB = nullptr, *Wp = nullptr;
+    double *WK = nullptr, *WK2 = nullptr, *zk = nullptr, *wsum = nullptr, *dq = nullptr, *eq = nullptr;
+    int32_t *org = nullptr, *perm = nullptr, *nsw = nullptr;
+    double2 *rot = nullptr;
+    int2 *hdr = nullptr;
+    bool leaf_batched = false;
+    size_t smem1 = 0, smem2 = 0, smem3 = 0, smem4 = 0, smem5 = 0;
+    int64_t cap = 0, caps = 0;
+};
+
 struct superdc_eigfact {
     const superdc_hss *h = nullptr;
     Tape tape;
@@ -51,6 +63,9 @@ struct superdc_eigfact {
     int32_t *status = nullptr;             // device status word
     int fmm_min_m = 0;                     // resolved FMM threshold of the factorisation (0: direct)
     cudaStream_t last_stream = nullptr;
+    superdc_opts opts{};                   // options of the plan
+    EigWork work;                          // buffers of the run
+    bool ran = false;                      // superdc_eig_run has been enqueued at least once
 };
 
 

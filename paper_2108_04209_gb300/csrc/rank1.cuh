@@ -37,3 +37,8 @@ struct R1Args {
 };
 
 superdc_status r1_run(const R1Args &a, cudaStream_t st);
+
+// One-time per-device set-up of the batched step's kernels (attributes);
+// r1_run does it on first use, callers that capture work into a graph call it
+// before the capture.
+cudaError_t r1_prepare();
