@@ -269,9 +269,10 @@ def eig_headline(dev, peak, peak_src, direct=True, reps=3):
     import paper_2108_04209_gb300 as sdc
     from paper_2108_04209_gb300 import _lib as L, inputs
     lib = L.lib()
+    from paper_2108_04209_gb300.autotune import tune_eig
     h = inputs.cfg_large_131072()
     H = sdc.HSSMatrix(h)
-    opts = sdc.default_opts()
+    opts, tune_ms = tune_eig(H, use_cache=False)
     clk = Clocks(dev.index or 0)
     lam, F = H.eig(opts)                       # warm-up
     del F
@@ -303,6 +304,8 @@ def eig_headline(dev, peak, peak_src, direct=True, reps=3):
                     "tau=1e-10; apply: Q^T X, X 131072 x 64 N(0,1) seed 104",
         "eig_s": {"wall_median": wall, "device_median": ev * 1e-3, "reps": reps,
                   "graph_replay_median": graph_s},
+        "schedule": {"autotuned": "sched=%d fmm_min_m=%d" % (opts.sched, opts.fmm_min_m),
+                     "candidates_ms": tune_ms},
         "apply_QT_64": {"wall_median_s": awall, "device_median_s": aev * 1e-3,
                         "hbm_gbs": nbytes / (aev * 1e-3) / 1e9, "algorithmic_bytes": nbytes,
                         "fp64_tflops": aflops / (aev * 1e-3) / 1e12, "fp64_frac": aflops / (aev * 1e-3) / 1e12 / peak,

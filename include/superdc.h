@@ -62,10 +62,20 @@ typedef struct {
                              sweeps, zhat, b and the Cauchy-like applications; smaller ones the
                              direct tiled evaluator.  0 = the library default (the crossover
                              measured on GB300), < 0 = direct evaluator only */
+    int32_t shifted;      /* 1 (default): every secular root is solved and stored relative to its
+                             nearest pole (the local shifting of Section 4.2, eqs. (4.13)-(4.21));
+                             0: ablation, the roots are solved and stored as plain positions, so
+                             every difference d_j - lambda is formed from rounded values (the
+                             unshifted variant Section 5 compares against) */
+    int32_t balanced;     /* 1 (default): the balanced dividing of eqs. (3.11)/(3.12); 0: ablation,
+                             the original dividing of eqs. (2.4)/(2.5) (no scaling by ||B||_2),
+                             whose generator norms can grow exponentially (Proposition 3.1;
+                             not with opts.tape = 1) */
 } superdc_opts;
 
 /* Fills *opts with the defaults: tau = 1e-10, stop_c = 8, max_iter = 50,
- * tile_roots = 0 (automatic), batching = 1, sched = 0, tape = 0, fmm_min_m = 0 (default crossover). */
+ * tile_roots = 0 (automatic), batching = 1, sched = 0, tape = 0, fmm_min_m = 0 (default crossover),
+ * shifted = 1, balanced = 1. */
 superdc_status superdc_opts_default(superdc_opts *opts);
 
 /* Test hook (no counterpart in the paper): from now on every device
@@ -381,6 +391,13 @@ superdc_status superdc_eigfact_stats(const superdc_eigfact *f, int64_t *deflated
  * node's step took the triangular FMM path).  Synchronous. */
 superdc_status superdc_eigfact_get(const superdc_eigfact *f, int32_t level, int32_t step,
                                    const char *field, void *dst);
+/* Generator norms after the dividing stage of the last run on this handle
+ * (HOST outputs, any may be NULL; synchronous): rho_bt = max over non-leaf
+ * nodes p of ||Bt_c1||_2 (the updated B of p's left child, eq. (3.8)),
+ * rho_dt = max over leaves of ||Dhat_k||_2 (the updated leaf blocks, from
+ * their eigenvalues) -- the quantities of Section 5's Table 6. */
+superdc_status superdc_eigfact_norms(const superdc_eigfact *f, double *rho_bt, double *rho_dt);
+
 /* Tree depth lmax (levels of non-leaf nodes are 0 .. lmax-1), rank r, order n. */
 superdc_status superdc_eigfact_shape(const superdc_eigfact *f, int32_t *lmax, int32_t *r, int64_t *n);
 

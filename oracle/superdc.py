@@ -42,7 +42,11 @@ class Divided:
     swapped: dict     # non-leaf node -> True if eq. (3.15) was used
 
 
-def divide(h) -> Divided:
+def divide(h, balanced=True) -> Divided:
+    """Algorithm 1.  balanced=True: eqs. (3.11)/(3.12) (scale beta = ||Bt||_2);
+    balanced=False: the original dividing of eqs. (2.4)/(2.5) (scale 1), kept
+    for the ablation of Section 5's Table 6.  Divided.beta holds ||Bt||_2 in
+    both cases."""
     t = h.tree
     Dh = {i: h.leaf_D(i).copy() for i in t.leaves}
     Bt = {i: h.B[i].copy() for i in range(t.nnodes)}
@@ -66,8 +70,8 @@ def divide(h) -> Divided:
             continue
         c1, c2 = int(t.lchild[i]), int(t.rchild[i])
         B1 = Bt[c1]
-        bn = np.linalg.norm(B1, 2)
-        beta[i] = bn
+        beta[i] = np.linalg.norm(B1, 2)
+        bn = beta[i] if balanced else 1.0
         if B1.shape[1] <= B1.shape[0]:
             swapped[i] = False
             updhss(c1, (B1 @ B1.T) / bn)
@@ -85,7 +89,7 @@ def divide(h) -> Divided:
             Ubig[i] = h.leaf_U(i).copy()
             continue
         c1, c2 = int(t.lchild[i]), int(t.rchild[i])
-        B1, bn = Bt[c1], beta[i]
+        B1, bn = Bt[c1], (beta[i] if balanced else 1.0)
         if not swapped[i]:
             Z[i] = np.vstack([Ubig[c1] @ B1 / np.sqrt(bn), np.sqrt(bn) * Ubig[c2]])
         else:

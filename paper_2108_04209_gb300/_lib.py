@@ -26,7 +26,7 @@ class SuperDCError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("tau", c_double), ("stop_c", c_double), ("max_iter", c_int32),
                 ("tile_roots", c_int32), ("batching", c_int32), ("sched", c_int32), ("tape", c_int32),
-                ("fmm_min_m", c_int32)]
+                ("fmm_min_m", c_int32), ("shifted", c_int32), ("balanced", c_int32)]
 
 
 class Tree(ctypes.Structure):
@@ -92,6 +92,8 @@ def lib():
         L.superdc_eigfact_stats.restype = c_int32
         L.superdc_eigfact_get.argtypes = [c_void_p, c_int32, c_int32, ctypes.c_char_p, c_void_p]
         L.superdc_eigfact_get.restype = c_int32
+        L.superdc_eigfact_norms.argtypes = [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]
+        L.superdc_eigfact_norms.restype = c_int32
         L.superdc_eigfact_shape.argtypes = [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
                                             ctypes.POINTER(c_int64)]
         L.superdc_eigfact_shape.restype = c_int32

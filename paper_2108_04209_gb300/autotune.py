@@ -1,4 +1,5 @@
-"""Autotuner for the schedule of the batched rank-one step.
+"""Autotuners for the schedule of the batched rank-one step and of the whole
+eigendecomposition.
 
 Stage 1, the direct secular kernel: per-warp root pools (sched=1) with
 256..2048 roots per work unit, and the pole-split schedule (sched=2) with
@@ -75,3 +76,46 @@ def tune_secular(offsets, d, z, rho=1.0, tau=1e-12, reps=2, use_cache=True):
     if use_cache:
         _save(tab)
     return default_opts(tau=tau, sched=s, tile_roots=t, fmm_min_m=f), ms
+
+
+EIG_FMM_CANDIDATES = (256, 512, 1024)
+EIG_SCHED_CANDIDATES = (1, 2)
+
+
+def tune_eig(H, tau=1e-10, reps=1, use_cache=True):
+    """Schedule of the whole eigendecomposition of the HSS handle H: stage 1
+    the FMM threshold (256 / 512 / 1024 kept poles) with the automatic secular
+    schedule, stage 2 the winner with the schedule forced to whole problems
+    per CTA (sched=1) or to the pole split (sched=2).  Each candidate is one
+    superdc_eig on H timed with CUDA events after one untimed run.  Returns
+    (opts, table of measured ms); cached per (device, n, rank)."""
+    from . import default_opts
+    key = "%s|eig|n%d|r%d" % (torch.cuda.get_device_name(), H.n, H.rank)
+    tab = _load() if use_cache else {}
+    if use_cache and key in tab and len(tab[key].get("best", [])) == 2:
+        s, f = tab[key]["best"]
+        return default_opts(tau=tau, sched=s, fmm_min_m=f), tab[key]["ms"]
+
+    def measure(o):
+        H.eig(o)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            H.eig(o)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    ms = {}
+    for f in EIG_FMM_CANDIDATES:
+        ms["0/fmm%d" % f] = measure(default_opts(tau=tau, fmm_min_m=f))
+    f = min(EIG_FMM_CANDIDATES, key=lambda c: ms["0/fmm%d" % c])
+    for s in EIG_SCHED_CANDIDATES:
+        ms["%d/fmm%d" % (s, f)] = measure(default_opts(tau=tau, sched=s, fmm_min_m=f))
+    s = min((0,) + EIG_SCHED_CANDIDATES, key=lambda c: ms["%d/fmm%d" % (c, f)])
+    tab[key] = {"best": [s, f], "ms": ms}
+    if use_cache:
+        _save(tab)
+    return default_opts(tau=tau, sched=s, fmm_min_m=f), ms

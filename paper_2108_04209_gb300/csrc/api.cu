@@ -49,6 +49,8 @@ superdc_status superdc_opts_default(superdc_opts *opts)
     opts->sched = 0;
     opts->tape = 0;
     opts->fmm_min_m = 0;
+    opts->shifted = 1;
+    opts->balanced = 1;
     return SUPERDC_OK;
 }
 
@@ -69,7 +71,8 @@ const char *superdc_status_string(superdc_status s)
 static bool opts_ok(const superdc_opts *op)
 {
     return op && op->tau >= 0.0 && op->stop_c > 0.0 && op->max_iter >= 1 && op->max_iter <= 10000 &&
-           op->sched >= 0 && op->sched <= 2;
+           op->sched >= 0 && op->sched <= 2 && (op->shifted == 0 || op->shifted == 1) &&
+           (op->balanced == 0 || op->balanced == 1);
 }
 
 superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, int64_t total,
@@ -103,6 +106,7 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
     a.o.vhat = out->vhat; a.o.bnorm = out->bnorm; a.o.org = out->org; a.o.src = out->src;
     a.o.perm = out->perm; a.o.giv_ab = out->giv_ab; a.o.giv_cs = out->giv_cs; a.o.mk = out->mk;
     a.o.ngiv = out->ngiv; a.o.sweeps = out->sweeps; a.o.status = out->status; a.o.fmm_used = out->fmm;
+    a.o.unshifted = opts->shifted ? 0 : 1;
     SdcScratch sc(stream);
     SDC_CHECK(sc.get(&a.o.dorg, total));
     SDC_CHECK(sc.get(&a.o.wsum, nprob));

@@ -40,7 +40,8 @@ cudaError_t dalloc(T **p, size_t n, std::vector<char *> *own)
 }
 
 // ---------------------------------------------------------------------------
-// Dividing stage, one CTA per non-leaf node of a level (top-down).
+// Dividing stage, one CTA per non-leaf node of a level (top-down); with
+// balanced = 0 the original dividing (beta replaced by 1; ablation).
 // For node i with children c1, c2 and accumulated update H_i (D_i -> D_i - U_i H_i U_i^T):
 //   Bt = B_c1 - R_c1 H_i R_c2^T                    (Lemma 2.1)
 //   beta = ||Bt||_2
@@ -118,7 +119,8 @@ __global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, con
                          const int32_t *__restrict__ rch, const double *__restrict__ R,
                          const double *__restrict__ B, double *__restrict__ H, double *__restrict__ Bts,
                          double *__restrict__ sqb, int32_t *status, double *__restrict__ tBt,
-                         double *__restrict__ tbeta, double *__restrict__ tu1, double *__restrict__ tv1)
+                         double *__restrict__ tbeta, double *__restrict__ tu1, double *__restrict__ tv1,
+                         int balanced, double *__restrict__ bnrm)
 {
     extern __shared__ double sm[];
     const int rr = r * r;
@@ -168,7 +170,10 @@ __global__ void k_divide(const int32_t *__restrict__ nodes, int root, int r, con
         }
     }
     __syncthreads();
-    const double beta = s_beta;
+    // balanced dividing (eqs. (3.11)/(3.12)) scales by beta = ||Bt||_2; the
+    // original one (eqs. (2.4)/(2.5)) by 1: H_c1 += Bt Bt^T, H_c2 += I
+    const double beta = balanced ? s_beta : 1.0;
+    if (bnrm && threadIdx.x == 0) bnrm[i] = s_beta;
     if (tBt) {      // forward tape for the adjoint: Bt, beta, top singular pair u1 = Bt v1 / beta, v1
         for (int e = threadIdx.x; e < rr; e += blockDim.x) tBt[(int64_t)i * rr + e] = Bt[e];
         for (int a = threadIdx.x; a < r; a += blockDim.x) {
@@ -762,6 +767,17 @@ __global__ void k_copy_cols(int64_t n, int ncols, const double *__restrict__ X, 
     }
 }
 
+// *out = max(*out, max_i |v_i|) (non-negative doubles compare as their bit patterns)
+__global__ void k_maxabs(int64_t n, const double *__restrict__ v, double *out)
+{
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(v[i]));
+    for (int sh = 16; sh > 0; sh >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, sh));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax((unsigned long long *)out, (unsigned long long)__double_as_longlong(isnan(m) ? INFINITY : m));
+}
+
 // Y(:, col) = fv .* Y(:, col) (rows scaled by the function values)
 __global__ void k_scale_rows(int64_t n, int ncols, const double *__restrict__ fv, double *__restrict__ Y, int64_t ldy)
 {
@@ -1090,7 +1106,8 @@ superdc_status superdc_eig_plan(const superdc_hss *h, const superdc_opts *opts, 
     superdc_opts def;
     if (!opts) { superdc_opts_default(&def); opts = &def; }
     if (!h || !fact || !(opts->tau >= 0) || !(opts->stop_c > 0) || opts->max_iter < 1 || opts->sched < 0 ||
-        opts->sched > 2)
+        opts->sched > 2 || (opts->shifted != 0 && opts->shifted != 1) || (opts->balanced != 0 && opts->balanced != 1) ||
+        (opts->tape && !opts->balanced))
         return SUPERDC_ERR_ARG;
     const int64_t n = h->n;
     const int r = h->r, lmax = h->lmax, rr = r * r, nn = h->nnodes;
@@ -1163,6 +1180,9 @@ superdc_status superdc_eig_plan(const superdc_hss *h, const superdc_opts *opts, 
     EIG_CHECK(dalloc(&w.org, n, &f->slabs));
     EIG_CHECK(dalloc(&w.perm, n, &f->slabs));
     EIG_CHECK(dalloc(&w.dq, n, &f->slabs));
+    EIG_CHECK(dalloc(&w.bnrm, nn, &f->slabs));
+    EIG_CHECK(dalloc(&w.rho_d, 1, &f->slabs));
+    EIG_CHECK(cudaMemset(w.bnrm, 0, nn * sizeof(double)));
     EIG_CHECK(dalloc(&w.eq, n, &f->slabs));
     // leaf eigensolver layout and kernel attributes (set here, not in the run)
     const size_t mm = (size_t)h->mmax;
@@ -1214,7 +1234,7 @@ superdc_status superdc_eig_run(superdc_eigfact *f, cudaStream_t st, double *lamb
         if (nnodes_l == 0) continue;
         PROF_LAUNCH("divide", st, k_divide<<<(unsigned)nnodes_l, 128, 8 * rr * sizeof(double), st>>>(
             h->d_lev_nodes[l], nn - 1, r, h->d_lch, h->d_rch, h->R, h->B, H, Bts, sqb, f->status,
-            T.on ? T.Bt : nullptr, T.beta, T.u1, T.v1));
+            T.on ? T.Bt : nullptr, T.beta, T.u1, T.v1, opts->balanced, w.bnrm));
     }
     // ---- 2. leaves: large leaves (one CTA per SM) batch the QL chases one
     // lane per leaf; small leaves chase inside each leaf's CTA, several CTAs per SM
@@ -1239,6 +1259,9 @@ superdc_status superdc_eig_run(superdc_eigfact *f, cudaStream_t st, double *lamb
                 f->status));
         }
     }
+    // largest |eigenvalue| of the updated leaf blocks, ||Dhat_k||_2 (Table 6's rho)
+    RUN_CHECK(cudaMemsetAsync(w.rho_d, 0, sizeof(double), st));
+    k_maxabs<<<(unsigned)nsm, 256, 0, st>>>(n, w.lamA, w.rho_d);
     // ---- 3. conquering stage, bottom-up over levels
     double *dcur = w.lamA, *dnxt = w.lamB;
     for (int l = lmax - 1; l >= 0; l--) {
@@ -1281,6 +1304,7 @@ superdc_status superdc_eig_run(superdc_eigfact *f, cudaStream_t st, double *lamb
                 a.o.giv_cs = S.giv_cs; a.o.mk = S.mk + q; a.o.ngiv = S.ngiv + q; a.o.sweeps = S.sweeps;
                 a.o.status = f->status; a.o.dorg = S.dorg; a.o.pinv = S.pinv; a.o.wsum = wsum + q;
                 a.o.fmm_used = S.fmm + q;
+                a.o.unshifted = opts->shifted ? 0 : 1;
                 const int c = ctot - (j + 1);
                 // the step's FMM plan (tree, near lists, M2L kernel matrices)
                 // also serves the Cauchy-like update of the remaining columns
@@ -1464,6 +1488,22 @@ superdc_status superdc_eigfact_get(const superdc_eigfact *f, int32_t level, int3
     else if (fld == "fmm") { src = S.fmm; bytes = np * 4; }
     else return SUPERDC_ERR_ARG;
     return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+}
+
+superdc_status superdc_eigfact_norms(const superdc_eigfact *f, double *rho_bt, double *rho_dt)
+{
+    if (!f || !f->ran) return f ? SUPERDC_ERR_STATE : SUPERDC_ERR_ARG;
+    const int nn = f->h->nnodes;
+    std::vector<double> b(nn);
+    double d = 0.0;
+    if (cudaMemcpy(b.data(), f->work.bnrm, nn * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&d, f->work.rho_d, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SUPERDC_ERR_CUDA;
+    double mb = 0.0;
+    for (int i = 0; i < nn; i++) mb = std::isnan(b[i]) ? INFINITY : std::max(mb, b[i]);
+    if (rho_bt) *rho_bt = mb;
+    if (rho_dt) *rho_dt = d;
+    return SUPERDC_OK;
 }
 
 superdc_status superdc_eigfact_shape(const superdc_eigfact *f, int32_t *lmax, int32_t *r, int64_t *n)

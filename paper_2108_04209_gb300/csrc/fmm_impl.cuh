@@ -902,7 +902,7 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
         int next = k0 + 32;
         Root R;
         R.dK = 0.0; R.y = 1.0; R.phase = 1;
-        if (act) R.init(dk, zk, k, m, W);
+        if (act) R.init(dk, zk, k, m, W, o.unshifted != 0);
         while (__any_sync(FULL, act)) {
             const int kwlo = __reduce_min_sync(FULL, act ? k : 0x7fffffff);
             const int kwhi = __reduce_max_sync(FULL, act ? k : -1);
@@ -948,7 +948,7 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
             if (fin) {
                 k = next + __popc(mask & ((1u << lane) - 1u));
                 act = k < kend;
-                if (act) R.init(dk, zk, k, m, W);
+                if (act) R.init(dk, zk, k, m, W, o.unshifted != 0);
             }
             next += __popc(mask);
             // no root left to refill and fewer than TAIL_X lanes busy: the
@@ -1009,7 +1009,7 @@ k_secular_tail(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
                 const int64_t p = tr.p;
                 b0 = off[p];
                 m = o.mk[p];
-                R.init(o.dk + b0, o.zk + b0, tr.k, m, o.wsum[p]);
+                R.init(o.dk + b0, o.zk + b0, tr.k, m, o.wsum[p], o.unshifted != 0);
                 R.K = tr.K; R.phase = tr.phase; R.nsw = tr.nsw;
                 R.dK = tr.dK; R.y = tr.y; R.lo = tr.lo; R.hi = tr.hi;
                 const int Tb = tr.k / B;
@@ -1129,7 +1129,7 @@ k_secular_fmm_split(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double 
             bool act = k < kendb;
             Root R;
             R.dK = 0.0; R.y = 1.0; R.phase = 1;
-            if (act) R.init(dk, zk, k, m, W);
+            if (act) R.init(dk, zk, k, m, W, o.unshifted != 0);
             while (__syncthreads_or(act)) {
                 const int kwlo = __reduce_min_sync(FULL, act ? k : 0x7fffffff);
                 const int kwhi = __reduce_max_sync(FULL, act ? k : -1);
@@ -1225,7 +1225,7 @@ k_secular_last(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
         Root R;
         __syncthreads();
         if (tid == 0) {
-            R.init(dk, zk, m - 1, m, o.wsum[p]);
+            R.init(dk, zk, m - 1, m, o.wsum[p], o.unshifted != 0);
             s_dK = R.dK; s_y = R.y; s_done = 0; s_p0 = 1;
             // every pole lies to the left of the root's bracket [d_{m-1}, d_{m-1} + W]:
             // a box at least its own width away from the bracket is summed

@@ -42,6 +42,8 @@ struct Tape {
 struct EigWork {
     double *H = nullptr, *Bts = nullptr, *sqb = nullptr, *lamA = nullptr, *lamB = nullptr, *Wp = nullptr;
     double *WK = nullptr, *WK2 = nullptr, *zk = nullptr, *wsum = nullptr, *dq = nullptr, *eq = nullptr;
+    double *bnrm = nullptr;                // per node: ||Bt||_2 of its left child (dividing stage)
+    double *rho_d = nullptr;               // max over leaves of ||Dhat_k||_2
     int32_t *org = nullptr, *perm = nullptr, *nsw = nullptr;
     double2 *rot = nullptr;
     int2 *hdr = nullptr;

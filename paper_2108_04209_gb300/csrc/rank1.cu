@@ -524,7 +524,7 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
         int next = wbeg + 32;
         Root R;
         R.dK = 0.0; R.y = 1.0; R.phase = 1;     // defined values for lanes that stay idle
-        if (act) R.init(dk, zk, k, m, W);
+        if (act) R.init(dk, zk, k, m, W, o.unshifted != 0);
         const bool single = (m <= SEC_CHUNK);
         if (single) {
             for (int j = threadIdx.x; j < m; j += NW * 32) {
@@ -615,7 +615,7 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
             if (fin) {
                 k = next + __popc(mask & ((1u << lane) - 1u));
                 act = k < wend;
-                if (act) R.init(dk, zk, k, m, W);
+                if (act) R.init(dk, zk, k, m, W, o.unshifted != 0);
             }
             next += __popc(mask);
         }
@@ -932,7 +932,7 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     if (!opts) { superdc_opts_default(&def); opts = &def; }
     if (nprob < 0 || total < 0 || !(rho > 0.0) || !out) return SUPERDC_ERR_ARG;
     if (!(opts->tau >= 0.0) || !(opts->stop_c > 0.0) || opts->max_iter < 1 || opts->max_iter > 10000 ||
-        opts->sched < 0 || opts->sched > 2)
+        opts->sched < 0 || opts->sched > 2 || (opts->shifted != 0 && opts->shifted != 1))
         return SUPERDC_ERR_ARG;
     if (nprob > NA_P || total > NA_T) return SUPERDC_ERR_ARG;   // beyond the static scratch
     if (nprob == 0) return SUPERDC_OK;
@@ -950,6 +950,7 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     a.o.vhat = out->vhat; a.o.bnorm = out->bnorm; a.o.org = out->org; a.o.src = out->src;
     a.o.perm = out->perm; a.o.giv_ab = out->giv_ab; a.o.giv_cs = out->giv_cs; a.o.mk = out->mk;
     a.o.ngiv = out->ngiv; a.o.sweeps = out->sweeps; a.o.status = out->status;
+    a.o.unshifted = opts->shifted ? 0 : 1;
     a.o.dorg = (double *)(base + NA_DORG);
     a.o.wsum = (double *)(base + NA_WSUM);
     a.o.pinv = (int32_t *)(base + NA_PINV);

@@ -14,6 +14,7 @@ struct R1Out {
     double *wsum;   // sum of kept z^2 per problem (scratch), nprob entries
     double *lamk;   // d_K + eta of every kept root, slot order (scratch), total entries
     int32_t *fmm_used = nullptr;   // per problem: 1 if it took the FMM path (may be NULL)
+    int32_t unshifted = 0;         // ablation: roots as plain positions (origin 0, no local shifting)
 };
 
 struct FmmPlan;

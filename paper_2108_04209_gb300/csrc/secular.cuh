@@ -144,13 +144,17 @@ __device__ __forceinline__ void sweep(const double *__restrict__ sd, const doubl
 
 struct Root {
     int k, m, K, phase, nsw;
-    bool last;
+    bool last, plain;
     double dK, y, lo, hi;
     double d0, d1, w0, w1, W;   // d_k, d_{k+1}, w_k, w_{k+1}, sum w
 
-    __device__ void init(const double *__restrict__ dk, const double *__restrict__ zk, int k_, int m_, double W_)
+    // plain (ablation of the local shifting): the origin is 0 instead of a
+    // pole, so y is the root's position itself and every difference
+    // (d_j - dK) - y is d_j - lambda formed from rounded values
+    __device__ void init(const double *__restrict__ dk, const double *__restrict__ zk, int k_, int m_, double W_,
+                         bool plain_ = false)
     {
-        k = k_; m = m_; W = W_;
+        k = k_; m = m_; W = W_; plain = plain_;
         last = (k == m - 1);
         d0 = dk[k];
         double z0 = zk[k];
@@ -158,8 +162,9 @@ struct Root {
         if (!last) { d1 = dk[k + 1]; double z1 = zk[k + 1]; w1 = z1 * z1; }
         else       { d1 = d0; w1 = 0.0; }
         phase = 0; nsw = 0;
-        K = k; dK = d0;
+        K = k; dK = plain ? 0.0 : d0;
         y = last ? 0.5 * W : 0.5 * (d1 - d0);     // midpoint sweep
+        if (plain) y += d0;
         lo = hi = 0.0;
     }
 
@@ -177,14 +182,16 @@ struct Root {
                 double rest = f + w0 / h - w1 / (D - h);
                 if (f >= 0.0) { K = k;     lo = 0.0; hi = h;   dK = d0; }
                 else          { K = k + 1; lo = -h;  hi = 0.0; dK = d1; }
-                double a = d0 - dK, b = d1 - dK;
-                y = quad_in(rest, -(rest * (a + b) + w0 + w1), w0 * b + w1 * a, lo, hi);
+                if (plain) { lo += dK; hi += dK; dK = 0.0; }
+                double a = d0 - dK, b = d1 - dK;     // one of them is 0 unless plain
+                y = quad_in(rest, -(rest * (a + b) + w0 + w1), w0 * b + w1 * a + rest * a * b, lo, hi);
             } else {
                 double ym = 0.5 * W;
                 if (f >= 0.0) { lo = 0.0; hi = ym; } else { lo = ym; hi = W; }
                 double rest = f + w0 / ym;
                 y = (rest > 0.0) ? w0 / rest : 0.5 * (lo + hi);
                 if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+                if (plain) { y += d0; lo += d0; hi += d0; }
             }
             phase = 1;
             return false;
