@@ -272,6 +272,11 @@ superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, cons
                                  superdc_hss **out);
 void superdc_hss_free(superdc_hss *h);
 
+/* Copy one generator array of a handle to HOST memory `dst` (inspection;
+ * synchronous): "D", "U" (leaf blocks, the packing of superdc_build_hss),
+ * "R", "B" (nnodes blocks of r x r). */
+superdc_status superdc_hss_get(const superdc_hss *h, const char *field, void *dst);
+
 /* Complex Hermitian HSS matrix (the extension the paper notes in Section 1:
  * its real symmetric treatment carries over to the Hermitian case).  Same
  * tree and packing as superdc_build_hss, but every generator entry is
@@ -291,6 +296,40 @@ void superdc_hss_free(superdc_hss *h);
 superdc_status superdc_build_hss_hermitian(const superdc_tree *tree, const double *D, const double *U,
                                            const double *R, const double *B, cudaStream_t stream,
                                            superdc_hss **out);
+
+/* HSS approximation of a symmetric matrix given by its entries, by
+ * compression of the off-diagonal block rows (Section 5, Example 4: the HSS
+ * form of a kernel matrix built by off-diagonal compression; the paper uses
+ * an existing routine of that kind, this one is randomized range finding on
+ * one sample of the whole matrix, with nested bases):
+ *   entries: kind 0 = dense matrix A (DEVICE, n x n column-major, ld lda >= n,
+ *            symmetric, both triangles read), kind 1 = sqrt(|x_i - x_j|),
+ *            kind 2 = exp(-|x_i - x_j| / param), at points x (DEVICE, n);
+ *   tree: perfect, leaves of `leaf` rows (n = leaf * 2^L, L >= 1, leaf <= 128),
+ *   one rank `rank` at every node (rank <= leaf, rank <= 32);
+ *   Omega: DEVICE n x nsamp column-major N(0,1) sample drawn by the caller
+ *   (rank <= nsamp <= 64; nsamp = rank + 10 is the usual oversampling).
+ * For a leaf i, U_i spans the leading rank left singular vectors of the
+ * sampled block row Y(I_i) - A(I_i, I_i) Omega(I_i); up the tree the children's
+ * projected samples, corrected for the sibling block, give [R_c1; R_c2]; every
+ * B_c1 = U_c1^T A(I_c1, I_c2) U_c2 is an exact block product; D_i = A(I_i, I_i).
+ * *err_est (HOST, may be NULL) receives the largest ratio sigma_{rank+1} /
+ * sigma_1 over the nodes' samples, the relative size of what was dropped
+ * (taken from the samples' Gram matrices, so ratios below about
+ * sqrt(eps) = 1.5e-8 read as that floor).
+ * The result is a handle as from superdc_build_hss; synchronous; work buffers
+ * from the stream-ordered allocator. */
+typedef struct {
+    int32_t kind;
+    const double *A;
+    int64_t lda;
+    const double *x;
+    double param;
+} superdc_matrix_entries;
+
+superdc_status superdc_build_hss_compress(int64_t n, int32_t leaf, int32_t rank,
+                                          const superdc_matrix_entries *entries, const double *Omega,
+                                          int32_t nsamp, cudaStream_t stream, superdc_hss **out, double *err_est);
 
 /* Eigendecomposition A = Q diag(lambda) Q^T (Algorithms 1-3):
  *   dividing stage (Algorithm 1, balanced eqs. (3.11)/(3.12), generator

@@ -52,6 +52,13 @@ def dense_from_hss_hermitian(h) -> np.ndarray:
     return A
 
 
+def kernel_matrix(x, kind="sqrt_dist", param=1.0):
+    """Dense kernel matrix at points x: sqrt|x_i - x_j| (Section 5, Example 4)
+    or exp(-|x_i - x_j| / param)."""
+    d = np.abs(np.asarray(x)[:, None] - np.asarray(x)[None, :])
+    return np.sqrt(d) if kind == "sqrt_dist" else np.exp(-d / param)
+
+
 def gamma(A, lam, Q):
     """max_k ||A q_k - lam_k q_k|| / (n ||A||_2)"""
     n = A.shape[0]

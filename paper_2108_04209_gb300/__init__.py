@@ -144,6 +144,55 @@ class HSSMatrix:
         L.check(code, "superdc_eig")
         return lam, fac
 
+    @classmethod
+    def from_entries(cls, n, leaf, rank, kind="sqrt_dist", A=None, x=None, param=0.0, nsamp=None, seed=0):
+        """HSS approximation by off-diagonal compression (superdc_build_hss_compress)
+        of the symmetric matrix with entries sqrt|x_i - x_j| ("sqrt_dist"),
+        exp(-|x_i - x_j| / param) ("exp_dist") at the points x (float64 CUDA
+        tensor), or the dense matrix A ("dense", float64 CUDA n x n).  The
+        Gaussian sample (n x nsamp, nsamp = rank + 10 by default) is drawn by
+        inputs.gaussian_block(seed).  The estimate sigma_{r+1}/sigma_1 of the
+        dropped part is in .err_est."""
+        import numpy as np
+        from . import inputs
+        kinds = {"dense": 0, "sqrt_dist": 1, "exp_dist": 2}
+        s = int(nsamp or min(64, rank + 10))
+        Om = torch.from_numpy(inputs.normal_block(n, s, seed=seed)).cuda()
+        ent = L.MatrixEntries(kinds[kind], _ptr(A).value if A is not None else None,
+                              int(A.stride(1)) if A is not None else 0,
+                              _ptr(x).value if x is not None else None, float(param))
+        hp = ctypes.c_void_p()
+        est = ctypes.c_double()
+        code = L.lib().superdc_build_hss_compress(int(n), int(leaf), int(rank), ctypes.byref(ent), _ptr(Om), s,
+                                                  _stream(), ctypes.byref(hp), ctypes.byref(est))
+        L.check(code, "superdc_build_hss_compress")
+        self = cls.__new__(cls)
+        t = inputs.perfect_tree(int(n), int(leaf), int(rank))
+        self.hermitian = False
+        self.n, self.rank, self.tree = int(n), int(rank), t
+        self._lch = np.ascontiguousarray(t.lchild, np.int32)
+        self._rch = np.ascontiguousarray(t.rchild, np.int32)
+        self._sz = np.ascontiguousarray(t.leaf_size, np.int64)
+        self.sizes = (int(n) * int(leaf), int(n) * int(rank), t.nnodes * rank * rank, t.nnodes * rank * rank)
+        self._h = hp
+        self.err_est = est.value
+        return self
+
+    def generators(self):
+        """The handle's generators as an inputs.HSS (host arrays; superdc_hss_get)."""
+        import numpy as np
+        from . import inputs
+        t = self.tree
+        D, U, R, B, d_off, u_off = inputs._alloc(t)
+        r = t.rank
+        for name, arr in (("D", D), ("U", U)):
+            L.check(L.lib().superdc_hss_get(self._h, name.encode(), arr.ctypes.data), "superdc_hss_get")
+        for name, arr in (("R", R), ("B", B)):
+            flat = np.empty(t.nnodes * r * r)
+            L.check(L.lib().superdc_hss_get(self._h, name.encode(), flat.ctypes.data), "superdc_hss_get")
+            arr[:] = np.transpose(flat.reshape(t.nnodes, r, r), (0, 2, 1))
+        return inputs.HSS(t, D, U, R, B, d_off, u_off)
+
     def eig_plan(self, opts=None):
         """superdc_eig_plan: a factor handle with every buffer allocated; run it
         with EigFactor.run (which can be captured into a CUDA graph)."""

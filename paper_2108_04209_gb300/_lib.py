@@ -34,6 +34,10 @@ class Tree(ctypes.Structure):
                 ("leaf_size", c_void_p), ("rank", c_int32)]
 
 
+class MatrixEntries(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("A", c_void_p), ("lda", c_int64), ("x", c_void_p), ("param", c_double)]
+
+
 class Rank1Out(ctypes.Structure):
     _fields_ = [(n, c_void_p) for n in ("lam", "dk", "zk", "eta", "vhat", "bnorm", "org", "src", "perm",
                                          "giv_ab", "giv_cs", "mk", "ngiv", "sweeps", "status", "fmm")]
@@ -68,6 +72,12 @@ def lib():
         L.superdc_build_hss_hermitian.argtypes = [ctypes.POINTER(Tree), c_void_p, c_void_p, c_void_p, c_void_p,
                                                   c_void_p, ctypes.POINTER(c_void_p)]
         L.superdc_build_hss_hermitian.restype = c_int32
+        L.superdc_hss_get.argtypes = [c_void_p, ctypes.c_char_p, c_void_p]
+        L.superdc_hss_get.restype = c_int32
+        L.superdc_build_hss_compress.argtypes = [c_int64, c_int32, c_int32, ctypes.POINTER(MatrixEntries), c_void_p,
+                                                 c_int32, c_void_p, ctypes.POINTER(c_void_p),
+                                                 ctypes.POINTER(c_double)]
+        L.superdc_build_hss_compress.restype = c_int32
         L.superdc_hss_free.argtypes = [c_void_p]
         L.superdc_hss_free.restype = None
         L.superdc_eig.argtypes = [c_void_p, ctypes.POINTER(Opts), c_void_p, c_void_p, ctypes.POINTER(c_void_p)]

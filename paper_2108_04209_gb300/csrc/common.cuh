@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <vector>
 #include "superdc.h"
 
 #define SDC_EPS 2.220446049250313080847263336181640625e-16   // 2^-52
@@ -60,18 +61,16 @@ static inline cudaError_t sdc_malloc(T **p, size_t bytes)
 // on the error paths as on the normal one.
 struct SdcScratch {
     cudaStream_t st;
-    void *p[16];
-    int n = 0;
+    std::vector<void *> p;
     explicit SdcScratch(cudaStream_t s) : st(s) {}
     template <typename T>
     cudaError_t get(T **ptr, size_t count)
     {
-        if (n >= 16) return cudaErrorInvalidValue;
         cudaError_t e = sdc_alloc(ptr, count, st);
-        if (e == cudaSuccess) p[n++] = (void *)*ptr;
+        if (e == cudaSuccess) p.push_back((void *)*ptr);
         return e;
     }
-    ~SdcScratch() { for (int i = 0; i < n; i++) cudaFreeAsync(p[i], st); }
+    ~SdcScratch() { for (void *q : p) cudaFreeAsync(q, st); }
     SdcScratch(const SdcScratch &) = delete;
     SdcScratch &operator=(const SdcScratch &) = delete;
 };

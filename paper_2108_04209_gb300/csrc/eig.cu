@@ -1055,6 +1055,23 @@ superdc_status superdc_build_hss_hermitian(const superdc_tree *tree, const doubl
     return st;
 }
 
+superdc_status superdc_hss_get(const superdc_hss *h, const char *field, void *dst)
+{
+    if (!h || !field || !dst) return SUPERDC_ERR_ARG;
+    size_t dsz = 0, usz = 0;
+    for (int k : h->leaves) { dsz += (size_t)h->size[k] * h->size[k]; usz += (size_t)h->size[k] * h->r; }
+    const size_t rr = (size_t)h->nnodes * h->r * h->r;
+    const std::string f(field);
+    const void *src = nullptr;
+    size_t bytes = 0;
+    if (f == "D") { src = h->D; bytes = dsz * 8; }
+    else if (f == "U") { src = h->U; bytes = usz * 8; }
+    else if (f == "R") { src = h->R; bytes = rr * 8; }
+    else if (f == "B") { src = h->B; bytes = rr * 8; }
+    else return SUPERDC_ERR_ARG;
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+}
+
 void superdc_hss_free(superdc_hss *h)
 {
     if (!h) return;

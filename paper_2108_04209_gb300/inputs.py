@@ -238,6 +238,13 @@ def hss_random_hermitian(n: int, leaf: int, rank: int, seed: int) -> HSS:
     return h
 
 
+def chebyshev_points(n: int) -> np.ndarray:
+    """cos((2i - 1) pi / (2n)), i = 1..n: the points of the paper's Example 4
+    (decreasing, so index order is position order)."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return np.cos((2.0 * i - 1.0) * np.pi / (2.0 * n))
+
+
 def real_layout(h: HSS, X: np.ndarray) -> np.ndarray:
     """Complex n x k block -> the 2n x k real block of a Hermitian HSS
     handle's layout: each leaf's rows as [Re rows; Im rows]."""

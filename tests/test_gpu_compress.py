@@ -1,0 +1,88 @@
+"""HSS construction by off-diagonal compression (superdc_build_hss_compress),
+the input side of the paper's Example 4 (Section 5: sqrt|s - t| at Chebyshev
+points, compressed to a moderate tolerance), checked against the dense
+matrices on the CPU: the reconstruction error of the HSS form, the
+eigenvalues of the compressed matrix (exactly, per entry, against the dense
+HSS matrix; within Weyl's bound against the original matrix), and Table 5's
+statistic with and without local shifting."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2108_04209_gb300 as sdc  # noqa: E402
+from paper_2108_04209_gb300 import inputs  # noqa: E402
+from oracle import dense  # noqa: E402
+from tests import parity as P  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda")
+
+
+def _ex4(n, leaf, rank, seed=0):
+    x = inputs.chebyshev_points(n)
+    H = sdc.HSSMatrix.from_entries(n, leaf, rank, "sqrt_dist", x=torch.from_numpy(x).to(DEV), seed=seed)
+    return x, H
+
+
+@pytest.mark.parametrize("n,leaf,rank", [(1024, 64, 10), (2048, 64, 16)])
+def test_compress_kernel_matrix_example4(n, leaf, rank):
+    x, H = _ex4(n, leaf, rank)
+    A = dense.kernel_matrix(x)
+    hg = H.generators()
+    Ah = dense.dense_from_hss(hg)
+    an = np.linalg.norm(A, 2)
+    rec = np.linalg.norm(A - Ah, 2) / an
+    lmax = int(np.log2(n // leaf))
+    print("n=%d rank %d: err_est %.2e, ||A - A_hss|| / ||A|| = %.2e" % (n, rank, H.err_est, rec))
+    assert rec <= 20.0 * lmax * H.err_est + 1e-13
+    tau = 1e-10
+    lam, F = H.eig(sdc.default_opts(tau=tau))
+    lam = lam.cpu().numpy()
+    lh = np.linalg.eigvalsh(Ah)
+    # the kernel's spectrum crowds near 0, where the deflation of Remark 4.1
+    # drops couplings below tau: the eigenvalues of the HSS matrix are met to
+    # within tau per rank-one step on an eigenvalue's path (levels x rank)
+    err = np.abs(lam - lh).max()
+    delta = np.linalg.norm(lam - lh) / (n * np.linalg.norm(lh))     # the paper's delta
+    print("eigenvalues vs the dense HSS matrix: max %.2e, delta %.2e" % (err, delta))
+    assert err <= F.lmax * F.rank * tau + 8 * F.lmax * F.rank * P.EPS * an
+    # Weyl: the eigenvalues of the compressed matrix are within ||A - A_hss|| of A's
+    assert np.abs(lam - np.linalg.eigvalsh(A)).max() <= rec * an * (1 + 1e-6) + F.lmax * F.rank * tau
+
+
+def test_compress_dense_input_of_exact_rank():
+    """A dense matrix that is exactly a rank-4 HSS matrix is recovered to
+    rounding (every dropped singular value is zero; the estimate, from the
+    eigenvalues of the samples' Gram matrices, cannot resolve ratios below
+    about sqrt(eps) = 1.5e-8)."""
+    h = inputs.hss_random(1024, 64, 4, seed=12)
+    A = dense.dense_from_hss(h)
+    Ad = torch.from_numpy(np.asfortranarray(A)).to(DEV)
+    Ad = Ad.t().contiguous().t()
+    H = sdc.HSSMatrix.from_entries(1024, 64, 4, "dense", A=Ad, seed=3)
+    Ah = dense.dense_from_hss(H.generators())
+    rec = np.linalg.norm(A - Ah, 2) / np.linalg.norm(A, 2)
+    print("exact rank 4: err_est %.2e, reconstruction %.2e" % (H.err_est, rec))
+    assert H.err_est <= 1e-7 and rec <= 1e-12
+
+
+def test_table5_statistic_example4():
+    """Section 5, Table 5: the largest fraction over the root node's r secular
+    equations of roots that need more than 5 iterations, with and without local
+    shifting, on Example 4 at n = 4096 (leaf 64)."""
+    x, H = _ex4(4096, 64, 16)
+    mu = {}
+    for sh in (1, 0):
+        F = H.eig_plan(sdc.default_opts(tau=1e-6, shifted=sh))
+        lam = torch.empty(H.n, dtype=torch.float64, device=DEV)
+        F.run(lam)
+        torch.cuda.synchronize()
+        fr = []
+        for j in range(F.rank):
+            mk = int(F.get(0, j, "mk")[0])
+            sw = F.get(0, j, "sweeps")[:mk]
+            fr.append(float(np.mean(sw - 1 > 5)))
+        mu[sh] = max(fr)
+    print("Example 4, n=4096: mu with local shifting %.4f, without %.4f (err_est %.2e)" % (mu[1], mu[0], H.err_est))
+    assert mu[1] < mu[0]
