@@ -241,7 +241,8 @@ superdc_status superdc_secular_batched_noalloc(int64_t nprob, const int64_t *off
  * Tree (HOST arrays): a postordered full binary tree with nnodes nodes, the
  * root is node nnodes-1; lchild/rchild are -1 at leaves; every leaf lies at
  * the same depth (perfect tree); leaf_size[i] = rows of leaf i (ignored for
- * non-leaves), 1 <= leaf_size <= 128; rank = r, the common HSS rank
+ * non-leaves), 1 <= leaf_size <= 128, or all leaves of one size M <= 4096
+ * that is 2^k times a size of at most 128 (see below); rank = r, the common HSS rank
  * (1 <= r <= 32): every U_i is m_i x r, every R_i and B_i is r x r.
  *
  * Generators (DEVICE, FP64, column-major blocks, caller-owned, read only):
@@ -254,6 +255,14 @@ superdc_status superdc_secular_batched_noalloc(int64_t nprob, const int64_t *off
  *       sibling: A(i, j) = U_i B_i U_j^T (nested U_p = [U_i R_i; U_j R_j]).
  * superdc_build_hss copies them into a library-owned handle (stream-ordered);
  * the caller may free its arrays once the stream has passed the call.
+ * Leaves of more than 128 rows (the paper's examples use 2048) are refined:
+ * each leaf block becomes a subtree with leaves of M / 2^k <= 128 rows whose
+ * top basis is the leaf's U, by the compression of superdc_build_hss_compress
+ * applied to the block with U as exact extra columns.  The refinement must be
+ * exact at rank r (relative projection residual <= 1e-12 at every node, as
+ * for banded or tridiagonal leaf blocks, Section 5's Examples 1-2), else
+ * SUPERDC_ERR_ARG; the handle then describes the refined tree (superdc_eig's
+ * levels count the refined levels).
  * -------------------------------------------------------------------- */
 typedef struct superdc_hss superdc_hss;
 typedef struct superdc_eigfact superdc_eigfact;
@@ -313,10 +322,9 @@ superdc_status superdc_build_hss_hermitian(const superdc_tree *tree, const doubl
  * sampled block row Y(I_i) - A(I_i, I_i) Omega(I_i); up the tree the children's
  * projected samples, corrected for the sibling block, give [R_c1; R_c2]; every
  * B_c1 = U_c1^T A(I_c1, I_c2) U_c2 is an exact block product; D_i = A(I_i, I_i).
- * *err_est (HOST, may be NULL) receives the largest ratio sigma_{rank+1} /
- * sigma_1 over the nodes' samples, the relative size of what was dropped
- * (taken from the samples' Gram matrices, so ratios below about
- * sqrt(eps) = 1.5e-8 read as that floor).
+ * *err_est (HOST, may be NULL) receives the largest relative residual
+ * ||M - U U^T M||_F / ||M||_F over the nodes' samples M, the relative size of
+ * what the rank-`rank` bases leave out.
  * The result is a handle as from superdc_build_hss; synchronous; work buffers
  * from the stream-ordered allocator. */
 typedef struct {

@@ -877,6 +877,24 @@ superdc_status superdc_build_hss(const superdc_tree *tree, const double *D, cons
     const int nn = tree->nnodes, r = tree->rank;
     if (nn < 1 || (nn % 2) == 0 || r < 1 || r > 32 || tree->n < 1) return SUPERDC_ERR_ARG;
     if (nn > 1 && !R) return SUPERDC_ERR_ARG;
+    bool big = false;
+    for (int i = 0; i < nn; i++) if (tree->lchild[i] < 0 && tree->leaf_size[i] > 128) big = true;
+    if (big && nn > 1) {
+        // leaves above 128 rows: refine them into exact rank-r subtrees first
+        std::vector<int32_t> lch2, rch2;
+        std::vector<int64_t> ls2;
+        double *D2 = nullptr, *U2 = nullptr, *R2 = nullptr, *B2 = nullptr;
+        superdc_status s = refine_leaves(tree, D, U, R, B, stream, lch2, rch2, ls2, &D2, &U2, &R2, &B2);
+        if (s != SUPERDC_OK) return s;
+        superdc_tree t2 = *tree;
+        t2.nnodes = (int32_t)lch2.size();
+        t2.lchild = lch2.data();
+        t2.rchild = rch2.data();
+        t2.leaf_size = ls2.data();
+        s = superdc_build_hss(&t2, D2, U2, R2, B2, stream, out);      // synchronises the stream
+        cudaFree(D2); cudaFree(U2); cudaFree(R2); cudaFree(B2);
+        return s;
+    }
     superdc_hss *h = new superdc_hss();
     h->nnodes = nn; h->r = r; h->n = tree->n;
     h->lch.assign(tree->lchild, tree->lchild + nn);

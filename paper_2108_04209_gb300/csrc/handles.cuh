@@ -76,3 +76,10 @@ FactorView factor_view(const superdc_eigfact *f, int l, int j);
 // dense leaf blocks: Y = Q_leaf^T X (trans) or Q_leaf X, all leaves
 superdc_status leaves_apply(const superdc_eigfact *f, int trans, int ncols, const double *X, int64_t ldx, double *Y,
                             int64_t ldy, cudaStream_t st);
+
+// Leaves above 128 rows refined into exact rank-r subtrees (compress.cu); new
+// device arrays returned in D2.. (cudaFree by the caller).
+superdc_status refine_leaves(const superdc_tree *tree, const double *D, const double *U, const double *R,
+                             const double *B, cudaStream_t st, std::vector<int32_t> &lch2,
+                             std::vector<int32_t> &rch2, std::vector<int64_t> &lsize2, double **D2, double **U2,
+                             double **R2, double **B2);

@@ -53,9 +53,8 @@ def test_compress_kernel_matrix_example4(n, leaf, rank):
 
 def test_compress_dense_input_of_exact_rank():
     """A dense matrix that is exactly a rank-4 HSS matrix is recovered to
-    rounding (every dropped singular value is zero; the estimate, from the
-    eigenvalues of the samples' Gram matrices, cannot resolve ratios below
-    about sqrt(eps) = 1.5e-8)."""
+    rounding (every dropped singular value is zero, and so is the samples'
+    projection residual up to rounding)."""
     h = inputs.hss_random(1024, 64, 4, seed=12)
     A = dense.dense_from_hss(h)
     Ad = torch.from_numpy(np.asfortranarray(A)).to(DEV)
@@ -64,7 +63,7 @@ def test_compress_dense_input_of_exact_rank():
     Ah = dense.dense_from_hss(H.generators())
     rec = np.linalg.norm(A - Ah, 2) / np.linalg.norm(A, 2)
     print("exact rank 4: err_est %.2e, reconstruction %.2e" % (H.err_est, rec))
-    assert H.err_est <= 1e-7 and rec <= 1e-12
+    assert H.err_est <= 1e-12 and rec <= 1e-12
 
 
 def test_table5_statistic_example4():

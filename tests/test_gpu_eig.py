@@ -202,6 +202,33 @@ def test_tridiagonal_131072_closed_form_every_eigenvalue():
     assert orth <= 1e-12 * np.sqrt(n)
 
 
+def test_tridiagonal_leaf2048_refined_closed_form():
+    """Example 1 with the paper's leaf size 2048 (n = 16384, 8 leaves): each
+    leaf block is refined into an exact rank-2 subtree with leaves of 128
+    rows; every eigenvalue against 3 - 2 cos(k pi/(n+1)), and the same
+    eigenvalues as the matrix built with leaves of 128 directly."""
+    n = 16384
+    h = inputs.hss_tridiag(n, 2048)
+    H, lam, F = gpu_eig(h)
+    k = np.arange(1, n + 1)
+    exact = np.sort(3.0 - 2.0 * np.cos(k * np.pi / (n + 1)))
+    rel = np.abs(lam - exact) / np.abs(exact)
+    print("tridiagonal n=16384, leaf 2048 refined to 128: levels", F.lmax, "max relative error", rel.max())
+    assert F.lmax == int(np.log2(n // 128))
+    assert rel.max() <= 1e-10
+    _, lam128, _ = gpu_eig(inputs.hss_tridiag(n, 128))
+    assert np.abs(lam - lam128).max() <= 1e-12
+
+
+def test_large_dense_leaf_that_is_not_rank_structured_is_rejected():
+    """A random dense leaf block of 256 rows has full off-diagonal rank: its
+    refinement at rank 4 is not exact, so superdc_build_hss refuses it."""
+    h = inputs.hss_random(1024, 256, 4, seed=3)
+    with pytest.raises(sdc.SuperDCError) as ei:
+        sdc.HSSMatrix(h)
+    assert ei.value.code == 1
+
+
 @pytest.fixture(scope="module")
 def large_131072():
     h = inputs.cfg_large_131072()
