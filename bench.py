@@ -24,7 +24,9 @@ on a 131072 x 64 block through superdc_apply_Q (time, HBM GB/s of its
 algorithmic bytes, FP64 fraction of its algorithmic flops), the direct-only
 eigendecomposition once (--no-direct skips it) and Table 5's statistic;
 ``hss_eig_16384`` times the clustered n=16384 problem level-batched and one
-node at a time, and the oracle on the same problem on the host cores.
+node at a time, and the oracle on the same problem on the host cores;
+``example1_262144`` runs the paper's Example 1 at its largest size with its
+leaf size 2048 against the closed-form spectrum.
 
 ``--impl reference`` times the CPU oracle (plain C + OpenMP, FP64) on a
 bounded sample of the same workload on the host cores.
@@ -325,6 +327,44 @@ def eig_headline(dev, peak, peak_src, direct=True, reps=3):
         out["eig_direct_only_s"] = {"wall": dw, "device": dev_ms * 1e-3}
     out["cpu_oracle"] = "not run at n=131072: the oracle needs ~5 min on 16 cores per run (direct O(n^2) sweeps " \
                         "at the top levels); timed at n=16384 in hss_eig_16384"
+    return out
+
+
+def example1(dev, n=262144, leaf=2048, reps=3, oracle=True):
+    """Section 5, Example 1 at the paper's largest size and leaf size: the
+    tridiagonal matrix (3 on the diagonal, -1 off it) in its explicit rank-2
+    HSS form with leaves of 2048 (refined by the library into subtrees of
+    128-row leaves), tau = 1e-10; every eigenvalue against 3 - 2 cos(k pi/(n+1));
+    beside the paper's 383.4 s (Matlab, 4 cores, same n, leaf and tau)."""
+    import torch
+    import paper_2108_04209_gb300 as sdc
+    from paper_2108_04209_gb300 import inputs
+    h = inputs.hss_tridiag(n, leaf)
+    t0 = time.perf_counter()
+    H = sdc.HSSMatrix(h)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    del h
+    opts = sdc.default_opts(tau=1e-10)
+    H.eig(opts)
+    wall, ev, (lam, F) = _timed(lambda: H.eig(opts), reps)
+    k = np.arange(1, n + 1)
+    exact = np.sort(3.0 - 2.0 * np.cos(k * np.pi / (n + 1)))
+    rel = float(np.max(np.abs(lam.cpu().numpy() - exact) / exact))
+    out = {"workload": "Example 1: tridiagonal (3, -1), n=%d, explicit rank-2 HSS form with leaves of %d "
+                       "(refined to %d-row leaves), tau=1e-10" % (n, leaf, n >> F.lmax),
+           "build_s": build_s, "eig_s": {"wall_median": wall, "device_median": ev * 1e-3},
+           "max_rel_error_vs_closed_form": rel, "deflated": F.stats()["deflated"],
+           "paper_s": {"total": 383.4, "dividing": 16.1, "hardware": "Matlab, 4 x 2.6 GHz CPU cores, FP64",
+                       "source": "Section 5, Example 1"}}
+    if oracle:
+        from oracle import superdc as osd
+        hs = inputs.hss_tridiag(8192, 128)
+        t0 = time.perf_counter()
+        osd.superdc(hs, tau=1e-10, mode=1)
+        out["cpu_oracle_n8192_s"] = {"s": time.perf_counter() - t0, "cores": len(os.sched_getaffinity(0)),
+                                     "note": "the oracle at n=8192, leaf 128 (n=262144 with leaves of 2048 "
+                                             "would take hours: its leaf solver is cyclic Jacobi)"}
     return out
 
 
@@ -636,6 +676,7 @@ def main():
             torch.cuda.empty_cache()
             line["hss_eig_131072"] = eig_headline(dev, peak, peak_src, direct=not args.no_direct)
             line["hss_eig_16384"] = eig_clustered(dev, oracle=(ws == 1 and not args.no_cpu_baseline))
+            line["example1_262144"] = example1(dev, oracle=not args.no_cpu_baseline)
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
