@@ -505,7 +505,7 @@ def main():
     kern = {}
     import ctypes
     for name in ("deflate", "tiles", "units", "secular", "lowner", "bnorm", "merge", "fmm_plan", "fmm_tree",
-                 "fmm_mom", "fmm_m2m", "fmm_m2l", "fmm_l2l", "fmm_secular", "fmm_secular_last", "fmm_lowner",
+                 "fmm_up", "fmm_m2l", "fmm_l2l", "fmm_secular", "fmm_secular_last", "fmm_lowner",
                  "fmm_bnorm"):
         n_ = ctypes.c_int64(0)
         t_ = ctypes.c_double(0.0)

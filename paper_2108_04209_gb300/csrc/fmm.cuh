@@ -34,7 +34,7 @@ struct FmmDev {
     const double *blo, *bhi;               // per box: interval [lo, hi] of its points
     const int32_t *nnear, *near;           // per box: near-list length (< 0: every source direct); list pool
     const int64_t *nstart;                 // per box: start of its near list in the pool
-    double *M, *W, *coef;                  // workspace: moments, node weights, leaf coefficients
+    double *W, *coef;                      // workspace: node weights, leaf coefficients
     double *F;                             // workspace: far field at every box's nodes
     double *lastp;                         // workspace: per leaf box (ncol wide), its sources' share of
                                            // the sums for the last eigenvalue (outside the tree)
@@ -44,6 +44,10 @@ struct FmmDev {
     int kslots;                            // matrix 1/(s_q2 - t_q) of nodes (M2L kernel, shared by
                                            // the far fields built on one plan)
     const int64_t *lev_off;                // per level: prefix of the FMM problems' box counts
+    const int64_t *top_off;                // the same per level counted from each problem's top box
+    int32_t *upcnt;                        // per box: children whose moments are done in the current
+                                           // upward pass (the last one computes the box; reset by it)
+    unsigned long long *upq;               // upward pass: next unclaimed leaf box, CTAs past the end
     int64_t cap_f;                         // capacity of the FMM problem list
     int ncol, nfield;                      // workspace widths
     unsigned long long *flops;             // algorithmic FP64 work of the far fields and of the

@@ -46,6 +46,7 @@
 // expansions on the leaf boxes' (fixed) intervals are computed once per
 // problem; each sweep costs a near-field pass plus one Clenshaw evaluation.
 #include <algorithm>
+#include <mutex>
 #include "common.cuh"
 #include "fmm.cuh"
 #include "secular.cuh"
@@ -60,7 +61,15 @@ namespace {
 
 constexpr int P = FMM_P;
 constexpr int B = FMM_BOX;
-constexpr double FMM_KAPPA = 1.0;
+// admissibility: gap >= 0.75 x the larger width.  The nearest source then lies
+// at least 2.5 half-widths from either box's centre (Bernstein ellipse
+// rho >= 2.5 + sqrt(5.25) = 4.79): at 22 nodes the interpolated 1/(s-t) stays at
+// the rounding floor (~1e-14 relative) and 1/(s-t)^2 within ~1e-13 over box-width
+// ratios 1e-3..1e3, while index-based boxes of random spectra drop from ~4.3
+// to ~3.2-3.4 near boxes per leaf (with 1.0 the box between two neighbours must
+// be at least as wide as both, which a random width sequence meets a third of
+// the time)
+constexpr double FMM_KAPPA = 0.75;
 constexpr int SPLIT_NEAR = 512 / B;   // leaf boxes with this many near boxes (512 poles) or more: CTA-split sweeps
 constexpr int TAIL_X = 12;        // k_secular_fmm hands a box's last roots to the tail pass below this many busy lanes
 constexpr int WMAX = 32;          // widest moment / coefficient block (columns)
@@ -356,34 +365,28 @@ struct SrcArgs {
     int col0, nc;
 };
 
-// leaf moments and node weights
+// leaf moments and node weights of leaf box gl (box g, index Tb within its
+// problem p); one thread per source (threads B.. only join the sums)
 //   M_SEC: w_j = z_j^2 at d_j            M_BN: w_i = vhat_i^2 at d_i
 //   M_LOW: +1 at lambda_j, -1 at d_j (j < m-1; Chebyshev differences of the pair)
 //   M_CT:  vhat_i x_{src_i} at d_i       M_CN: b_j x_{pinv_j} at lambda_j (j < m-1)
-template <int MODE>
-__global__ void __launch_bounds__(B) k_fmm_leafmom(FmmDev pl, SrcArgs a)
+constexpr int UP_ROWS = (B > 2 * P) ? B : 2 * P;   // rows of the staging arrays (sources, or 2 children x P)
+
+template <int MODE, int WW>
+__device__ __forceinline__ void leaf_moments(const FmmDev &pl, const SrcArgs &a, int64_t p, int64_t gl, int64_t g,
+                                             int Tb, int nw, double (*Tt)[P + 1], double (*Wt)[WW + 1],
+                                             double (*Ms)[WW + 1], const double *Tx)
 {
-    __shared__ double Tt[B][P + 1];
-    __shared__ double Wt[B][WMAX + 1];
-    __shared__ double Ms[P][WMAX + 1];
-    __shared__ double Tx[P * P], xq[P];
-    cheb_tables(xq, Tx);
-    const int nw = (MODE == M_CT || MODE == M_CN) ? a.nc : 1;
     const int tid = threadIdx.x;
-    const int64_t nleaf = pl.leaf_base[pl.nprob];
-    for (int64_t gl = blockIdx.x; gl < nleaf; gl += gridDim.x) {
-        const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
-        if (pl.fslot[p] < 0) continue;
-        const int64_t b0 = a.off[p];
-        const int m = a.mk[p];
-        const int Tb = (int)(gl - pl.leaf_base[p]);
-        const int64_t g = pl.box_base[p] + Tb;
-        double c, h;
-        box_ch(pl.blo[g], pl.bhi[g], c, h);
-        const int j = Tb * B + tid;
-        const int jend = (MODE == M_LOW || MODE == M_CN) ? m - 1 : m;
-        const bool act = j < jend;
-        __syncthreads();
+    const int64_t b0 = a.off[p];
+    const int m = a.mk[p];
+    double c, h;
+    box_ch(pl.blo[g], pl.bhi[g], c, h);
+    const int j = Tb * B + tid;
+    const int jend = (MODE == M_LOW || MODE == M_CN) ? m - 1 : m;
+    const bool act = tid < B && j < jend;
+    __syncthreads();
+    if (tid < B) {
         if (MODE == M_LOW) {
             // D_n = T_n(b) - T_n(a) with b = a + delta, by the recurrence
             // D_{n+1} = 2 delta T_n(b) + 2 a D_n - D_{n-1} (no cancellation)
@@ -434,25 +437,24 @@ __global__ void __launch_bounds__(B) k_fmm_leafmom(FmmDev pl, SrcArgs a)
                 for (int q = 0; q < nw; q++) Wt[tid][q] = act ? bj * a.X[row + (int64_t)(a.col0 + q) * a.ldx] : 0.0;
             }
         }
-        __syncthreads();
-        for (int t = tid; t < P * nw; t += B) {
-            const int n = t / nw, q = t % nw;
-            double s = 0.0;
-            for (int jj = 0; jj < B; jj++) s = fma(Tt[jj][n], Wt[jj][q], s);
-            Ms[n][q] = s;
-            pl.M[(g * P + n) * pl.ncol + q] = s;
-        }
-        __syncthreads();
-        for (int t = tid; t < P * nw; t += B) {
-            const int qn = t / nw, q = t % nw;
-            double s = Ms[0][q];
-            for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
-            pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
-        }
-        // Chebyshev recurrence per source, moments, moments -> node weights
-        const int64_t cnt = max(0, min(B, jend - Tb * B));
-        fl_add(pl, cnt * ((MODE == M_LOW) ? 4 : 2) * (P - 2) + 2 * cnt * P * nw + 2 * P * P * nw);
     }
+    __syncthreads();
+    for (int t = tid; t < P * nw; t += blockDim.x) {
+        const int n = t / nw, q = t % nw;
+        double s = 0.0;
+        for (int jj = 0; jj < B; jj++) s = fma(Tt[jj][n], Wt[jj][q], s);
+        Ms[n][q] = s;
+    }
+    __syncthreads();
+    for (int t = tid; t < P * nw; t += blockDim.x) {
+        const int qn = t / nw, q = t % nw;
+        double s = Ms[0][q];
+        for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
+        pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
+    }
+    // Chebyshev recurrence per source, moments, moments -> node weights
+    const int64_t cnt = max(0, min(B, jend - Tb * B));
+    fl_add(pl, cnt * ((MODE == M_LOW) ? 4 : 2) * (P - 2) + 2 * cnt * P * nw + 2 * P * P * nw);
 }
 
 // Boxes of level l of the FMM problems, enumerated as (FMM problem f, box b)
@@ -474,9 +476,19 @@ __device__ __forceinline__ bool level_box(const FmmDev &pl, const int32_t *__res
     return true;
 }
 
-// per-level prefix of the box counts of the FMM problems (one CTA per level)
+// per-level prefix of the box counts of the FMM problems (one CTA per level):
+// lev_off by absolute level (leaves 0), top_off by level counted from each
+// problem's top box (top 0)
+__device__ __forceinline__ int levoff_count(int nb0, int l, bool top)
+{
+    const int L = lev_count(nb0);
+    if (l >= L) return 0;
+    return lev_nb(nb0, top ? L - 1 - l : l);
+}
+
 __global__ void k_fmm_levoff(const int32_t *__restrict__ mk, const int32_t *__restrict__ fprob,
-                             const int32_t *__restrict__ nfmm, int64_t cap_f, int64_t *__restrict__ lev_off)
+                             const int32_t *__restrict__ nfmm, int64_t cap_f, int64_t *__restrict__ lev_off,
+                             int64_t *__restrict__ top_off)
 {
     __shared__ int64_t part[1024];
     const int l = blockIdx.x;
@@ -484,94 +496,161 @@ __global__ void k_fmm_levoff(const int32_t *__restrict__ mk, const int32_t *__re
     const int T = blockDim.x;
     const int per = (nf + T - 1) / T;
     const int beg = min(nf, (int)threadIdx.x * per), end = min(nf, beg + per);
-    int64_t sum = 0;
-    for (int f = beg; f < end; f++) {
-        const int nb0 = (mk[fprob[f]] + B - 1) / B;
-        if (l < lev_count(nb0)) sum += lev_nb(nb0, l);
-    }
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t acc = 0;
-        for (int i = 0; i < T; i++) { const int64_t v = part[i]; part[i] = acc; acc += v; }
-        lev_off[(int64_t)l * (cap_f + 1) + nf] = acc;
-    }
-    __syncthreads();
-    int64_t acc = part[threadIdx.x];
-    for (int f = beg; f < end; f++) {
-        lev_off[(int64_t)l * (cap_f + 1) + f] = acc;
-        const int nb0 = (mk[fprob[f]] + B - 1) / B;
-        if (l < lev_count(nb0)) acc += lev_nb(nb0, l);
+    for (int pass = 0; pass < 2; pass++) {
+        const bool top = pass == 1;
+        int64_t *out = (top ? top_off : lev_off) + (int64_t)l * (cap_f + 1);
+        int64_t sum = 0;
+        for (int f = beg; f < end; f++) sum += levoff_count((mk[fprob[f]] + B - 1) / B, l, top);
+        __syncthreads();
+        part[threadIdx.x] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t acc = 0;
+            for (int i = 0; i < T; i++) { const int64_t v = part[i]; part[i] = acc; acc += v; }
+            out[nf] = acc;
+        }
+        __syncthreads();
+        int64_t acc = part[threadIdx.x];
+        for (int f = beg; f < end; f++) {
+            out[f] = acc;
+            acc += levoff_count((mk[fprob[f]] + B - 1) / B, l, top);
+        }
     }
 }
 
-// moments of the boxes of level l from their children's node weights:
+// moments of box g (level l >= 1, index b) from its children's node weights:
 // M_n(parent) = sum_children sum_q W_q(child) T_n(alpha x_q + beta), exact
 // because T_n(alpha u + beta) has degree n < P and the children's weights
-// reproduce every moment of degree < P
-__global__ void __launch_bounds__(128) k_fmm_m2m(FmmDev pl, const int32_t *__restrict__ mk, int l, int nw)
+// reproduce every moment of degree < P.  The children's weights are read
+// through L2 (ld.global.cg): the sibling's were written by another CTA of the
+// same launch, which published them before its arrival count.
+template <int WW>
+__device__ __forceinline__ void m2m_box(const FmmDev &pl, int64_t p, int nb0, int l, int b, int64_t g, int nw,
+                                        double (*Tv)[P + 1], double (*Wc)[WW + 1], double (*Ms)[WW + 1],
+                                        const double *Tx, const double *xq)
 {
-    __shared__ double Tv[2][P][P + 1];
-    __shared__ double Wc[2][P][WMAX + 1];
-    __shared__ double Ms[P][WMAX + 1];
-    __shared__ double Tx[P * P], xq[P];
-    cheb_tables(xq, Tx);
     const int tid = threadIdx.x;
-    const int64_t nu = pl.lev_off[(int64_t)l * (pl.cap_f + 1) + *pl.nfmm];
-    for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
-        int64_t p, g;
-        int nb0, b;
-        if (!level_box(pl, mk, l, u, p, nb0, b, g)) continue;
-        double cP = 0.0, ihP = 1.0;
-        if (tid < 2 * P) {                 // the warps that build Tv (uniform FP64 work costs every warp)
-            double hP;
-            box_ch(pl.blo[g], pl.bhi[g], cP, hP);
-            ihP = 1.0 / hP;
+    double cP = 0.0, ihP = 1.0;
+    if (tid < 2 * P) {                 // the threads that build Tv (uniform FP64 work costs every warp)
+        double hP;
+        box_ch(pl.blo[g], pl.bhi[g], cP, hP);
+        ihP = 1.0 / hP;
+    }
+    const int nbc = lev_nb(nb0, l - 1);
+    const int64_t gcb = pl.box_base[p] + lev_base(nb0, l - 1);
+    const int nch = (2 * b + 1 < nbc) ? 2 : 1;
+    __syncthreads();
+    for (int t = tid; t < 2 * P; t += blockDim.x) {
+        const int ci = t / P, q = t % P;
+        if (ci >= nch) continue;
+        const int64_t gc = gcb + 2 * b + ci;
+        double cc, hc;
+        box_ch(pl.blo[gc], pl.bhi[gc], cc, hc);
+        const double v = (cc + hc * xq[q] - cP) * ihP;
+        double t0 = 1.0, t1 = v;
+        Tv[t][0] = 1.0;
+        Tv[t][1] = v;
+        for (int n = 2; n < P; n++) {
+            const double t2 = 2.0 * v * t1 - t0;
+            Tv[t][n] = t2;
+            t0 = t1; t1 = t2;
         }
-        const int nbc = lev_nb(nb0, l - 1);
-        const int64_t gcb = pl.box_base[p] + lev_base(nb0, l - 1);
-        const int nch = (2 * b + 1 < nbc) ? 2 : 1;
+    }
+    for (int t = tid; t < 2 * P * nw; t += blockDim.x) {
+        const int ci = t / (P * nw), r = t % (P * nw);
+        if (ci >= nch) continue;
+        const int64_t gc = gcb + 2 * b + ci;
+        Wc[ci * P + r / nw][r % nw] = __ldcg(&pl.W[(gc * P + r / nw) * pl.ncol + r % nw]);
+    }
+    __syncthreads();
+    for (int t = tid; t < P * nw; t += blockDim.x) {
+        const int n = t / nw, q = t % nw;
+        double s = 0.0;
+        for (int ci = 0; ci < nch; ci++)
+            for (int k = 0; k < P; k++) s = fma(Tv[ci * P + k][n], Wc[ci * P + k][q], s);
+        Ms[n][q] = s;
+    }
+    __syncthreads();
+    for (int t = tid; t < P * nw; t += blockDim.x) {
+        const int qn = t / nw, q = t % nw;
+        double s = Ms[0][q];
+        for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
+        pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
+    }
+    // children's node positions, the children's weights into moments, moments -> weights
+    fl_add(pl, (int64_t)nch * 2 * P * (P - 2) + (int64_t)nch * 2 * P * P * nw + 2 * P * P * nw);
+}
+
+// The whole upward pass in one launch: the leaf boxes' moments and node
+// weights (grid-stride over the leaf boxes of the FMM problems), then each
+// box climbs towards its problem's top box.  A box that has finished its
+// weights counts itself into its parent's arrival counter (after a device-
+// scope fence); the child that arrives last computes the parent and climbs
+// on, the other stops.  No CTA ever waits for another, so any grid size and
+// any scheduling order are safe, and every box is computed exactly once, by
+// the same arithmetic as a level-by-level pass.  The counter is reset by the
+// child that consumes it, ready for the next far field built on the plan.
+// Threads and staged columns of the upward pass: the one-column far fields
+// (secular, b, Loewner) take 64 threads (one per source of a box of 64, and
+// the 2P children's nodes of a box), the Cauchy-like ones 128 and WMAX columns.
+template <int MODE> constexpr bool up_wide() { return MODE == M_CT || MODE == M_CN; }
+template <int MODE> constexpr int up_threads() { return up_wide<MODE>() ? 128 : 64; }
+template <int MODE> constexpr int up_cols() { return up_wide<MODE>() ? WMAX : 1; }
+
+template <int MODE>
+__global__ void __launch_bounds__(up_threads<MODE>()) k_fmm_up(FmmDev pl, SrcArgs a)
+{
+    constexpr int WW = up_cols<MODE>();
+    __shared__ double Tt[UP_ROWS][P + 1];
+    __shared__ double Wt[UP_ROWS][WW + 1];
+    __shared__ double Ms[P][WW + 1];
+    __shared__ double Tx[P * P], xq[P];
+    __shared__ int last;
+    __shared__ int64_t next;
+    cheb_tables(xq, Tx);
+    const int nw = (MODE == M_CT || MODE == M_CN) ? a.nc : 1;
+    const int tid = threadIdx.x;
+    const int64_t nleaf = pl.leaf_base[pl.nprob];
+    for (;;) {
+        // leaf boxes are claimed one at a time: a CTA that climbs takes fewer
+        // (a fixed stride would pile the climbs onto the CTAs that start late)
         __syncthreads();
-        for (int t = tid; t < 2 * P; t += blockDim.x) {
-            const int ci = t / P, q = t % P;
-            if (ci >= nch) continue;
-            const int64_t gc = gcb + 2 * b + ci;
-            double cc, hc;
-            box_ch(pl.blo[gc], pl.bhi[gc], cc, hc);
-            const double v = (cc + hc * xq[q] - cP) * ihP;
-            double t0 = 1.0, t1 = v;
-            Tv[ci][q][0] = 1.0;
-            Tv[ci][q][1] = v;
-            for (int n = 2; n < P; n++) {
-                const double t2 = 2.0 * v * t1 - t0;
-                Tv[ci][q][n] = t2;
-                t0 = t1; t1 = t2;
+        if (tid == 0) {
+            next = (int64_t)atomicAdd(&pl.upq[0], 1ull);
+            if (next >= nleaf && atomicAdd(&pl.upq[1], 1ull) == gridDim.x - 1) {
+                pl.upq[0] = 0;                 // every CTA has run past the end: reset for the next launch
+                pl.upq[1] = 0;
             }
         }
-        for (int t = tid; t < 2 * P * nw; t += blockDim.x) {
-            const int ci = t / (P * nw), r = t % (P * nw);
-            if (ci >= nch) continue;
-            const int64_t gc = gcb + 2 * b + ci;
-            Wc[ci][r / nw][r % nw] = pl.W[(gc * P + r / nw) * pl.ncol + r % nw];
-        }
         __syncthreads();
-        for (int t = tid; t < P * nw; t += blockDim.x) {
-            const int n = t / nw, q = t % nw;
-            double s = 0.0;
-            for (int ci = 0; ci < nch; ci++)
-                for (int k = 0; k < P; k++) s = fma(Tv[ci][k][n], Wc[ci][k][q], s);
-            Ms[n][q] = s;
-            pl.M[(g * P + n) * pl.ncol + q] = s;
+        const int64_t gl = next;
+        if (gl >= nleaf) break;
+        const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
+        if (pl.fslot[p] < 0) continue;
+        const int Tb = (int)(gl - pl.leaf_base[p]);
+        const int64_t g = pl.box_base[p] + Tb;
+        leaf_moments<MODE, WW>(pl, a, p, gl, g, Tb, nw, Tt, Wt, Ms, Tx);
+        const int nb0 = (a.mk[p] + B - 1) / B;
+        const int L = lev_count(nb0);
+        int l = 0, b = Tb;
+        while (l + 1 < L) {
+            const int bp = b >> 1;
+            const int nch = (2 * bp + 1 < lev_nb(nb0, l)) ? 2 : 1;
+            const int64_t gp = pl.box_base[p] + lev_base(nb0, l + 1) + bp;
+            __threadfence();               // this box's weights, visible before the count
+            __syncthreads();
+            if (tid == 0) {
+                const int old = atomicAdd(&pl.upcnt[gp], 1);
+                last = (old == nch - 1);
+                if (last) pl.upcnt[gp] = 0;
+            }
+            __syncthreads();
+            if (!last) break;
+            __threadfence();
+            m2m_box<WW>(pl, p, nb0, l + 1, bp, gp, nw, Tt, Wt, Ms, Tx, xq);
+            l++;
+            b = bp;
         }
-        __syncthreads();
-        for (int t = tid; t < P * nw; t += blockDim.x) {
-            const int qn = t / nw, q = t % nw;
-            double s = Ms[0][q];
-            for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
-            pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
-        }
-        // children's node positions, the children's weights into moments, moments -> weights
-        fl_add(pl, (int64_t)nch * 2 * P * (P - 2) + (int64_t)nch * 2 * P * P * nw + 2 * P * P * nw);
     }
 }
 
@@ -771,76 +850,129 @@ __global__ void __launch_bounds__(128) k_fmm_m2l(FmmDev pl, const int32_t *__res
     }
 }
 
-// Local-to-local for the boxes of level l: add the parent's far field,
-// interpolated at the box's Chebyshev nodes (Chebyshev coefficients of the
-// parent's node values, evaluated at alpha x_q + beta).  On the leaf level
-// the field is converted to Chebyshev coefficients for the targets.
-__global__ void __launch_bounds__(128) k_fmm_l2l(FmmDev pl, const int32_t *__restrict__ mk, int l, int nf)
+// Local-to-local for box g (level l, index b, below its problem's top box):
+// add the parent's far field, interpolated at the box's Chebyshev nodes
+// (Chebyshev coefficients of the parent's node values, evaluated at
+// alpha x_q + beta).  On the leaf level the field is converted to Chebyshev
+// coefficients for the targets.  Computed by a group of G threads (a warp, or
+// the whole CTA), tid in [0, G); WF the staged width.
+template <int G>
+__device__ __forceinline__ void grp_sync()
 {
+    if (G == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <int G, int WF>
+__device__ __forceinline__ void l2l_box(const FmmDev &pl, int64_t p, int nb0, int l, int b, int64_t g, int nf, int tid,
+                                        double (*Fs)[WF + 1], double (*Ac)[WF + 1], double (*Tv)[P + 1],
+                                        const double *Tx, const double *xq)
+{
+    const bool alln = pl.nnear[g] < 0;
+    const int64_t gP = pl.box_base[p] + lev_base(nb0, l + 1) + (b >> 1);
+    grp_sync<G>();
+    if (!alln) {
+        // parent's node values
+        for (int t = tid; t < P * nf; t += G) Fs[t / nf][t % nf] = pl.F[(gP * P + t / nf) * pl.nfield + t % nf];
+        if (tid < P) {
+            double cP, hP, cT, hT;
+            box_ch(pl.blo[gP], pl.bhi[gP], cP, hP);
+            box_ch(pl.blo[g], pl.bhi[g], cT, hT);
+            const double v = (cT + hT * xq[tid] - cP) / hP;
+            double t0 = 1.0, t1 = v;
+            Tv[tid][0] = 1.0;
+            Tv[tid][1] = v;
+            for (int n = 2; n < P; n++) {
+                const double t2 = 2.0 * v * t1 - t0;
+                Tv[tid][n] = t2;
+                t0 = t1; t1 = t2;
+            }
+        }
+        grp_sync<G>();
+        for (int t = tid; t < P * nf; t += G) {
+            const int n = t / nf, f = t % nf;
+            double s = 0.0;
+            for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
+            Ac[n][f] = s * ((n == 0) ? (1.0 / P) : (2.0 / P));
+        }
+        grp_sync<G>();
+        for (int t = tid; t < P * nf; t += G) {
+            const int q = t / nf, f = t % nf;
+            double s = pl.F[(g * P + q) * pl.nfield + f];
+            for (int n = 0; n < P; n++) s = fma(Tv[q][n], Ac[n][f], s);
+            Fs[q][f] = s;     // own row (q, f) only
+        }
+    } else {
+        for (int t = tid; t < P * nf; t += G) Fs[t / nf][t % nf] = 0.0;
+    }
+    grp_sync<G>();
+    // parent's node values -> coefficients -> this box's nodes; on the
+    // leaves the field -> coefficients for the targets
+    if (tid == 0 && pl.flops) {
+        const int64_t v = (alln ? 0 : 2 * P * (P - 2) + 4 * P * P * nf) + ((l == 0) ? 2 * P * P * nf : 0);
+        if (v > 0) atomicAdd(pl.flops, (unsigned long long)v);
+    }
+    if (l > 0) {
+        for (int t = tid; t < P * nf; t += G) pl.F[(g * P + t / nf) * pl.nfield + t % nf] = Fs[t / nf][t % nf];
+    } else {
+        const int64_t gl = pl.leaf_base[p] + b;
+        for (int t = tid; t < P * nf; t += G) {
+            const int n = t / nf, f = t % nf;
+            double s = 0.0;
+            for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
+            pl.coef[(gl * pl.nfield + f) * P + n] = s * ((n == 0) ? (1.0 / P) : (2.0 / P));
+        }
+    }
+}
+
+// Downward pass, launched per top-relative level t0 >= 1 (levels counted from
+// each problem's top box, level L-1 of a problem with L levels), one CTA per
+// box of level t0 (the parent is final: done by an earlier launch).
+//   NARROW (fields of at most NARROW_NF columns: secular, b, Loewner): the
+//     CTA also finishes the box's subtree DOWN_LEVELS - 1 levels further
+//     down, level by level, a warp per box (the 1, 2, 4, 8 boxes of the four
+//     levels take 1, 1, 1, 2 rounds of the four warps), so the narrow fields
+//     take a quarter of the launches;
+//   wide fields (the Cauchy-like ones, one field per column): one level per
+//     launch, the whole CTA on one box.
+// Same arithmetic per box either way.
+constexpr int DOWN_LEVELS = 4;
+constexpr int NARROW_NF = 4;
+
+template <bool NARROW>
+__global__ void __launch_bounds__(128) k_fmm_down(FmmDev pl, const int32_t *__restrict__ mk, int t0, int nf)
+{
+    constexpr int WF = NARROW ? NARROW_NF : WMAX;
+    constexpr int NG = NARROW ? 4 : 1;               // box groups per CTA
+    constexpr int G = 128 / NG;
     __shared__ double xq[P];
     __shared__ double Tx[P * P];
-    __shared__ double Fs[P][WMAX + 1];
-    __shared__ double Ac[P][WMAX + 1];
-    __shared__ double Tv[P][P + 1];
+    __shared__ double Fs[NG][P][WF + 1];
+    __shared__ double Ac[NG][P][WF + 1];
+    __shared__ double Tv[NG][P][P + 1];
     cheb_tables(xq, Tx);
-    const int tid = threadIdx.x;
-    const int64_t nu = pl.lev_off[(int64_t)l * (pl.cap_f + 1) + *pl.nfmm];
+    const int grp = threadIdx.x / G, tid = threadIdx.x % G;
+    const int nf_ = *pl.nfmm;
+    const int64_t *lo = pl.top_off + (int64_t)t0 * (pl.cap_f + 1);
+    const int64_t nu = lo[nf_];
     for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
-        int64_t p, g;
-        int nb0, b;
-        if (!level_box(pl, mk, l, u, p, nb0, b, g)) continue;
+        const int64_t f = sdc_upper_index(lo, (int64_t)nf_, u);
+        const int br = (int)(u - lo[f]);
+        const int64_t p = pl.fprob[f];
+        if (pl.fslot[p] < 0) continue;
+        const int nb0 = (mk[p] + B - 1) / B;
         const int L = lev_count(nb0);
-        if (l >= L - 1) continue;                      // the top box has no far field
-        const bool alln = pl.nnear[g] < 0;
-        const int64_t gP = pl.box_base[p] + lev_base(nb0, l + 1) + (b >> 1);
-        __syncthreads();
-        if (!alln) {
-            // parent's Chebyshev coefficients
-            for (int t = tid; t < P * nf; t += blockDim.x) Fs[t / nf][t % nf] = pl.F[(gP * P + t / nf) * pl.nfield + t % nf];
-            if (tid < P) {
-                double cP, hP, cT, hT;
-                box_ch(pl.blo[gP], pl.bhi[gP], cP, hP);
-                box_ch(pl.blo[g], pl.bhi[g], cT, hT);
-                const double v = (cT + hT * xq[tid] - cP) / hP;
-                double t0 = 1.0, t1 = v;
-                Tv[tid][0] = 1.0;
-                Tv[tid][1] = v;
-                for (int n = 2; n < P; n++) {
-                    const double t2 = 2.0 * v * t1 - t0;
-                    Tv[tid][n] = t2;
-                    t0 = t1; t1 = t2;
-                }
-            }
-            __syncthreads();
-            for (int t = tid; t < P * nf; t += blockDim.x) {
-                const int n = t / nf, f = t % nf;
-                double s = 0.0;
-                for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
-                Ac[n][f] = s * ((n == 0) ? (1.0 / P) : (2.0 / P));
-            }
-            __syncthreads();
-            for (int t = tid; t < P * nf; t += blockDim.x) {
-                const int q = t / nf, f = t % nf;
-                double s = pl.F[(g * P + q) * pl.nfield + f];
-                for (int n = 0; n < P; n++) s = fma(Tv[q][n], Ac[n][f], s);
-                Fs[q][f] = s;     // own row (q, f) only
-            }
-        } else {
-            for (int t = tid; t < P * nf; t += blockDim.x) Fs[t / nf][t % nf] = 0.0;
-        }
-        __syncthreads();
-        // parent's node values -> coefficients -> this box's nodes; on the
-        // leaves the field -> coefficients for the targets
-        fl_add(pl, (alln ? 0 : 2 * P * (P - 2) + 4 * P * P * nf) + ((l == 0) ? 2 * P * P * nf : 0));
-        if (l > 0) {
-            for (int t = tid; t < P * nf; t += blockDim.x) pl.F[(g * P + t / nf) * pl.nfield + t % nf] = Fs[t / nf][t % nf];
-        } else {
-            const int64_t gl = pl.leaf_base[p] + b;
-            for (int t = tid; t < P * nf; t += blockDim.x) {
-                const int n = t / nf, f = t % nf;
-                double s = 0.0;
-                for (int q = 0; q < P; q++) s = fma(Fs[q][f], Tx[q * P + n], s);
-                pl.coef[(gl * pl.nfield + f) * P + n] = s * ((n == 0) ? (1.0 / P) : (2.0 / P));
+        const int lr = L - 1 - t0;
+        if (lr < 0 || br >= lev_nb(nb0, lr)) continue;
+        for (int k = 0; k < (NARROW ? DOWN_LEVELS : 1) && lr - k >= 0; k++) {
+            const int l = lr - k;
+            const int b0 = br << k, bend = min(lev_nb(nb0, l), (br + 1) << k);
+            __syncthreads();                   // the parents (previous level) are written
+            for (int bb = b0; bb < bend; bb += NG) {
+                const int b = bb + grp;
+                if (b < bend)
+                    l2l_box<G, WF>(pl, p, nb0, l, b, pl.box_base[p] + lev_base(nb0, l) + b, nf, tid, Fs[grp],
+                                   Ac[grp], Tv[grp], Tx, xq);
             }
         }
     }
@@ -1693,6 +1825,26 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
 
 unsigned fmm_grid() { return (unsigned)(sdc_num_sms() * 8); }
 
+// Grid of the upward pass: as many CTAs as the GPU holds at once (every CTA
+// strides over the same number of leaf boxes, so a second partial wave would
+// double the launch), from the occupancy calculator, once per device.
+template <int MODE>
+unsigned up_grid()
+{
+    static std::mutex mu;
+    static int per_sm[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return (unsigned)sdc_num_sms();
+    std::lock_guard<std::mutex> lk(mu);
+    if (per_sm[dev] == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_fmm_up<MODE>, up_threads<MODE>(), 0) != cudaSuccess)
+            v = 1;
+        per_sm[dev] = v > 0 ? v : 1;
+    }
+    return (unsigned)(sdc_num_sms() * per_sm[dev]);
+}
+
 // one warp per (FMM problem, column) of k_fmm_lastsum, 4 warps per CTA
 unsigned lastsum_grid(const FmmPlan &pl, int nc)
 {
@@ -1700,10 +1852,13 @@ unsigned lastsum_grid(const FmmPlan &pl, int nc)
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((w + 3) / 4, (int64_t)sdc_num_sms() * 8));
 }
 
-// grid of a level launch: at most one CTA per box the level can hold
-unsigned lev_grid(const FmmPlan &pl, int l)
+// grid of a downward-pass launch: at most one CTA per box that top-relative
+// level t0 can hold (a problem has at most 2^t0 boxes there, and at most its
+// leaf boxes)
+unsigned down_grid(const FmmPlan &pl, int t0)
 {
-    const int64_t nb = (int64_t)lev_nb(pl.nb0max, l) * std::max<int64_t>(1, pl.cap_f);
+    const int64_t per = (t0 >= 30) ? (int64_t)pl.nb0max : std::min<int64_t>(pl.nb0max, (int64_t)1 << t0);
+    const int64_t nb = per * std::max<int64_t>(1, pl.cap_f);
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)sdc_num_sms() * 8));
 }
 
@@ -1720,13 +1875,16 @@ superdc_status far_field(const FmmPlan &pl, const SrcArgs &a, int nw, int kmode,
 {
     const unsigned g = fmm_grid();
     const int nf = (KER == K_SEC) ? 4 : nw;
-    PROF_LAUNCH("fmm_mom", st, k_fmm_leafmom<MODE><<<g, B, 0, st>>>(pl.dv, a));
-    for (int l = 1; l < pl.lmax; l++)
-        PROF_LAUNCH("fmm_m2m", st, k_fmm_m2m<<<lev_grid(pl, l), 128, 0, st>>>(pl.dv, a.mk, l, nw));
+    PROF_LAUNCH("fmm_up", st, k_fmm_up<MODE><<<up_grid<MODE>(), up_threads<MODE>(), 0, st>>>(pl.dv, a));
     PROF_LAUNCH("fmm_m2l", st, k_fmm_m2l<KER><<<g, 128, 0, st>>>(pl.dv, a.mk, nw,
                                                                   pl.dv.kslots > 0 ? kmode : 0));
-    for (int l = pl.lmax - 2; l >= 0; l--)
-        PROF_LAUNCH("fmm_l2l", st, k_fmm_l2l<<<lev_grid(pl, l), 128, 0, st>>>(pl.dv, a.mk, l, nf));
+    if (nf <= NARROW_NF) {
+        for (int t0 = 1; t0 < pl.lmax; t0 += DOWN_LEVELS)
+            PROF_LAUNCH("fmm_l2l", st, k_fmm_down<true><<<down_grid(pl, t0), 128, 0, st>>>(pl.dv, a.mk, t0, nf));
+    } else {
+        for (int t0 = 1; t0 < pl.lmax; t0++)
+            PROF_LAUNCH("fmm_l2l", st, k_fmm_down<false><<<down_grid(pl, t0), 128, 0, st>>>(pl.dv, a.mk, t0, nf));
+    }
     return SUPERDC_OK;
 }
 
@@ -1791,7 +1949,6 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     SDC_CHECK(al(&nnear, pl.cap_boxes));
     SDC_CHECK(al(&near, pl.cap_boxes * FMM_NPOOL));
     SDC_CHECK(al(&nstart, pl.cap_boxes));
-    SDC_CHECK(al(&d.M, (size_t)pl.cap_boxes * P * ncol));
     SDC_CHECK(al(&d.W, (size_t)pl.cap_boxes * P * ncol));
     SDC_CHECK(al(&d.coef, (size_t)pl.cap_leaves * nfield * P));
     SDC_CHECK(al(&d.F, (size_t)pl.cap_boxes * P * nfield));
@@ -1805,9 +1962,15 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     d.kslots = (kslots > 0 && kbytes <= 8.0e9) ? kslots : 0;
     d.kmat = nullptr;
     if (d.kslots > 0) SDC_CHECK(al(&d.kmat, (size_t)pl.cap_boxes * d.kslots * P * P));
-    int64_t *lev_off;
+    int64_t *lev_off, *top_off;
     SDC_CHECK(al(&lev_off, (size_t)pl.lmax * (nf_cap + 1)));
+    SDC_CHECK(al(&top_off, (size_t)pl.lmax * (nf_cap + 1)));
+    SDC_CHECK(al(&d.upcnt, pl.cap_boxes));
+    SDC_CHECK(cudaMemsetAsync(d.upcnt, 0, (size_t)pl.cap_boxes * sizeof(int32_t), st));
+    SDC_CHECK(al(&d.upq, 2));
+    SDC_CHECK(cudaMemsetAsync(d.upq, 0, 2 * sizeof(unsigned long long), st));
     d.lev_off = lev_off;
+    d.top_off = top_off;
     d.cap_f = nf_cap;
 
     d.flops = prof_counter("fmm_flops");
@@ -1818,7 +1981,8 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     const unsigned gt = (unsigned)std::min<int64_t>(nprob, (int64_t)sdc_num_sms() * 4);
     PROF_LAUNCH("fmm_tree", st, k_fmm_tree<<<gt, 256, 0, st>>>(nprob, off, mk, dk, box_base, fslot, blo, bhi,
                                                                nnear, nstart, near, used));
-    PROF_LAUNCH("fmm_plan", st, k_fmm_levoff<<<pl.lmax, 1024, 0, st>>>(mk, fprob, nfmm, nf_cap, lev_off));
+    PROF_LAUNCH("fmm_plan", st, k_fmm_levoff<<<pl.lmax, 1024, 0, st>>>(mk, fprob, nfmm, nf_cap, lev_off,
+                                                                   top_off));
     SDC_CHECK(cudaGetLastError());
     pl.on = true;
     return SUPERDC_OK;
