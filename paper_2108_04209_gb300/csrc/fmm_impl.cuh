@@ -130,18 +130,19 @@ __device__ __forceinline__ int near_box(const FmmDev &pl, int64_t g, int nn, int
 
 // Chebyshev nodes x_q = cos((2q+1) pi / 2P) and T_n(x_q) (Tx[q * P + n], by
 // the three-term recurrence, one row per thread); the caller synchronises
-// before the first use
-__device__ __forceinline__ void cheb_tables(double *xq, double *Tx)
+// before the first use.  sc scales the entries n >= 1 (2: the weights of the
+// moments -> node weights sums, exact, saving a multiply per term)
+__device__ __forceinline__ void cheb_tables(double *xq, double *Tx, double sc = 1.0)
 {
     for (int q = threadIdx.x; q < P; q += blockDim.x) {
         const double x = cospi((double)(2 * q + 1) / (2.0 * P));
         xq[q] = x;
         double t0 = 1.0, t1 = x;
         Tx[q * P] = 1.0;
-        Tx[q * P + 1] = x;
+        Tx[q * P + 1] = sc * x;
         for (int n = 2; n < P; n++) {
             const double t2 = 2.0 * x * t1 - t0;
-            Tx[q * P + n] = t2;
+            Tx[q * P + n] = sc * t2;
             t0 = t1; t1 = t2;
         }
     }
@@ -449,7 +450,7 @@ __device__ __forceinline__ void leaf_moments(const FmmDev &pl, const SrcArgs &a,
     for (int t = tid; t < P * nw; t += blockDim.x) {
         const int qn = t / nw, q = t % nw;
         double s = Ms[0][q];
-        for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
+        for (int n = 1; n < P; n++) s = fma(Tx[qn * P + n], Ms[n][q], s);     // Tx holds 2 T_n
         pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
     }
     // Chebyshev recurrence per source, moments, moments -> node weights
@@ -574,7 +575,7 @@ __device__ __forceinline__ void m2m_box(const FmmDev &pl, int64_t p, int nb0, in
     for (int t = tid; t < P * nw; t += blockDim.x) {
         const int qn = t / nw, q = t % nw;
         double s = Ms[0][q];
-        for (int n = 1; n < P; n++) s = fma(2.0 * Tx[qn * P + n], Ms[n][q], s);
+        for (int n = 1; n < P; n++) s = fma(Tx[qn * P + n], Ms[n][q], s);     // Tx holds 2 T_n
         pl.W[(g * P + qn) * pl.ncol + q] = s * (1.0 / P);
     }
     // children's node positions, the children's weights into moments, moments -> weights
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(up_threads<MODE>()) k_fmm_up(FmmDev pl, SrcArg
     __shared__ double Tx[P * P], xq[P];
     __shared__ int last;
     __shared__ int64_t next;
-    cheb_tables(xq, Tx);
+    cheb_tables(xq, Tx, 2.0);          // 2 T_n(x_q), n >= 1: the moments -> weights sums
     const int nw = (MODE == M_CT || MODE == M_CN) ? a.nc : 1;
     const int tid = threadIdx.x;
     const int64_t nleaf = pl.leaf_base[pl.nprob];
@@ -1729,10 +1730,10 @@ k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
             for (int q = 0; q < NC; q++) sx[q][tid] = 0.0;
         }
         __syncthreads();
-        if (tid < nc) {
+        for (int q = tid; q < nc; q += B) {
             double t = 0.0;
-            for (int i = 0; i < B; i++) t += sx[tid][i];
-            pl.lastp[gl * pl.ncol + tid] = t;
+            for (int i = 0; i < B; i++) t += sx[q][i];
+            pl.lastp[gl * pl.ncol + q] = t;
         }
         // near terms (difference, reciprocal, one FMA per column), Clenshaw
         // and the scale by b per column, the last row's share per source
@@ -1825,11 +1826,12 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
 
 unsigned fmm_grid() { return (unsigned)(sdc_num_sms() * 8); }
 
-// Grid of the upward pass: as many CTAs as the GPU holds at once (every CTA
-// strides over the same number of leaf boxes, so a second partial wave would
-// double the launch), from the occupancy calculator, once per device.
-template <int MODE>
-unsigned up_grid()
+// As many CTAs of kernel K as the GPU holds at once (threads per CTA, static
+// shared memory only), from the occupancy calculator, once per device: the
+// grid of kernels whose CTAs take equal shares of the work (a second, partial
+// wave would double the launch).
+template <auto K>
+unsigned resident_grid(int threads)
 {
     static std::mutex mu;
     static int per_sm[64] = {0};
@@ -1838,12 +1840,14 @@ unsigned up_grid()
     std::lock_guard<std::mutex> lk(mu);
     if (per_sm[dev] == 0) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_fmm_up<MODE>, up_threads<MODE>(), 0) != cudaSuccess)
-            v = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, K, threads, 0) != cudaSuccess) v = 1;
         per_sm[dev] = v > 0 ? v : 1;
     }
     return (unsigned)(sdc_num_sms() * per_sm[dev]);
 }
+
+template <int MODE>
+unsigned up_grid() { return resident_grid<k_fmm_up<MODE>>(up_threads<MODE>()); }
 
 // one warp per (FMM problem, column) of k_fmm_lastsum, 4 warps per CTA
 unsigned lastsum_grid(const FmmPlan &pl, int nc)
@@ -1873,33 +1877,37 @@ SrcArgs src_from_r1(const int64_t *off, const R1Out &o)
 template <int MODE, int KER>
 superdc_status far_field(const FmmPlan &pl, const SrcArgs &a, int nw, int kmode, cudaStream_t st)
 {
+    const FmmDev &dv = pl.dv;
     const unsigned g = fmm_grid();
     const int nf = (KER == K_SEC) ? 4 : nw;
-    PROF_LAUNCH("fmm_up", st, k_fmm_up<MODE><<<up_grid<MODE>(), up_threads<MODE>(), 0, st>>>(pl.dv, a));
-    PROF_LAUNCH("fmm_m2l", st, k_fmm_m2l<KER><<<g, 128, 0, st>>>(pl.dv, a.mk, nw,
-                                                                  pl.dv.kslots > 0 ? kmode : 0));
+    PROF_LAUNCH("fmm_up", st, k_fmm_up<MODE><<<up_grid<MODE>(), up_threads<MODE>(), 0, st>>>(dv, a));
+    PROF_LAUNCH("fmm_m2l", st, k_fmm_m2l<KER><<<g, 128, 0, st>>>(dv, a.mk, nw, dv.kslots > 0 ? kmode : 0));
     if (nf <= NARROW_NF) {
         for (int t0 = 1; t0 < pl.lmax; t0 += DOWN_LEVELS)
-            PROF_LAUNCH("fmm_l2l", st, k_fmm_down<true><<<down_grid(pl, t0), 128, 0, st>>>(pl.dv, a.mk, t0, nf));
+            PROF_LAUNCH("fmm_l2l", st, k_fmm_down<true><<<down_grid(pl, t0), 128, 0, st>>>(dv, a.mk, t0, nf));
     } else {
         for (int t0 = 1; t0 < pl.lmax; t0++)
-            PROF_LAUNCH("fmm_l2l", st, k_fmm_down<false><<<down_grid(pl, t0), 128, 0, st>>>(pl.dv, a.mk, t0, nf));
+            PROF_LAUNCH("fmm_l2l", st, k_fmm_down<false><<<down_grid(pl, t0), 128, 0, st>>>(dv, a.mk, t0, nf));
     }
     return SUPERDC_OK;
 }
 
+// grids: 8 CTAs per SM, or what fits when the column count's accumulators
+// leave room for fewer
 template <int NC>
 void launch_ct(const FmmPlan &pl, const FactorView &f, const double *X, int64_t ldx, double *Y, int64_t ldy, int col0,
                int nc, cudaStream_t st)
 {
-    k_cauchyT_fmm<NC><<<fmm_grid(), B, 0, st>>>(pl.dv, f, X, ldx, Y, ldy, col0, nc);
+    const unsigned g = std::min(fmm_grid(), resident_grid<k_cauchyT_fmm<NC>>(B));
+    k_cauchyT_fmm<NC><<<g, B, 0, st>>>(pl.dv, f, X, ldx, Y, ldy, col0, nc);
 }
 
 template <int NC>
 void launch_cn(const FmmPlan &pl, const FactorView &f, const double *X, int64_t ldx, double *Y, int64_t ldy, int col0,
                int nc, cudaStream_t st)
 {
-    k_cauchyN_fmm<NC><<<fmm_grid(), B, 0, st>>>(pl.dv, f, X, ldx, Y, ldy, col0, nc);
+    const unsigned g = std::min(fmm_grid(), resident_grid<k_cauchyN_fmm<NC>>(B));
+    k_cauchyN_fmm<NC><<<g, B, 0, st>>>(pl.dv, f, X, ldx, Y, ldy, col0, nc);
 }
 
 }  // namespace
