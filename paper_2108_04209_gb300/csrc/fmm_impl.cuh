@@ -267,13 +267,13 @@ __device__ __forceinline__ int64_t cta_exscan(int64_t v, int64_t *sh)
     return before + x - v;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
 k_fmm_tree(int64_t nprob, const int64_t *__restrict__ off, const int32_t *__restrict__ mk,
            const double *__restrict__ dk, const int64_t *__restrict__ box_base, int32_t *__restrict__ fslot,
            double *__restrict__ blo, double *__restrict__ bhi, int32_t *__restrict__ nnear,
            int64_t *__restrict__ nstart, int32_t *__restrict__ near, int32_t *__restrict__ used)
 {
-    __shared__ int64_t wsum[8];
+    __shared__ int64_t wsum[32];
     __shared__ int64_t s_pos;
     const int T = blockDim.x;
     for (int64_t p = blockIdx.x; p < nprob; p += gridDim.x) {
@@ -1986,8 +1986,11 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     d.blo = blo; d.bhi = bhi; d.nnear = nnear; d.near = near; d.nstart = nstart;
     PROF_LAUNCH("fmm_plan", st, k_fmm_plan<<<1, 1024, 0, st>>>(nprob, mk, min_m, pl.cap_boxes, pl.cap_leaves,
                                                                pl.cap_f, box_base, leaf_base, fslot, fprob, nfmm));
+    // one CTA per problem; a batch of fewer problems than SMs (the top tree
+    // levels) gives each tree 1024 threads instead of 256
     const unsigned gt = (unsigned)std::min<int64_t>(nprob, (int64_t)sdc_num_sms() * 4);
-    PROF_LAUNCH("fmm_tree", st, k_fmm_tree<<<gt, 256, 0, st>>>(nprob, off, mk, dk, box_base, fslot, blo, bhi,
+    const int tt = (nprob < sdc_num_sms()) ? 1024 : 256;
+    PROF_LAUNCH("fmm_tree", st, k_fmm_tree<<<gt, tt, 0, st>>>(nprob, off, mk, dk, box_base, fslot, blo, bhi,
                                                                nnear, nstart, near, used));
     PROF_LAUNCH("fmm_plan", st, k_fmm_levoff<<<pl.lmax, 1024, 0, st>>>(mk, fprob, nfmm, nf_cap, lev_off,
                                                                    top_off));
