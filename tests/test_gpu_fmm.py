@@ -64,8 +64,11 @@ def test_fmm_secular_vs_oracle():
 
 def test_fmm_results_are_reproducible():
     """The tail pass takes straggler roots in whatever order its warps claim
-    them; every root's arithmetic is independent of that order, so two runs
-    agree bit for bit."""
+    them, and the upward pass computes each parent box in whichever CTA
+    finishes its second child last (leaf boxes claimed from a queue); every
+    root's and every box's arithmetic is independent of that order, so two
+    runs agree bit for bit (three far fields per plan, so the arrival counters
+    and the queue reset themselves between launches)."""
     b = fmm_batch()
     o1 = run_batch(b, 1e-12, fmm_min_m=FMM_ON)
     o2 = run_batch(b, 1e-12, fmm_min_m=FMM_ON)
