@@ -434,12 +434,17 @@ __device__ __forceinline__ int ql_sweep_tri(double *a, double *b, int l, int h, 
     return q;
 }
 
-// Implicit QL on the tridiagonal (d, e) of every leaf, one lane per leaf; d
-// and e staged in shared memory ([index][lane]).  Sweep t of leaf L records
-// its first column and count in hdr[L * caps + t] and its rotations (c, s) in
-// rot[L * cap + ...] (rotation q of the sweep acts on columns (first - q,
-// first - q + 1)).  A leaf whose iterations or records exceed the caps latches
-// SUPERDC_DEV_NOCONV.
+// Implicit QL on the tridiagonal (d, e) of every leaf, one lane per leaf and
+// LPW leaves per warp (lanes LPW.. idle); d and e staged in shared memory
+// ([index][lane]).  A chain of dependent FP64 steps advances at the pipe's
+// latency whatever the number of lanes that share it, so a batch of fewer
+// leaves than the GPU has warp schedulers spreads them thin (LPW = 2 puts the
+// 1024 leaves of n = 131072 on 512 warps instead of 32).  Sweep t of leaf L
+// records its first column and count in hdr[L * caps + t] and its rotations
+// (c, s) in rot[L * cap + ...] (rotation q of the sweep acts on columns
+// (first - q, first - q + 1)).  A leaf whose iterations or records exceed the
+// caps latches SUPERDC_DEV_NOCONV.
+template <int LPW>
 __global__ void __launch_bounds__(32)
 k_leaf_ql(int nleaves, int mmax, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ leaf_m,
           double *__restrict__ dd, const double *__restrict__ ein, double2 *__restrict__ rot, int2 *__restrict__ hdr,
@@ -447,12 +452,13 @@ k_leaf_ql(int nleaves, int mmax, const int64_t *__restrict__ leaf_off, const int
 {
     extern __shared__ double sq[];
     const int lane = threadIdx.x;
-    const int L = blockIdx.x * 32 + lane;
-    double *sd = sq, *se = sq + (size_t)mmax * 32;
+    if (lane >= LPW) return;
+    const int L = blockIdx.x * LPW + lane;
+    double *sd = sq, *se = sq + (size_t)mmax * LPW;
     const bool act = L < nleaves;
     const int m = act ? (int)leaf_m[L] : 0;
     const int64_t o = act ? leaf_off[L] : 0;
-    for (int i = 0; i < m; i++) { sd[i * 32 + lane] = dd[o + i]; se[i * 32 + lane] = ein[o + i]; }
+    for (int i = 0; i < m; i++) { sd[i * LPW + lane] = dd[o + i]; se[i * LPW + lane] = ein[o + i]; }
     int64_t nrot = 0;
     int nsweep = 0;
     bool bad = false;
@@ -462,13 +468,13 @@ k_leaf_ql(int nleaves, int mmax, const int64_t *__restrict__ leaf_off, const int
         for (int iter = 0;; iter++) {
             int mm = l;
             for (; mm < m - 1; mm++) {
-                const double s2 = fabs(sd[mm * 32 + lane]) + fabs(sd[(mm + 1) * 32 + lane]);
-                if (fabs(se[mm * 32 + lane]) <= SDC_EPS * s2) break;
+                const double s2 = fabs(sd[mm * LPW + lane]) + fabs(sd[(mm + 1) * LPW + lane]);
+                if (fabs(se[mm * LPW + lane]) <= SDC_EPS * s2) break;
             }
             if (mm == l) break;
             if (iter >= 64 || nsweep >= caps || nrot + (mm - l) > cap) { bad = true; break; }
             double2 *Rs = R + nrot;
-            const int cnt = ql_sweep_tri<32>(sd + lane, se + lane, l, mm,
+            const int cnt = ql_sweep_tri<LPW>(sd + lane, se + lane, l, mm,
                                              [&](int q, double c, double s) { Rs[q] = make_double2(c, s); });
             Hd[nsweep] = make_int2(mm - 1, cnt);
             nsweep++;
@@ -477,7 +483,7 @@ k_leaf_ql(int nleaves, int mmax, const int64_t *__restrict__ leaf_off, const int
     }
     if (act) {
         nsw[L] = nsweep;
-        for (int i = 0; i < m; i++) dd[o + i] = sd[i * 32 + lane];
+        for (int i = 0; i < m; i++) dd[o + i] = sd[i * LPW + lane];
         if (bad) sdc_latch(status, SUPERDC_DEV_NOCONV);
     }
 }
@@ -1125,7 +1131,7 @@ cudaError_t leaf_attrs()
     const size_t mm = 128, rmax = 32;
     const struct { const void *fn; size_t bytes; } at[] = {
         {(const void *)k_leaf_tri, (mm * (mm | 1) + std::max(mm * rmax, mm)) * sizeof(double)},
-        {(const void *)k_leaf_ql, 2 * mm * 32 * sizeof(double)},
+        {(const void *)k_leaf_ql<32>, 2 * mm * 32 * sizeof(double)},
         {(const void *)k_leaf_out, mm * (mm | 1) * sizeof(double)},
         {(const void *)k_leaf_qlcta, (mm * (mm | 1) + 4 * mm) * sizeof(double)}};
     for (const auto &a : at) {
@@ -1224,6 +1230,9 @@ superdc_status superdc_eig_plan(const superdc_hss *h, const superdc_opts *opts, 
     w.leaf_batched = mm >= 96;
     w.smem1 = (mm * (mm | 1) + std::max(mm * (size_t)r, mm)) * sizeof(double);
     w.smem2 = 2 * mm * 32 * sizeof(double);
+    // leaves per warp of the QL chase: about one warp per scheduler (4 per SM)
+    w.ql_lpw = 1;
+    while (w.ql_lpw < 32 && (int64_t)w.ql_lpw * 4 * sdc_num_sms() < h->nleaves) w.ql_lpw *= 2;
     w.smem3 = mm * (mm | 1) * sizeof(double);
     w.smem4 = (mm * (mm | 1) + 4 * mm) * sizeof(double);
     w.smem5 = (size_t)LEAF_R * (mm | 1) * sizeof(double);
@@ -1279,9 +1288,16 @@ superdc_status superdc_eig_run(superdc_eigfact *f, cudaStream_t st, double *lamb
             r, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H, f->Qleaf,
             f->d_qoff, w.dq, w.eq));
         if (w.leaf_batched) {
-            PROF_LAUNCH("leaf", st, k_leaf_ql<<<(unsigned)((h->nleaves + 31) / 32), 32, w.smem2, st>>>(
-                h->nleaves, mm, h->d_leaf_off, h->d_leaf_m, w.dq, w.eq, w.rot, w.hdr, w.nsw, w.cap, (int)w.caps,
-                f->status));
+            const int lpw = w.ql_lpw;
+            const unsigned gq = (unsigned)((h->nleaves + lpw - 1) / lpw);
+            const size_t sq = 2 * (size_t)mm * lpw * sizeof(double);
+#define SDC_QL(W) \
+            if (lpw == W) \
+                PROF_LAUNCH("leaf", st, k_leaf_ql<W><<<gq, 32, sq, st>>>(h->nleaves, mm, h->d_leaf_off, h->d_leaf_m, \
+                                                                        w.dq, w.eq, w.rot, w.hdr, w.nsw, w.cap, \
+                                                                        (int)w.caps, f->status));
+            SDC_QL(1) SDC_QL(2) SDC_QL(4) SDC_QL(8) SDC_QL(16) SDC_QL(32)
+#undef SDC_QL
             PROF_LAUNCH("leaf", st, k_leaf_rot<<<dim3((unsigned)h->nleaves, (unsigned)((mm + LEAF_R - 1) / LEAF_R)),
                                                  LEAF_R, w.smem5, st>>>(h->d_leaf_m, f->Qleaf, f->d_qoff, w.rot, w.hdr,
                                                                         w.nsw, w.cap, (int)w.caps));

@@ -49,6 +49,7 @@ struct EigWork {
     int2 *hdr = nullptr;
     bool leaf_batched = false;
     size_t smem1 = 0, smem2 = 0, smem3 = 0, smem4 = 0, smem5 = 0;
+    int ql_lpw = 32;                       // leaves per warp of the batched QL chase
     int64_t cap = 0, caps = 0;
 };
 
