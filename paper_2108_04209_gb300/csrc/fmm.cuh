@@ -48,6 +48,8 @@ struct FmmDev {
     int32_t *upcnt;                        // per box: children whose moments are done in the current
                                            // upward pass (the last one computes the box; reset by it)
     unsigned long long *upq;               // upward pass: next unclaimed leaf box, CTAs past the end
+    int64_t *split;                        // leaf boxes with long near lists (any order) and their
+    int32_t *nsplit;                       // count, filled by the tree build
     int64_t cap_f;                         // capacity of the FMM problem list
     int ncol, nfield;                      // workspace widths
     unsigned long long *flops;             // algorithmic FP64 work of the far fields and of the

@@ -271,7 +271,8 @@ __global__ void __launch_bounds__(1024)
 k_fmm_tree(int64_t nprob, const int64_t *__restrict__ off, const int32_t *__restrict__ mk,
            const double *__restrict__ dk, const int64_t *__restrict__ box_base, int32_t *__restrict__ fslot,
            double *__restrict__ blo, double *__restrict__ bhi, int32_t *__restrict__ nnear,
-           int64_t *__restrict__ nstart, int32_t *__restrict__ near, int32_t *__restrict__ used)
+           int64_t *__restrict__ nstart, int32_t *__restrict__ near, int32_t *__restrict__ used,
+           const int64_t *__restrict__ leaf_base, int64_t *__restrict__ split, int32_t *__restrict__ nsplit)
 {
     __shared__ int64_t wsum[32];
     __shared__ int64_t s_pos;
@@ -341,6 +342,9 @@ k_fmm_tree(int64_t nprob, const int64_t *__restrict__ off, const int32_t *__rest
                     }
                 }
                 nnear[gb + b] = cnt;
+                // leaf boxes with long near lists, for k_secular_fmm_split (in
+                // any order: each box's sweeps are independent of the others)
+                if (l == 0 && (cnt < 0 || cnt >= SPLIT_NEAR)) split[atomicAdd(nsplit, 1)] = leaf_base[p] + b;
             }
             __syncthreads();
             if (threadIdx.x == T - 1) s_pos = pos;
@@ -1234,8 +1238,9 @@ k_secular_fmm_split(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double 
     __shared__ double red[SPW][4][32];
     const unsigned FULL = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nleaf = pl.leaf_base[pl.nprob];
-    for (int64_t gl = blockIdx.x; gl < nleaf; gl += gridDim.x) {
+    const int nsplit = *pl.nsplit;
+    for (int u = blockIdx.x; u < nsplit; u += gridDim.x) {
+        const int64_t gl = pl.split[u];                  // a leaf box with a long near list
         const int64_t p = sdc_upper_index(pl.leaf_base, pl.nprob, gl);
         if (pl.fslot[p] < 0) continue;
         const int64_t b0 = off[p];
@@ -1243,7 +1248,6 @@ k_secular_fmm_split(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double 
         const int Tb = (int)(gl - pl.leaf_base[p]);
         const int64_t g = pl.box_base[p] + Tb;
         const int nnr = pl.nnear[g];
-        if (nnr >= 0 && nnr < SPLIT_NEAR) continue;     // short list: k_secular_fmm
         const int nn = near_len(nnr, (m + B - 1) / B);
         const int k0b = Tb * B;
         const int kendb = min(k0b + B, m - 1);
@@ -1976,6 +1980,8 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     SDC_CHECK(al(&d.upcnt, pl.cap_boxes));
     SDC_CHECK(cudaMemsetAsync(d.upcnt, 0, (size_t)pl.cap_boxes * sizeof(int32_t), st));
     SDC_CHECK(al(&d.upq, 2));
+    SDC_CHECK(al(&d.split, pl.cap_leaves));
+    SDC_CHECK(al(&d.nsplit, 1));
     SDC_CHECK(cudaMemsetAsync(d.upq, 0, 2 * sizeof(unsigned long long), st));
     d.lev_off = lev_off;
     d.top_off = top_off;
@@ -1990,8 +1996,10 @@ superdc_status plan(FmmPlan &pl, int64_t nprob, const int64_t *off, int64_t tota
     // levels) gives each tree 1024 threads instead of 256
     const unsigned gt = (unsigned)std::min<int64_t>(nprob, (int64_t)sdc_num_sms() * 4);
     const int tt = (nprob < sdc_num_sms()) ? 1024 : 256;
+    SDC_CHECK(cudaMemsetAsync(d.nsplit, 0, sizeof(int32_t), st));
     PROF_LAUNCH("fmm_tree", st, k_fmm_tree<<<gt, tt, 0, st>>>(nprob, off, mk, dk, box_base, fslot, blo, bhi,
-                                                               nnear, nstart, near, used));
+                                                               nnear, nstart, near, used, leaf_base, d.split,
+                                                               d.nsplit));
     PROF_LAUNCH("fmm_plan", st, k_fmm_levoff<<<pl.lmax, 1024, 0, st>>>(mk, fprob, nfmm, nf_cap, lev_off,
                                                                    top_off));
     SDC_CHECK(cudaGetLastError());
