@@ -2,6 +2,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cuda_runtime.h>
+#include <mutex>
+#include <vector>
 #include "common.cuh"
 #include "rank1.cuh"
 #include "fmm.cuh"
@@ -27,6 +29,72 @@ int sdc_num_sms()
         cached[dev] = n;
     }
     return cached[dev];
+}
+
+// the batched step's arguments from the public options (device arrays)
+static R1Args r1args(int64_t nprob, const int64_t *offsets, int64_t total, const double *d, const double *z,
+                     double rho, const superdc_opts *opts)
+{
+    R1Args a;
+    a.nprob = nprob;
+    a.total = total;
+    a.off = offsets;
+    a.d = d;
+    a.z = z;
+    a.sqrt_rho = sqrt(rho);
+    a.tau = opts->tau;
+    a.stop_c = opts->stop_c;
+    a.max_iter = opts->max_iter;
+    a.tile_roots = opts->tile_roots;
+    a.sched = opts->sched;
+    a.fmm_min_m = fmm_resolve(opts->fmm_min_m);
+    a.o.unshifted = opts->shifted ? 0 : 1;
+    return a;
+}
+
+// two non-blocking streams of the library on the current device (created on
+// first use), for the host-buffer entry point's copy/compute pipeline
+static cudaError_t sdc_side_streams(cudaStream_t *s2)
+{
+    static std::mutex mu;
+    static cudaStream_t ss[64][2] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    for (int k = 0; k < 2; k++)
+        if (!ss[dev][k] && (e = cudaStreamCreateWithFlags(&ss[dev][k], cudaStreamNonBlocking)) != cudaSuccess) return e;
+    s2[0] = ss[dev][0];
+    s2[1] = ss[dev][1];
+    return cudaSuccess;
+}
+
+cudaMemPool_t sdc_pool()
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    static bool tried[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tried[dev]) {
+        tried[dev] = true;
+        cudaMemPoolProps pp = {};
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.handleTypes = cudaMemHandleTypeNone;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &pp) == cudaSuccess) {
+            unsigned long long keep = SDC_POOL_KEEP;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools[dev] = pool;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return pools[dev];
 }
 
 extern "C" {
@@ -89,24 +157,11 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
         !out->src || !out->perm || !out->giv_ab || !out->giv_cs || !out->mk || !out->ngiv ||
         !out->status)
         return SUPERDC_ERR_ARG;
-    R1Args a;
-    a.nprob = nprob;
-    a.total = total;
-    a.off = offsets;
-    a.d = d;
-    a.z = z;
-    a.sqrt_rho = sqrt(rho);
-    a.tau = opts->tau;
-    a.stop_c = opts->stop_c;
-    a.max_iter = opts->max_iter;
-    a.tile_roots = opts->tile_roots;
-    a.sched = opts->sched;
-    a.fmm_min_m = fmm_resolve(opts->fmm_min_m);
+    R1Args a = r1args(nprob, offsets, total, d, z, rho, opts);
     a.o.lam = out->lam; a.o.dk = out->dk; a.o.zk = out->zk; a.o.eta = out->eta;
     a.o.vhat = out->vhat; a.o.bnorm = out->bnorm; a.o.org = out->org; a.o.src = out->src;
     a.o.perm = out->perm; a.o.giv_ab = out->giv_ab; a.o.giv_cs = out->giv_cs; a.o.mk = out->mk;
     a.o.ngiv = out->ngiv; a.o.sweeps = out->sweeps; a.o.status = out->status; a.o.fmm_used = out->fmm;
-    a.o.unshifted = opts->shifted ? 0 : 1;
     SdcScratch sc(stream);
     SDC_CHECK(sc.get(&a.o.dorg, total));
     SDC_CHECK(sc.get(&a.o.wsum, nprob));
@@ -125,9 +180,13 @@ superdc_status superdc_secular_batched_host(int64_t nprob, const int64_t *offset
     if (nprob == 0) { *out->status = 0; return SUPERDC_OK; }
     if (!offsets || !d || !z || total > INT32_MAX) return SUPERDC_ERR_ARG;
     if (offsets[0] != 0 || offsets[nprob] != total) return SUPERDC_ERR_ARG;
+    for (int64_t p = 0; p < nprob; p++)
+        if (offsets[p + 1] < offsets[p]) return SUPERDC_ERR_ARG;
     const size_t T = (size_t)std::max<int64_t>(total, 1), NP = (size_t)nprob;
-    // one device slab: inputs, every output, status (8-byte fields first)
-    const size_t n8 = (NP + 1) + 3 * T + 6 * T + 2 * T, n4 = 3 * T + 2 * T + 2 * NP + T + 1 + NP;
+    // one device slab: offsets, inputs, every output, the step's per-row and
+    // per-problem scratch, status (8-byte fields first)
+    const size_t n8 = (NP + 1) + 2 * T + 6 * T + 2 * T + T + NP;
+    const size_t n4 = 3 * T + 2 * T + 2 * NP + T + 1 + NP + T;
     char *slab = nullptr;
     SDC_CHECK(sdc_alloc(&slab, n8 * 8 + n4 * 4, stream));
     int64_t *doff = (int64_t *)slab;
@@ -135,28 +194,76 @@ superdc_status superdc_secular_batched_host(int64_t nprob, const int64_t *offset
     superdc_rank1_out o;
     o.lam = dz + T; o.dk = o.lam + T; o.zk = o.dk + T; o.eta = o.zk + T; o.vhat = o.eta + T; o.bnorm = o.vhat + T;
     o.giv_cs = o.bnorm + T;
-    int32_t *ip = (int32_t *)(o.giv_cs + 2 * T);
+    double *dorg = o.giv_cs + 2 * T, *wsum = dorg + T;
+    int32_t *ip = (int32_t *)(wsum + NP);
     o.org = ip; o.src = o.org + T; o.perm = o.src + T; o.giv_ab = o.perm + T; o.mk = o.giv_ab + 2 * T;
     o.ngiv = o.mk + NP; o.sweeps = o.ngiv + NP; o.status = o.sweeps + T; o.fmm = o.status + 1;
+    int32_t *pinv = o.fmm + NP;
+    // chunks of about equal root counts at problem boundaries, on two streams:
+    // one chunk's copies overlap another's kernels.  Rows stay absolute and the
+    // schedule is that of the whole batch, so every problem's arithmetic (and
+    // result) is the same as in one call over the batch.
+    const int nch = (total >= (1 << 20) && nprob >= 16) ? 4 : 1;
+    std::vector<int64_t> cut(nch + 1, nprob);
+    cut[0] = 0;
+    for (int c = 1; c < nch; c++)
+        cut[c] = std::lower_bound(offsets, offsets + nprob + 1, (total * c) / nch) - offsets;
+    cudaStream_t side[2] = {stream, stream};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     cudaError_t e = cudaMemcpyAsync(doff, offsets, (NP + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, d, (size_t)total * sizeof(double), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dz, z, (size_t)total * sizeof(double), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(o.status, 0, sizeof(int32_t), stream);
-    superdc_status st = (e == cudaSuccess)
-        ? superdc_secular_batched(nprob, doff, total, dd, dz, rho, opts, &o, stream) : SUPERDC_ERR_CUDA;
-    // results back to the caller's host arrays (NULL fields are skipped)
-    struct Cp { void *h; const void *dv; size_t bytes; };
-    const Cp cps[] = {
-        {out->lam, o.lam, T * 8}, {out->dk, o.dk, T * 8}, {out->zk, o.zk, T * 8}, {out->eta, o.eta, T * 8},
-        {out->vhat, o.vhat, T * 8}, {out->bnorm, o.bnorm, T * 8}, {out->giv_cs, o.giv_cs, 2 * T * 8},
-        {out->org, o.org, T * 4}, {out->src, o.src, T * 4}, {out->perm, o.perm, T * 4},
-        {out->giv_ab, o.giv_ab, 2 * T * 4}, {out->mk, o.mk, NP * 4}, {out->ngiv, o.ngiv, NP * 4},
-        {out->sweeps, o.sweeps, T * 4}, {out->fmm, o.fmm, NP * 4}, {out->status, o.status, 4}};
-    if (st == SUPERDC_OK)
-        for (const Cp &c : cps)
-            if (c.h && e == cudaSuccess) e = cudaMemcpyAsync(c.h, c.dv, c.bytes, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && nch > 1) {
+        e = sdc_side_streams(side);
+        for (int k = 0; k < 3 && e == cudaSuccess; k++) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], stream);
+        for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaStreamWaitEvent(side[k], ev[0], 0);
+    }
+    superdc_status st = (e == cudaSuccess) ? SUPERDC_OK : SUPERDC_ERR_CUDA;
+    for (int c = 0; c < nch && st == SUPERDC_OK; c++) {
+        const int64_t p0 = cut[c], p1 = cut[c + 1];
+        if (p1 <= p0) continue;
+        cudaStream_t sc = side[c & 1];
+        const int64_t o0 = offsets[p0], o1 = offsets[p1];
+        const size_t nr = (size_t)(o1 - o0), npc = (size_t)(p1 - p0);
+        e = cudaMemcpyAsync(dd + o0, d + o0, nr * sizeof(double), cudaMemcpyHostToDevice, sc);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dz + o0, z + o0, nr * sizeof(double), cudaMemcpyHostToDevice, sc);
+        if (e != cudaSuccess) { st = SUPERDC_ERR_CUDA; break; }
+        R1Args a = r1args(p1 - p0, doff + p0, total, dd, dz, rho, opts);
+        a.rows = total;
+        a.o.lam = o.lam; a.o.dk = o.dk; a.o.zk = o.zk; a.o.eta = o.eta; a.o.vhat = o.vhat; a.o.bnorm = o.bnorm;
+        a.o.org = o.org; a.o.src = o.src; a.o.perm = o.perm; a.o.giv_ab = o.giv_ab; a.o.giv_cs = o.giv_cs;
+        a.o.mk = o.mk + p0; a.o.ngiv = o.ngiv + p0; a.o.sweeps = o.sweeps; a.o.status = o.status;
+        a.o.fmm_used = o.fmm + p0; a.o.dorg = dorg; a.o.wsum = wsum + p0; a.o.pinv = pinv;
+        st = r1_run(a, sc);
+        if (st != SUPERDC_OK) break;
+        // this chunk's results to the caller's host arrays (NULL fields are skipped)
+        struct Cp { void *h; const void *dv; size_t bytes; };
+        const Cp cps[] = {
+            {out->lam, o.lam, 8}, {out->dk, o.dk, 8}, {out->zk, o.zk, 8}, {out->eta, o.eta, 8},
+            {out->vhat, o.vhat, 8}, {out->bnorm, o.bnorm, 8}, {out->giv_cs, o.giv_cs, 16},
+            {out->org, o.org, 4}, {out->src, o.src, 4}, {out->perm, o.perm, 4},
+            {out->giv_ab, o.giv_ab, 8}, {out->sweeps, o.sweeps, 4}};
+        for (const Cp &cp : cps)
+            if (cp.h && e == cudaSuccess)
+                e = cudaMemcpyAsync((char *)cp.h + o0 * cp.bytes, (const char *)cp.dv + o0 * cp.bytes, nr * cp.bytes,
+                                    cudaMemcpyDeviceToHost, sc);
+        const Cp pps[] = {{out->mk, o.mk, 4}, {out->ngiv, o.ngiv, 4}, {out->fmm, o.fmm, 4}};
+        for (const Cp &cp : pps)
+            if (cp.h && e == cudaSuccess)
+                e = cudaMemcpyAsync((char *)cp.h + p0 * cp.bytes, (const char *)cp.dv + p0 * cp.bytes, npc * cp.bytes,
+                                    cudaMemcpyDeviceToHost, sc);
+        if (e != cudaSuccess) st = SUPERDC_ERR_CUDA;
+    }
+    // join the side streams before the status is read and the slab freed
+    if (nch > 1 && ev[1] && ev[2]) {
+        for (int k = 0; k < 2; k++)
+            if (cudaEventRecord(ev[1 + k], side[k]) == cudaSuccess) cudaStreamWaitEvent(stream, ev[1 + k], 0);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->status, o.status, 4, cudaMemcpyDeviceToHost, stream);
     cudaFreeAsync(slab, stream);
     cudaError_t es = cudaStreamSynchronize(stream);
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     if (st != SUPERDC_OK) return st;
     if (e != cudaSuccess || es != cudaSuccess) return SUPERDC_ERR_CUDA;
     const int32_t w = *out->status;

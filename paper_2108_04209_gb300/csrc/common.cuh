@@ -38,12 +38,23 @@ int sdc_num_sms();
 // many bytes must fail as if the device were out of memory.
 bool sdc_alloc_denied(size_t bytes);
 
+// The library's stream-ordered memory pool on the current device (created on
+// first use): freed scratch stays in the pool across synchronisations (up to
+// SDC_POOL_KEEP bytes), so a call after a synchronising one does not map its
+// scratch again (the device's default pool returns everything to the driver
+// at every synchronisation).  NULL if the pool cannot be created (then the
+// default pool serves).
+cudaMemPool_t sdc_pool();
+constexpr unsigned long long SDC_POOL_KEEP = 16ull << 30;
+
 // Stream-ordered scratch allocation helpers.
 template <typename T>
 static inline cudaError_t sdc_alloc(T **p, size_t count, cudaStream_t st)
 {
     if (count == 0) count = 1;
     if (sdc_alloc_denied(count * sizeof(T))) return cudaErrorMemoryAllocation;
+    cudaMemPool_t pool = sdc_pool();
+    if (pool) return cudaMallocFromPoolAsync((void **)p, count * sizeof(T), pool, st);
     return cudaMallocAsync((void **)p, count * sizeof(T), st);
 }
 

@@ -787,7 +787,7 @@ void secular_schedule(int64_t rows, int sched, int tile_roots, int slots, bool *
 
 }  // namespace
 
-cudaError_t r1_prepare() { return units_attr(); }
+cudaError_t r1_prepare() { sdc_pool(); return units_attr(); }
 
 // ---------------------------------------------------------------------------
 // Host launcher
