@@ -161,8 +161,19 @@ superdc_status superdc_secular_batched(int64_t nprob, const int64_t *offsets, in
  * copies the inputs to a stream-ordered device slab, runs the batched step,
  * copies the requested outputs back, releases the slab and synchronises the
  * stream; it returns SUPERDC_ERR_NONFINITE / SUPERDC_ERR_NOCONV when the
- * status word says so.  Argument errors as superdc_secular_batched, plus
- * offsets[0] != 0 or offsets[nprob] != total. */
+ * status word says so.  A batch of 2^20 entries or more (and at least 16
+ * problems) runs as four chunks of problems on two library-owned streams
+ * that wait for the work already queued on `stream`, so that one chunk's
+ * copies overlap another chunk's kernels; every chunk uses the schedule of
+ * the whole batch and absolute rows, so the results are bit-identical to one
+ * superdc_secular_batched call over the batch.  Argument errors as
+ * superdc_secular_batched, plus offsets[0] != 0, offsets[nprob] != total or
+ * decreasing offsets.
+ *
+ * Device scratch of every entry point comes from a stream-ordered memory
+ * pool of the library on each device, which keeps up to 16 GiB of freed
+ * scratch across synchronisations (so a call after a synchronising one does
+ * not map its scratch again); that memory stays reserved by the process. */
 superdc_status superdc_secular_batched_host(int64_t nprob, const int64_t *offsets, int64_t total,
                                             const double *d, const double *z, double rho,
                                             const superdc_opts *opts, superdc_rank1_out *out,
