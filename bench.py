@@ -330,12 +330,43 @@ def eig_headline(dev, peak, peak_src, direct=True, reps=3):
     return out
 
 
+def table1_metrics(n, leaf, nprobe=64):
+    """Table 1's accuracy measures for Example 1 at size n (leaves of
+    ``leaf``): delta = ||lambda - lambda*||_2 / (n ||lambda*||_2) against the
+    closed form 3 - 2 cos(k pi/(n+1)); gamma = max_k ||A q_k - lambda_k q_k||
+    / (n ||A||_2) and theta = max_k ||Q^T q_k - e_k|| / n over nprobe
+    eigenvectors q_k (columns of Q read through superdc_apply_Q at evenly
+    spread k; A q by the tridiagonal stencil)."""
+    import torch
+    import paper_2108_04209_gb300 as sdc
+    from paper_2108_04209_gb300 import inputs
+    H = sdc.HSSMatrix(inputs.hss_tridiag(n, leaf))
+    lam, F = H.eig(sdc.default_opts(tau=1e-10))
+    k = np.arange(1, n + 1)
+    exact = np.sort(3.0 - 2.0 * np.cos(k * np.pi / (n + 1)))
+    ln = lam.cpu().numpy()
+    delta = float(np.linalg.norm(ln - exact) / (n * np.linalg.norm(exact)))
+    idx = np.unique(np.linspace(0, n - 1, nprobe).astype(np.int64))
+    E = torch.zeros((n, len(idx)), dtype=torch.float64, device="cuda")
+    E[torch.from_numpy(idx).cuda(), torch.arange(len(idx), device="cuda")] = 1.0
+    Qk = F.apply_Q(E)
+    AQ = 3.0 * Qk
+    AQ[1:] -= Qk[:-1]
+    AQ[:-1] -= Qk[1:]
+    lk = lam[torch.from_numpy(idx).cuda()]
+    anorm = 3.0 + 2.0 * np.cos(np.pi / (n + 1))
+    gamma = float(torch.linalg.vector_norm(AQ - Qk * lk[None, :], dim=0).max()) / (n * anorm)
+    theta = float(torch.linalg.vector_norm(F.apply_Q(Qk, trans=True) - E, dim=0).max()) / n
+    return {"n": n, "gamma": gamma, "delta": delta, "theta": theta, "probes": int(len(idx))}
+
+
 def example1(dev, n=262144, leaf=2048, reps=3, oracle=True):
     """Section 5, Example 1 at the paper's largest size and leaf size: the
     tridiagonal matrix (3 on the diagonal, -1 off it) in its explicit rank-2
     HSS form with leaves of 2048 (refined by the library into subtrees of
     128-row leaves), tau = 1e-10; every eigenvalue against 3 - 2 cos(k pi/(n+1));
-    beside the paper's 383.4 s (Matlab, 4 cores, same n, leaf and tau)."""
+    beside the paper's 383.4 s (Matlab, 4 cores, same n, leaf and tau); and
+    Table 1's gamma, delta, theta at n = 8192 ... 131072 and n."""
     import torch
     import paper_2108_04209_gb300 as sdc
     from paper_2108_04209_gb300 import inputs
@@ -357,6 +388,8 @@ def example1(dev, n=262144, leaf=2048, reps=3, oracle=True):
            "max_rel_error_vs_closed_form": rel, "deflated": F.stats()["deflated"],
            "paper_s": {"total": 383.4, "dividing": 16.1, "hardware": "Matlab, 4 x 2.6 GHz CPU cores, FP64",
                        "source": "Section 5, Example 1"}}
+    del F, H
+    out["table1"] = [table1_metrics(nn, leaf) for nn in (8192, 16384, 32768, 65536, 131072, n)]
     if oracle:
         from oracle import superdc as osd
         hs = inputs.hss_tridiag(8192, 128)

@@ -11,6 +11,7 @@ from oracle import dense, superdc as osd  # noqa: E402
 from tests import parity as P  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda")
 
 METRIC_TOL = 1e-12    # residual and orthogonality (the paper's gamma, theta)
 
@@ -218,6 +219,36 @@ def test_tridiagonal_leaf2048_refined_closed_form():
     assert rel.max() <= 1e-10
     _, lam128, _ = gpu_eig(inputs.hss_tridiag(n, 128))
     assert np.abs(lam - lam128).max() <= 1e-12
+
+
+def test_table1_metrics_example1_leaf2048():
+    """Table 1's accuracy measures for Example 1 (n = 32768, leaves of 2048,
+    tau = 1e-10): delta against the closed form over every eigenvalue, and
+    gamma = max ||A q_k - lambda_k q_k|| / (n ||A||_2), theta = max ||Q^T q_k -
+    e_k|| / n over 64 eigenvectors read through superdc_apply_Q (A q by the
+    tridiagonal stencil).  The paper prints gamma <= 8.8e-16, delta <= 8.0e-18,
+    theta <= 6.4e-16 for n = 8192 ... 131072; the bounds here are ten times
+    those."""
+    n = 32768
+    H = sdc.HSSMatrix(inputs.hss_tridiag(n, 2048))
+    lam, F = H.eig(sdc.default_opts(tau=1e-10))
+    k = np.arange(1, n + 1)
+    exact = np.sort(3.0 - 2.0 * np.cos(k * np.pi / (n + 1)))
+    ln = lam.cpu().numpy()
+    delta = np.linalg.norm(ln - exact) / (n * np.linalg.norm(exact))
+    idx = np.linspace(0, n - 1, 64).astype(np.int64)
+    E = torch.zeros((n, 64), dtype=torch.float64, device=DEV)
+    E[torch.from_numpy(idx).to(DEV), torch.arange(64, device=DEV)] = 1.0
+    Qk = F.apply_Q(E)
+    AQ = 3.0 * Qk
+    AQ[1:] -= Qk[:-1]
+    AQ[:-1] -= Qk[1:]
+    lk = lam[torch.from_numpy(idx).to(DEV)]
+    anorm = 3.0 + 2.0 * np.cos(np.pi / (n + 1))
+    gamma = float(torch.linalg.vector_norm(AQ - Qk * lk[None, :], dim=0).max()) / (n * anorm)
+    theta = float(torch.linalg.vector_norm(F.apply_Q(Qk, trans=True) - E, dim=0).max()) / n
+    print("Example 1, n=32768, leaf 2048: gamma %.2e delta %.2e theta %.2e" % (gamma, delta, theta))
+    assert gamma <= 8.8e-15 and delta <= 8.0e-17 and theta <= 6.4e-15
 
 
 def test_large_dense_leaf_that_is_not_rank_structured_is_rejected():
