@@ -122,6 +122,76 @@ def perfect_tree(n: int, leaf: int, rank: int) -> Tree:
     return Tree(n, nnodes, lchild, rchild, parent, size, off, level, rank)
 
 
+def perfect_tree_sizes(sizes, rank: int) -> Tree:
+    """Postordered perfect binary tree whose leaves (left to right) have the
+    given row counts (len(sizes) a power of two; sizes may differ)."""
+    sizes = [int(x) for x in sizes]
+    nleaves = len(sizes)
+    assert nleaves >= 1 and nleaves & (nleaves - 1) == 0, "the number of leaves must be a power of two"
+    lmax = nleaves.bit_length() - 1
+    nnodes = 2 * nleaves - 1
+    lchild = -np.ones(nnodes, np.int32)
+    rchild = -np.ones(nnodes, np.int32)
+    parent = -np.ones(nnodes, np.int32)
+    size = np.zeros(nnodes, np.int64)
+    off = np.zeros(nnodes, np.int64)
+    level = np.zeros(nnodes, np.int32)
+    counter = [0]
+    leafpos = [0, 0]                      # leaf index, row offset
+
+    def build(lev):
+        if lev == lmax:
+            i = counter[0]
+            counter[0] += 1
+            size[i] = sizes[leafpos[0]]
+            off[i] = leafpos[1]
+            leafpos[0] += 1
+            leafpos[1] += size[i]
+            level[i] = lev
+            return i
+        a = build(lev + 1)
+        b = build(lev + 1)
+        i = counter[0]
+        counter[0] += 1
+        lchild[i], rchild[i] = a, b
+        parent[a] = parent[b] = i
+        size[i] = size[a] + size[b]
+        off[i] = off[a]
+        level[i] = lev
+        return i
+
+    build(0)
+    return Tree(int(sum(sizes)), nnodes, lchild, rchild, parent, size, off, level, rank)
+
+
+def hss_random_sizes(sizes, rank: int, seed: int) -> HSS:
+    """Random symmetric HSS matrix on a perfect tree with ragged leaf sizes:
+    the recipe of ``hss_random`` (leaf D = (G + G^T)/2; leaf U the Q-factor of
+    an m x r N(0,1) matrix when m >= r, else an m x r N(0,1) matrix scaled by
+    1/sqrt(r); [R_c1; R_c2] the Q-factor of a 2r x r N(0,1) matrix; B = N(0,1)
+    diag(2^-k)), same draw order."""
+    tree = perfect_tree_sizes(sizes, rank)
+    rng = np.random.default_rng(seed)
+    D, U, R, B, d_off, u_off = _alloc(tree)
+    h = HSS(tree, D, U, R, B, d_off, u_off)
+    colscale = 2.0 ** (-np.arange(rank, dtype=np.float64))
+    for i in range(tree.nnodes):
+        m = int(tree.leaf_size[i])
+        if tree.lchild[i] < 0:
+            G = rng.standard_normal((m, m))
+            h.leaf_D(i)[:, :] = 0.5 * (G + G.T)
+            g = rng.standard_normal((m, rank))
+            h.leaf_U(i)[:, :] = _qfactor(g) if m >= rank else g / np.sqrt(rank)
+        else:
+            c1, c2 = int(tree.lchild[i]), int(tree.rchild[i])
+            if i != tree.root:
+                q = _qfactor(rng.standard_normal((2 * rank, rank)))
+                R[c1] = q[:rank]
+                R[c2] = q[rank:]
+            B[c1] = rng.standard_normal((rank, rank)) * colscale[None, :]
+    return h
+
+
 def _alloc(tree: Tree):
     r = tree.rank
     d_off = -np.ones(tree.nnodes, np.int64)

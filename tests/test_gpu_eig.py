@@ -251,6 +251,30 @@ def test_table1_metrics_example1_leaf2048():
     assert gamma <= 8.8e-15 and delta <= 8.0e-17 and theta <= 6.4e-15
 
 
+@pytest.mark.parametrize("sizes,rank", [([1, 7, 128, 33, 2, 64, 100, 5], 4), ([37], 3), ([3, 1], 5),
+                                        ([16] * 7 + [9], 2), ([128] * 3 + [97], 6)])
+def test_ragged_leaves_and_single_leaf_vs_oracle(sizes, rank):
+    """Perfect trees with ragged leaf sizes (1 to 128 rows, leaves smaller
+    than the rank, the batched QL path when a leaf has 96 rows or more, the
+    per-CTA path otherwise), a single-leaf tree (no conquering step) and a
+    two-leaf tree smaller than its rank: every eigenvalue against the oracle
+    (per entry), the dense Q from superdc_apply_Q against the paper's metrics,
+    Q^T = the transposed application."""
+    h = inputs.hss_random_sizes(sizes, rank, seed=3)
+    A = dense.dense_from_hss(h)
+    n = h.tree.n
+    H, lam, F = gpu_eig(h, tau=1e-14)
+    O = osd.superdc(h, tau=1e-14, mode=0)
+    an = np.abs(O.eigenvalues).max()
+    ok, info = P.lam_check(lam, O.eigenvalues, an, max(1, int(h.tree.level.max())) * rank)
+    print("ragged", sizes, info)
+    assert ok, info
+    Q, QT = dense_Q(F, n)
+    assert np.abs(QT - Q.T).max() < 1e-13
+    assert dense.gamma(A, lam, Q) <= 1e-13
+    assert dense.theta(Q) <= 1e-13
+
+
 def test_large_dense_leaf_that_is_not_rank_structured_is_rejected():
     """A random dense leaf block of 256 rows has full off-diagonal rank: its
     refinement at rank 4 is not exact, so superdc_build_hss refuses it."""

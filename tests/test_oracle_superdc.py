@@ -134,3 +134,23 @@ def test_hss_matvec_vs_dense():
         A = dense.dense_from_hss(h)
         X = np.random.default_rng(1).standard_normal((h.tree.n, 3))
         assert np.abs(dense.hss_matvec(h, X) - A @ X).max() < 1e-13 * np.abs(A).max() * 10
+
+
+@pytest.mark.parametrize("sizes,rank", [([1, 7, 128, 33, 2, 64, 100, 5], 4), ([37], 3), ([3, 1], 5),
+                                        ([16] * 7 + [9], 2)])
+def test_ragged_leaves_and_single_leaf_vs_dense(sizes, rank):
+    """Perfect trees with ragged leaf sizes (1 to 128 rows, leaves smaller
+    than the rank), a single-leaf tree and a two-leaf tree whose size is below
+    the rank: eigenvalues against numpy's eigvalsh of the assembled matrix,
+    the dense Q against the paper's metrics."""
+    h = inputs.hss_random_sizes(sizes, rank, seed=3)
+    A = dense.dense_from_hss(h)
+    F = sd.superdc(h, tau=1e-14, mode=0)
+    lam = F.eigenvalues
+    ev = np.linalg.eigvalsh(A)
+    an = np.abs(ev).max()
+    assert np.abs(lam - ev).max() <= 1e-12 * an
+    n = h.tree.n
+    Q = sd.superdcmv(F, h.tree.root, np.eye(n), 0)
+    assert dense.gamma(A, lam, Q) < 1e-14
+    assert dense.theta(Q) < 1e-14
