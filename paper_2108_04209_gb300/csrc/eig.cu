@@ -1133,7 +1133,8 @@ cudaError_t leaf_attrs()
         {(const void *)k_leaf_tri, (mm * (mm | 1) + std::max(mm * rmax, mm)) * sizeof(double)},
         {(const void *)k_leaf_ql<32>, 2 * mm * 32 * sizeof(double)},
         {(const void *)k_leaf_out, mm * (mm | 1) * sizeof(double)},
-        {(const void *)k_leaf_qlcta, (mm * (mm | 1) + 4 * mm) * sizeof(double)}};
+        {(const void *)k_leaf_qlcta, (mm * (mm | 1) + 4 * mm) * sizeof(double)},
+        {(const void *)k_divide, 8 * rmax * rmax * sizeof(double)}};   // 64 KiB at the largest rank
     for (const auto &a : at) {
         e = cudaFuncSetAttribute(a.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.bytes);
         if (e != cudaSuccess) return e;

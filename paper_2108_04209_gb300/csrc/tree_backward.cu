@@ -15,6 +15,7 @@
 //     W = Q^T U and Q^T V, then Dhat = D - U H U^T;
 //   * the dividing stage bottom-up: H_c1 = R_c1 H R_c1^T + B~B~^T/beta,
 //     H_c2 = R_c2 H R_c2^T + beta I, B~ = B_c1 - R_c1 H R_c2^T, d beta = u1^T dB~ v1.
+#include <mutex>
 #include <vector>
 #include <cuda_runtime.h>
 #include "common.cuh"
@@ -311,6 +312,28 @@ __global__ void k_divide_bw(const int32_t *__restrict__ nodes, int root, int r, 
 
 }  // namespace
 
+namespace {
+// dynamic shared memory of k_divide_bw above the 48 KiB default (9 r^2
+// doubles: 72 KiB at the largest rank), once per device
+cudaError_t divide_bw_attr()
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        e = cudaFuncSetAttribute(k_divide_bw, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(9 * 32 * 32 * sizeof(double)));
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
 extern "C" superdc_status superdc_eig_backward(const superdc_hss *h, const superdc_eigfact *f,
                                                const double *lam_bar, int64_t k, const double *V, int64_t ldv,
                                                const double *Ybar, int64_t ldy, double *gD, double *gU,
@@ -325,6 +348,7 @@ extern "C" superdc_status superdc_eig_backward(const superdc_hss *h, const super
     const int nsm = sdc_num_sms();
     const unsigned g = (unsigned)(nsm * 8);
     const Tape &T = f->tape;
+    if (divide_bw_attr() != cudaSuccess) return SUPERDC_ERR_CUDA;
     std::vector<void *> tmp;
     auto alloc = [&](auto **p, size_t cnt) -> cudaError_t {
         cudaError_t e = sdc_alloc(p, cnt, st);

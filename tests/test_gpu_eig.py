@@ -275,6 +275,22 @@ def test_ragged_leaves_and_single_leaf_vs_oracle(sizes, rank):
     assert dense.theta(Q) <= 1e-13
 
 
+def test_maximum_rank_32_vs_oracle():
+    """The largest rank the library accepts (r = 32; n = 1024, leaves of 64):
+    per-entry eigenvalues against the oracle, probes of Q."""
+    h = inputs.hss_random(1024, 64, 32, seed=7)
+    A = dense.dense_from_hss(h)
+    H, lam, F = gpu_eig(h)
+    O = osd.superdc(h, tau=1e-10, mode=0)
+    an = np.abs(O.eigenvalues).max()
+    ok, info = P.lam_check(lam, O.eigenvalues, an, int(h.tree.level.max()) * 32, tau=1e-10,
+                           decisions_differ=True)
+    print("rank 32", info)
+    assert ok, info
+    Q, QT = dense_Q(F, h.tree.n)
+    assert dense.gamma(A, lam, Q) <= 1e-12 and dense.theta(Q) <= 1e-12
+
+
 def test_large_dense_leaf_that_is_not_rank_structured_is_rejected():
     """A random dense leaf block of 256 rows has full off-diagonal rank: its
     refinement at rank 4 is not exact, so superdc_build_hss refuses it."""

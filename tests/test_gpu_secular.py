@@ -40,6 +40,12 @@ def edge_batch():
     probs.append((np.sort(d2), rng.standard_normal(129)))
     for m in (31, 32, 33, 127, 128, 129, 255, 257, 1000, 2048, 2049, 4500):   # tile and chunk edges
         probs.append((np.sort(rng.uniform(-2, 3, m)), rng.standard_normal(m)))
+    # exactly repeated poles (Givens deflation of equal d), small and FMM-sized
+    probs.append((np.array([0.1, 0.2, 0.2, 0.2, 0.5, 0.7, 0.7]), rng.standard_normal(7)))
+    dr = np.sort(rng.uniform(0, 1, 700))
+    dr[200:210] = dr[200]
+    dr[400:403] = dr[400]
+    probs.append((dr, rng.standard_normal(700)))
     offs = np.zeros(len(probs) + 1, np.int64)
     offs[1:] = np.cumsum([len(p[0]) for p in probs])
     d = np.concatenate([p[0] for p in probs]).astype(np.float64)
