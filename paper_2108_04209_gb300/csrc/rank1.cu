@@ -141,10 +141,11 @@ __global__ void k_deflate(int64_t nprob, const int64_t *__restrict__ off,
 // The arithmetic is the same explicitly rounded sequence as k_deflate, so
 // decisions and rotated values agree bit for bit.
 // ---------------------------------------------------------------------------
-constexpr int DB_T = 512;
+constexpr int DB_T = 512;         // threads per problem; 1024 when a batch has fewer problems than SMs
 constexpr int WALK_CAP = 64;      // speculative steps of one chain before one thread finishes it
 
 // exclusive block scan of one int per thread; returns the prefix, *total = sum
+template <int T>
 __device__ __forceinline__ int block_exscan(int v, int *sh, int *total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -156,7 +157,7 @@ __device__ __forceinline__ int block_exscan(int v, int *sh, int *total)
     if (lane == 31) sh[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        int w = (lane < DB_T / 32) ? sh[lane] : 0;
+        int w = (lane < T / 32) ? sh[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
@@ -165,19 +166,20 @@ __device__ __forceinline__ int block_exscan(int v, int *sh, int *total)
     }
     __syncthreads();
     const int before = (warp > 0) ? sh[warp - 1] : 0;
-    *total = sh[DB_T / 32 - 1];
+    *total = sh[T / 32 - 1];
     __syncthreads();
     return before + x - v;
 }
 
-__global__ void __launch_bounds__(DB_T)
+template <int T>
+__global__ void __launch_bounds__(T)
 k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__restrict__ d,
               const double *__restrict__ z, double sqrt_rho, double tau, double *__restrict__ wd,
               double *__restrict__ wz, int8_t *__restrict__ kept, int32_t *__restrict__ surv, R1Out o)
 {
     __shared__ int sh[32];
     __shared__ int s_bad, s_ng;
-    __shared__ double s_w[DB_T / 32];
+    __shared__ double s_w[T / 32];
     const int64_t p = blockIdx.x;
     if (p >= nprob) return;
     const int64_t b0 = off[p];
@@ -188,7 +190,7 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     __syncthreads();
     // A: copy, mask, survivor list
     int S = 0;
-    for (int c = 0; c < m; c += DB_T) {
+    for (int c = 0; c < m; c += T) {
         const int i = c + tid;
         int keep = 0;
         if (i < m) {
@@ -200,7 +202,7 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
             kept[b0 + i] = (int8_t)keep;
         }
         int tot;
-        int pre = block_exscan(keep, sh, &tot);
+        int pre = block_exscan<T>(keep, sh, &tot);
         if (keep) surv[b0 + S + pre] = i;
         S += tot;
     }
@@ -211,7 +213,7 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     // data only right after a rotation.  B1 evaluates every adjacent test on
     // the original values in parallel and marks the survivors whose test
     // passes (kept = 2, "chain heads").  B2 takes the positions in rounds of
-    // DB_T: every head of the round walks its chain in its own thread on the
+    // T: every head of the round walks its chain in its own thread on the
     // original values (rotate, re-test the next pair with the rotated values,
     // until a test fails; at most WALK_CAP steps); one thread then decides in
     // order which heads start a chain of the sequential scan (a head inside or
@@ -221,7 +223,7 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     // and written by that one thread).  Each chain evaluates the same
     // explicitly rounded operations in the same order as the plain sequential
     // scan (k_deflate), so decisions and rotated values agree bit for bit.
-    for (int t = 1 + tid; t < S; t += DB_T) {
+    for (int t = 1 + tid; t < S; t += T) {
         const int ia = surv[b0 + t - 1], ib = surv[b0 + t];
         const double da = wd[b0 + ia], za = wz[b0 + ia], db = wd[b0 + ib], zb = wz[b0 + ib];
         const double lhs = fabs(__dmul_rn(__dmul_rn(__dsub_rn(da, db), za), zb));
@@ -230,7 +232,7 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     }
     __syncthreads();
     {
-        __shared__ int h_pos[DB_T], h_end[DB_T], h_off[DB_T];
+        __shared__ int h_pos[T], h_end[T], h_off[T];
         __shared__ int s_nh, s_eprev;
         // one chain from position h (candidate s_{h-1}); write = false: count
         // only.  Returns the first position whose test fails (or S), or -1 when
@@ -276,11 +278,11 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
             return t2;
         };
         if (tid == 0) { s_eprev = 0; s_ng = 0; }
-        for (int c = 1; c < S; c += DB_T) {
+        for (int c = 1; c < S; c += T) {
             const int t = c + tid;
             const int hf = (t < S && kept[b0 + surv[b0 + t]] == 2) ? 1 : 0;
             int nh;
-            const int pre = block_exscan(hf, sh, &nh);
+            const int pre = block_exscan<T>(hf, sh, &nh);
             if (hf) h_pos[pre] = t;
             __syncthreads();
             if (nh == 0) continue;
@@ -319,11 +321,11 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     // C: compaction, kept slots in index order, then deflated slots in index order
     int mk = 0;
     double wpart = 0.0;
-    for (int c = 0; c < m; c += DB_T) {
+    for (int c = 0; c < m; c += T) {
         const int i = c + tid;
         const int k = (i < m) ? (int)(kept[b0 + i] != 0) : 0;
         int tot;
-        int pre = block_exscan(k, sh, &tot);
+        int pre = block_exscan<T>(k, sh, &tot);
         if (k) {
             double zi = wz[b0 + i];
             o.dk[b0 + mk + pre] = wd[b0 + i];
@@ -334,11 +336,11 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
         mk += tot;
     }
     int nd = 0;
-    for (int c = 0; c < m; c += DB_T) {
+    for (int c = 0; c < m; c += T) {
         const int i = c + tid;
         const int dflt = (i < m) ? (int)(kept[b0 + i] == 0) : 0;
         int tot;
-        int pre = block_exscan(dflt, sh, &tot);
+        int pre = block_exscan<T>(dflt, sh, &tot);
         if (dflt) {
             o.dk[b0 + mk + nd + pre] = wd[b0 + i];
             o.src[b0 + mk + nd + pre] = i;
@@ -353,7 +355,7 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
     // out of order only inside tau-sized intervals, so insertion is short
     if (tid == 0) {
         double W = 0.0;
-        for (int w = 0; w < DB_T / 32; w++) W += s_w[w];
+        for (int w = 0; w < T / 32; w++) W += s_w[w];
         o.wsum[p] = W;
         o.mk[p] = mk;
         o.ngiv[p] = s_ng;
@@ -371,7 +373,7 @@ k_deflate_big(int64_t nprob, const int64_t *__restrict__ off, const double *__re
         }
     }
     __syncthreads();
-    for (int s2 = mk + tid; s2 < m; s2 += DB_T) {
+    for (int s2 = mk + tid; s2 < m; s2 += T) {
         o.zk[b0 + s2] = 0.0;
         o.org[b0 + s2] = -1;
         o.eta[b0 + s2] = 0.0;
@@ -817,7 +819,8 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
     PROF_LAUNCH("deflate", st, k_deflate<<<(unsigned)((a.nprob + tpb - 1) / tpb), tpb, 0, st>>>(
         a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau, wd, wz, kept, a.o));
     if (a.total > DEFL_BIG)
-        PROF_LAUNCH("deflate", st, k_deflate_big<<<(unsigned)a.nprob, DB_T, 0, st>>>(
+        PROF_LAUNCH("deflate", st, (nsm > a.nprob ? k_deflate_big<1024> : k_deflate_big<DB_T>)<<<
+                                       (unsigned)a.nprob, nsm > a.nprob ? 1024 : DB_T, 0, st>>>(
             a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau, wd, wz, kept, surv, a.o));
     // problems whose kept size reaches the threshold take the triangular FMM
     // path; the direct kernels below skip them
@@ -968,7 +971,7 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     k_deflate<<<(unsigned)((a.nprob + tpb - 1) / tpb), tpb, 0, st>>>(a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau,
                                                                       wd, wz, kept, a.o);
     if (a.total > DEFL_BIG)
-        k_deflate_big<<<(unsigned)a.nprob, DB_T, 0, st>>>(a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau, wd, wz,
+        k_deflate_big<DB_T><<<(unsigned)a.nprob, DB_T, 0, st>>>(a.nprob, a.off, a.d, a.z, a.sqrt_rho, a.tau, wd, wz,
                                                            kept, surv, a.o);
     const int TR = 128;
     k_tiles<<<1, 1024, 0, st>>>(a.nprob, a.o.mk, TR, tile_off);
