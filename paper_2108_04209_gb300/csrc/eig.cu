@@ -846,6 +846,170 @@ FactorView view(const superdc_eigfact *f, int l, int j)
     return v;
 }
 
+// ---------------------------------------------------------------------------
+// Leaves of 128 rows: divide and conquer on the tridiagonal form (the
+// method's own rank-one machinery applied inside the leaves).  The QL chase
+// of a 128-row leaf is one chain of about 12,000 dependent rotations; torn into
+// blocks of 32 (Cuppen's splitting T = diag(T_1', ..., T_4') + sum of rank-one
+// couplings), the chains are 16 times shorter, and the two merge levels are
+// batched rank-one steps (deflation, secular roots, Loewner zhat, b) whose
+// eigenvector products go through the Cauchy-like application.
+//   k_dc_tear      per leaf: scale (d, e) by a power of two >= ||T||_inf (so an
+//                  absolute deflation tolerance of a few eps serves every
+//                  leaf), then tear at every block boundary j: the coupling
+//                  beta = e_{j-1} leaves the tridiagonal, d_{j-1} and d_j lose
+//                  |beta|, and T = blocks + |beta| v v^T, v = e_{j-1} +
+//                  sign(beta) e_j;
+//   k_leaf_ql / k_leaf_rot on the 32-row blocks (identity start);
+//   k_dc_base      block eigenvalues ascending, eigenvector j of a block as
+//                  row (block start + j) of an n x 32 column-major array;
+//   k_dc_merge_in  per merge problem: the children's eigenvalues merged
+//                  (stable, left child first on ties), z = sqrt|beta| (last
+//                  row of the left eigenvectors; sign(beta) first row of the
+//                  right ones), and X = (blkdiag(Q_1, Q_2) P)^T with P the merge;
+//   then the batched rank-one step and Y = Qhat^T X (eigenvectors of the
+//   merged block as rows, in ascending eigenvalue order);
+//   k_dc_gemm      Q_leaf = Q_householder Q_tridiagonal (row-major, into the
+//                  leaf's slot), eigenvalues scaled back.
+// ---------------------------------------------------------------------------
+constexpr int DC_B = 32;        // rows of a block solved by QL
+constexpr int DC_M = 128;       // leaf rows of the divide-and-conquer path
+
+__global__ void k_dc_tear(const int64_t *__restrict__ leaf_off, double *__restrict__ d, double *__restrict__ e,
+                          double *__restrict__ scale, double *__restrict__ beta_at)
+{
+    __shared__ double red[4];
+    const int L = blockIdx.x, tid = threadIdx.x;            // DC_M threads
+    const int64_t o = leaf_off[L];
+    const double di = d[o + tid], ei = (tid + 1 < DC_M) ? e[o + tid] : 0.0;
+    const double em = (tid > 0) ? e[o + tid - 1] : 0.0;
+    double rowsum = fabs(di) + fabs(ei) + fabs(em);
+    for (int sh = 16; sh > 0; sh >>= 1) rowsum = fmax(rowsum, __shfl_xor_sync(0xffffffffu, rowsum, sh));
+    if ((tid & 31) == 0) red[tid >> 5] = rowsum;
+    __syncthreads();
+    const double nrm = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+    // the power of two at or above the norm (1 for a zero block), exact scaling
+    int ex = 0;
+    const double fr = frexp(nrm > 0.0 && isfinite(nrm) ? nrm : 1.0, &ex);
+    const double s = ldexp(1.0, fr == 0.5 ? ex - 1 : ex);
+    const double is = 1.0 / s;
+    double dn = di * is;
+    // couplings torn at the block boundaries (block starts j = 32, 64, 96)
+    if ((tid % DC_B) == DC_B - 1 && tid + 1 < DC_M) dn -= fabs(ei * is);
+    if ((tid % DC_B) == 0 && tid > 0) {
+        dn -= fabs(em * is);
+        beta_at[o + tid] = em * is;
+    }
+    d[o + tid] = dn;
+    e[o + tid] = ((tid % DC_B) == DC_B - 1) ? 0.0 : ei * is;
+    if (tid == 0) scale[L] = s;
+}
+
+// QB (row-major 32 x 32 per block, identity before k_leaf_rot)
+__global__ void k_dc_eye(int64_t nblk, double *__restrict__ QB)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nblk * DC_B * DC_B;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(t % (DC_B * DC_B));
+        QB[t] = (e / DC_B == e % DC_B) ? 1.0 : 0.0;
+    }
+}
+
+// block eigenvalues ascending (ties by index) into lam, eigenvector j of
+// block b as row (o_b + j) of Y (n x 32, column-major, ld n); one warp per block
+__global__ void k_dc_base(int64_t nblk, int64_t n, const double *__restrict__ dd, const double *__restrict__ QB,
+                          double *__restrict__ lam, double *__restrict__ Y)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= nblk) return;
+    const int64_t o = b * DC_B;
+    const double li = dd[o + lane];
+    int rk = 0;
+    for (int j = 0; j < DC_B; j++) {
+        const double lj = __shfl_sync(0xffffffffu, li, j);
+        rk += (lj < li) || (lj == li && j < lane);
+    }
+    lam[o + rk] = li;
+    const double *Q = QB + b * DC_B * DC_B;
+    for (int c = 0; c < DC_B; c++) Y[(o + rk) + (int64_t)c * n] = Q[c * DC_B + lane];
+}
+
+// merge problem p of size s (children of h = s/2 rows): merged d, z and X
+__global__ void k_dc_merge_in(int64_t n, int s, const double *__restrict__ lam, const double *__restrict__ beta_at,
+                              const double *__restrict__ Yin, double *__restrict__ din, double *__restrict__ zin,
+                              double *__restrict__ X)
+{
+    const int h = s / 2;
+    const int64_t o = (int64_t)blockIdx.x * s;
+    const int t = threadIdx.x;                    // s threads
+    const double beta = beta_at[o + h];
+    const double sb = sqrt(fabs(beta));
+    const bool left = t < h;
+    const int j = left ? t : t - h;
+    const int64_t ro = left ? o : o + h;          // the child's first row
+    const double *other = lam + (left ? o + h : o);
+    const double lj = lam[ro + j];
+    // elements of the other child before this one: strictly smaller (left
+    // child) or smaller or equal (right child): left first on ties
+    int lo = 0, hi = h;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (left ? (other[mid] < lj) : (other[mid] <= lj)) lo = mid + 1; else hi = mid;
+    }
+    const int64_t pos = o + j + lo;
+    din[pos] = lj;
+    zin[pos] = left ? sb * Yin[(ro + j) + (int64_t)(h - 1) * n] : copysign(sb, beta) * Yin[(ro + j)];
+    for (int c = 0; c < s; c++) {
+        const bool mine = left ? (c < h) : (c >= h);
+        X[pos + (int64_t)c * n] = mine ? Yin[(ro + j) + (int64_t)(left ? c : c - h) * n] : 0.0;
+    }
+}
+
+// Q_leaf = Q_householder Q_tridiagonal for every leaf (row-major, into the
+// leaf's slot), with Q_tridiagonal(c, k) = Y(o + k, c); 64 x 64 tiles, 256
+// threads, 4 x 4 outputs per thread, k-chunks of 16 staged in shared memory.
+// Eigenvalues (lam, ascending) scaled back into dd.
+__global__ void __launch_bounds__(256)
+k_dc_gemm(int64_t n, const int64_t *__restrict__ leaf_off, const int64_t *__restrict__ qoff,
+          const double *__restrict__ Qh, const double *__restrict__ Y, double *__restrict__ Qleaf,
+          const double *__restrict__ lam, const double *__restrict__ scale, double *__restrict__ dd)
+{
+    __shared__ double As[16][64 + 1], Bs[16][64 + 1];
+    const int L = blockIdx.x, tr = blockIdx.y * 64, tc = blockIdx.z * 64;
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    const int64_t o = leaf_off[L];
+    const double *A = Qh + qoff[L];
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < DC_M; k0 += 16) {
+        __syncthreads();
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int kk = e % 16, rr = e / 16;
+            As[kk][rr] = A[(int64_t)(tr + rr) * DC_M + k0 + kk];          // Q_h(row, k)
+            const int cc = e % 64, kb = e / 64;
+            Bs[kb][cc] = Y[(o + tc + cc) + (int64_t)(k0 + kb) * n];         // Q_tri(k, col)
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+    }
+    double *C = Qleaf + qoff[L];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) C[(int64_t)(tr + ty * 4 + i) * DC_M + tc + tx * 4 + j] = acc[i][j];
+    if (blockIdx.y == 0 && blockIdx.z == 0)
+        for (int k = tid; k < DC_M; k += 256) dd[o + k] = lam[o + k] * scale[L];
+}
+
 }  // namespace
 
 extern "C" {
@@ -1239,16 +1403,126 @@ superdc_status superdc_eig_plan(const superdc_hss *h, const superdc_opts *opts, 
     w.smem5 = (size_t)LEAF_R * (mm | 1) * sizeof(double);
     w.cap = 3 * (int64_t)mm * mm;
     w.caps = 16 * (int64_t)mm;
+    // leaves all of 128 rows: divide and conquer inside the leaves (blocks of
+    // 32, two merge levels); its QL records fit the leaves' record buffers
+    w.leaf_dc = (mm == DC_M);
+    for (int L : h->leaves) w.leaf_dc = w.leaf_dc && h->size[L] == DC_M;
+    const int64_t nblk = n / DC_B;
     if (w.leaf_batched) {
         EIG_CHECK(dalloc(&w.rot, (size_t)h->nleaves * w.cap, &f->slabs));
         EIG_CHECK(dalloc(&w.hdr, (size_t)h->nleaves * w.caps, &f->slabs));
-        EIG_CHECK(dalloc(&w.nsw, h->nleaves, &f->slabs));
+        EIG_CHECK(dalloc(&w.nsw, std::max<int64_t>(h->nleaves, w.leaf_dc ? nblk : 0), &f->slabs));
+    }
+    if (w.leaf_dc) {
+        std::vector<int64_t> bo(nblk), bm(nblk, DC_B), bq(nblk);
+        for (int64_t b = 0; b < nblk; b++) { bo[b] = b * DC_B; bq[b] = b * DC_B * DC_B; }
+        EIG_CHECK(dalloc(&w.dc_boff, nblk, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_bm, nblk, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_bq, nblk, &f->slabs));
+        EIG_CHECK(cudaMemcpy(w.dc_boff, bo.data(), nblk * sizeof(int64_t), cudaMemcpyHostToDevice));
+        EIG_CHECK(cudaMemcpy(w.dc_bm, bm.data(), nblk * sizeof(int64_t), cudaMemcpyHostToDevice));
+        EIG_CHECK(cudaMemcpy(w.dc_bq, bq.data(), nblk * sizeof(int64_t), cudaMemcpyHostToDevice));
+        for (int lv = 0; lv < 2; lv++) {
+            const int64_t sz = 64 << lv, np = n / sz;
+            std::vector<int64_t> po(np + 1);
+            for (int64_t p = 0; p <= np; p++) po[p] = p * sz;
+            EIG_CHECK(dalloc(&w.dc_off[lv], np + 1, &f->slabs));
+            EIG_CHECK(cudaMemcpy(w.dc_off[lv], po.data(), (np + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        }
+        EIG_CHECK(dalloc(&w.dc_scale, h->nleaves, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_beta, n, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_QB, (size_t)n * DC_B, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_Ya, (size_t)n * DC_M, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_Yb, (size_t)n * DC_M, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_X, (size_t)n * DC_M, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_Qh, (size_t)n * DC_M, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_lam, n, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_din, n, &f->slabs));
+        EIG_CHECK(dalloc(&w.dc_zin, n, &f->slabs));
+        R1Out &o = w.dc_o;
+        for (double **x : {&o.dk, &o.zk, &o.eta, &o.vhat, &o.bnorm, &o.dorg}) EIG_CHECK(dalloc(x, n, &f->slabs));
+        EIG_CHECK(dalloc(&o.giv_cs, 2 * (size_t)n, &f->slabs));
+        for (int32_t **x : {&o.org, &o.src, &o.perm, &o.sweeps, &o.pinv}) EIG_CHECK(dalloc(x, n, &f->slabs));
+        EIG_CHECK(dalloc(&o.giv_ab, 2 * (size_t)n, &f->slabs));
+        EIG_CHECK(dalloc(&o.mk, n / 64, &f->slabs));
+        EIG_CHECK(dalloc(&o.ngiv, n / 64, &f->slabs));
+        EIG_CHECK(dalloc(&o.wsum, n / 64, &f->slabs));
+        o.lam = w.dc_lam;
+        o.status = f->status;
+        o.fmm_used = nullptr;
+        o.unshifted = 0;
     }
     EIG_CHECK(leaf_attrs());
     EIG_CHECK(r1_prepare());
 #undef EIG_CHECK
     *fact = f;
     return SUPERDC_OK;
+}
+
+// Leaves of 128 rows, divide and conquer (see k_dc_tear): from the
+// tridiagonal forms (w.dq, w.eq) and the Householder factors (w.dc_Qh) to
+// the eigenvalues (w.dq) and row-major eigenvectors in the leaves' slots.
+static superdc_status leaf_dc_run(superdc_eigfact *f, cudaStream_t st)
+{
+    const superdc_hss *h = f->h;
+    const int64_t n = f->n, nblk = n / DC_B;
+    EigWork &w = f->work;
+    PROF_LAUNCH("leaf", st, k_dc_tear<<<(unsigned)h->nleaves, DC_M, 0, st>>>(h->d_leaf_off, w.dq, w.eq, w.dc_scale,
+                                                                            w.dc_beta));
+    // blocks of 32: QL chases (about one warp per scheduler), rotations onto identities
+    int lpw = 1;
+    while (lpw < 32 && (int64_t)lpw * 4 * sdc_num_sms() < nblk) lpw *= 2;
+    const unsigned gq = (unsigned)((nblk + lpw - 1) / lpw);
+    const size_t sq = 2 * (size_t)DC_B * lpw * sizeof(double);
+    const int64_t capb = 3 * DC_B * DC_B, capsb = 16 * DC_B;
+#define SDC_QL(W) \
+    if (lpw == W) \
+        PROF_LAUNCH("leaf", st, k_leaf_ql<W><<<gq, 32, sq, st>>>((int)nblk, DC_B, w.dc_boff, w.dc_bm, w.dq, w.eq, \
+                                                                w.rot, w.hdr, w.nsw, capb, (int)capsb, f->status));
+    SDC_QL(1) SDC_QL(2) SDC_QL(4) SDC_QL(8) SDC_QL(16) SDC_QL(32)
+#undef SDC_QL
+    const unsigned g = (unsigned)(sdc_num_sms() * 8);
+    PROF_LAUNCH("leaf", st, k_dc_eye<<<g, 256, 0, st>>>(nblk, w.dc_QB));
+    PROF_LAUNCH("leaf", st, k_leaf_rot<<<dim3((unsigned)nblk, 1), LEAF_R, (size_t)LEAF_R * (DC_B | 1) * sizeof(double),
+                                         st>>>(w.dc_bm, w.dc_QB, w.dc_bq, w.rot, w.hdr, w.nsw, capb, (int)capsb));
+    PROF_LAUNCH("leaf", st, k_dc_base<<<(unsigned)((nblk * 32 + 255) / 256), 256, 0, st>>>(nblk, n, w.dq, w.dc_QB,
+                                                                                          w.dc_lam, w.dc_Ya));
+    // two merge levels: 64 and 128 rows
+    double *Yin = w.dc_Ya, *Yout = w.dc_Yb;
+    for (int lv = 0; lv < 2; lv++) {
+        const int sz = 64 << lv;
+        const int64_t np = n / sz;
+        PROF_LAUNCH("leaf", st, k_dc_merge_in<<<(unsigned)np, sz, 0, st>>>(n, sz, w.dc_lam, w.dc_beta, Yin, w.dc_din,
+                                                                           w.dc_zin, w.dc_X));
+        R1Args a;
+        a.nprob = np;
+        a.total = n;
+        a.off = w.dc_off[lv];
+        a.d = w.dc_din;
+        a.z = w.dc_zin;
+        a.sqrt_rho = 1.0;
+        a.tau = 16.0 * SDC_EPS;                 // the leaves are scaled to norm <= 1
+        a.stop_c = f->opts.stop_c;
+        a.max_iter = f->opts.max_iter;
+        a.tile_roots = 0;
+        a.sched = 0;
+        a.fmm_min_m = 0;
+        a.max_m = sz;
+        a.o = w.dc_o;
+        superdc_status s = r1_run(a, st);
+        if (s != SUPERDC_OK) return s;
+        FactorView fv;
+        fv.nprob = np; fv.off = w.dc_off[lv]; fv.mk = w.dc_o.mk; fv.ngiv = w.dc_o.ngiv; fv.dk = w.dc_o.dk;
+        fv.eta = w.dc_o.eta; fv.dorg = w.dc_o.dorg; fv.vhat = w.dc_o.vhat; fv.bnorm = w.dc_o.bnorm;
+        fv.src = w.dc_o.src; fv.perm = w.dc_o.perm; fv.pinv = w.dc_o.pinv; fv.giv_ab = w.dc_o.giv_ab;
+        fv.giv_cs = w.dc_o.giv_cs; fv.fmm_min_m = 0; fv.max_m = sz;
+        s = cauchy_apply_T(fv, n, w.dc_X, n, Yout, n, sz, st);
+        if (s != SUPERDC_OK) return s;
+        std::swap(Yin, Yout);
+    }
+    PROF_LAUNCH("leaf", st, k_dc_gemm<<<dim3((unsigned)h->nleaves, DC_M / 64, DC_M / 64), 256, 0, st>>>(
+                                n, h->d_leaf_off, f->d_qoff, w.dc_Qh, Yin, f->Qleaf, w.dc_lam, w.dc_scale, w.dq));
+    return cudaGetLastError() == cudaSuccess ? SUPERDC_OK : SUPERDC_ERR_CUDA;
 }
 
 superdc_status superdc_eig_run(superdc_eigfact *f, cudaStream_t st, double *lambda)
@@ -1286,9 +1560,15 @@ superdc_status superdc_eig_run(superdc_eigfact *f, cudaStream_t st, double *lamb
     {
         const int mm = h->mmax;
         PROF_LAUNCH("leaf", st, k_leaf_tri<<<(unsigned)h->nleaves, LEAF_T, w.smem1, st>>>(
-            r, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H, f->Qleaf,
-            f->d_qoff, w.dq, w.eq));
-        if (w.leaf_batched) {
+            r, h->d_leaf_off, h->d_leaf_m, h->d_leaf_doff, h->d_leaf_uoff, h->d_leaf_id, h->D, h->U, H,
+            w.leaf_dc ? w.dc_Qh : f->Qleaf, f->d_qoff, w.dq, w.eq));
+        if (w.leaf_dc) {
+            const superdc_status ls = leaf_dc_run(f, st);
+            if (ls != SUPERDC_OK) return ls;
+            PROF_LAUNCH("leaf", st, k_leaf_out<<<(unsigned)h->nleaves, LEAF_T, w.smem3, st>>>(
+                r, n, h->d_leaf_off, h->d_leaf_m, h->d_leaf_uoff, h->U, f->Qleaf, f->d_qoff, w.dq, w.lamA, Wp,
+                f->status));
+        } else if (w.leaf_batched) {
             const int lpw = w.ql_lpw;
             const unsigned gq = (unsigned)((h->nleaves + lpw - 1) / lpw);
             const size_t sq = 2 * (size_t)mm * lpw * sizeof(double);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include "common.cuh"
 #include "cauchy.cuh"
+#include "rank1.cuh"
 
 struct superdc_hss {
     int64_t n = 0;
@@ -51,6 +52,18 @@ struct EigWork {
     size_t smem1 = 0, smem2 = 0, smem3 = 0, smem4 = 0, smem5 = 0;
     int ql_lpw = 32;                       // leaves per warp of the batched QL chase
     int64_t cap = 0, caps = 0;
+    // leaves of 128 rows: divide and conquer on the tridiagonal form
+    // (blocks of 32 by implicit QL, two levels of batched rank-one merges)
+    bool leaf_dc = false;
+    int64_t *dc_boff = nullptr, *dc_bm = nullptr, *dc_bq = nullptr;   // per 32-row block
+    int64_t *dc_off[2] = {nullptr, nullptr};  // merge levels (64, 128 rows): problem offsets
+    double *dc_scale = nullptr;            // per leaf: power of two >= ||T||_inf
+    double *dc_beta = nullptr;             // per row: the coupling torn at that row (block starts)
+    double *dc_QB = nullptr;               // 32 x 32 block eigenvectors (row-major)
+    double *dc_Ya = nullptr, *dc_Yb = nullptr, *dc_X = nullptr;   // n x 128, column-major
+    double *dc_Qh = nullptr;               // Householder factors of the leaves (row-major)
+    double *dc_lam = nullptr, *dc_din = nullptr, *dc_zin = nullptr;
+    R1Out dc_o{};                          // outputs of the merge steps
 };
 
 struct superdc_eigfact {

@@ -275,6 +275,29 @@ def test_ragged_leaves_and_single_leaf_vs_oracle(sizes, rank):
     assert dense.theta(Q) <= 1e-13
 
 
+@pytest.mark.parametrize("clustered", [False, True])
+def test_leaf128_divide_and_conquer_vs_dense(clustered):
+    """Leaves of 128 rows take the divide-and-conquer leaf solver (blocks of
+    32 by QL, two batched rank-one merge levels, deflation at 16 eps of the
+    scaled leaf): n = 1024, rank 6, random and clustered leaf spectra (leaf
+    eigenvalues repeated to 1e-12, which the merges deflate); every eigenvalue
+    per entry against numpy's eigvalsh of the dense matrix and the oracle, and
+    the dense Q against the paper's metrics."""
+    h = inputs.hss_random(1024, 128, 6, seed=13, clustered=clustered)
+    A = dense.dense_from_hss(h)
+    H, lam, F = gpu_eig(h)
+    ev = np.linalg.eigvalsh(A)
+    an = np.abs(ev).max()
+    O = osd.superdc(h, tau=1e-10, mode=0)
+    for ref in (ev, O.eigenvalues):
+        ok, info = P.lam_check(lam, ref, an, int(h.tree.level.max()) * 6, tau=1e-10, decisions_differ=True)
+        print("leaf 128 D&C clustered=%s" % clustered, info)
+        assert ok, info
+    Q, QT = dense_Q(F, h.tree.n)
+    assert np.abs(QT - Q.T).max() < 1e-13
+    assert dense.gamma(A, lam, Q) <= 1e-12 and dense.theta(Q) <= 1e-12
+
+
 def test_maximum_rank_32_vs_oracle():
     """The largest rank the library accepts (r = 32; n = 1024, leaves of 64):
     per-entry eigenvalues against the oracle, probes of Q."""
