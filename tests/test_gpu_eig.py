@@ -281,16 +281,18 @@ def test_leaf128_divide_and_conquer_vs_dense(clustered):
     32 by QL, two batched rank-one merge levels, deflation at 16 eps of the
     scaled leaf): n = 1024, rank 6, random and clustered leaf spectra (leaf
     eigenvalues repeated to 1e-12, which the merges deflate); every eigenvalue
-    per entry against numpy's eigvalsh of the dense matrix and the oracle, and
-    the dense Q against the paper's metrics."""
+    per entry against numpy's eigvalsh of the dense matrix and the oracle
+    (tree deflation tau = 1e-14), and the dense Q against the paper's metrics."""
     h = inputs.hss_random(1024, 128, 6, seed=13, clustered=clustered)
     A = dense.dense_from_hss(h)
-    H, lam, F = gpu_eig(h)
+    # tau = 1e-14: the tree's own deflation (Remark 4.1) stays at rounding
+    # level, so the dense eigenvalues are a per-entry reference too
+    H, lam, F = gpu_eig(h, tau=1e-14)
     ev = np.linalg.eigvalsh(A)
     an = np.abs(ev).max()
-    O = osd.superdc(h, tau=1e-10, mode=0)
+    O = osd.superdc(h, tau=1e-14, mode=0)
     for ref in (ev, O.eigenvalues):
-        ok, info = P.lam_check(lam, ref, an, int(h.tree.level.max()) * 6, tau=1e-10, decisions_differ=True)
+        ok, info = P.lam_check(lam, ref, an, int(h.tree.level.max()) * 6)
         print("leaf 128 D&C clustered=%s" % clustered, info)
         assert ok, info
     Q, QT = dense_Q(F, h.tree.n)
