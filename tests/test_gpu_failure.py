@@ -88,6 +88,35 @@ def test_nonfinite_leaf_block_eig():
     assert ei.value.code == ERR_NONFINITE
 
 
+def test_nonfinite_leaf_block_divide_and_conquer_leaves():
+    """The same with leaves of 128 rows (the leaf divide-and-conquer path): a
+    NaN on a diagonal entry bounds every loop (QL chases hit their iteration
+    cap, the merge steps' deflation latches NONFINITE) and the call returns
+    SUPERDC_ERR_NONFINITE; the library is still usable afterwards."""
+    h = inputs.hss_random(512, 128, 4, seed=2)
+    m = int(h.tree.leaf_size[h.tree.leaves[1]])
+    h.D[int(h.d_off[h.tree.leaves[1]]) + 40 * m + 40] = np.nan
+    H = sdc.HSSMatrix(h)
+    with pytest.raises(sdc.SuperDCError) as ei:
+        H.eig(sdc.default_opts(fmm_min_m=-1))
+    assert ei.value.code == ERR_NONFINITE
+    lam, F = sdc.HSSMatrix(inputs.hss_random(512, 128, 4, seed=2)).eig()
+    assert torch.isfinite(lam).all()
+
+
+def test_zero_matrix_divide_and_conquer_leaves():
+    """All generators zero (leaves of 128): every coupling is zero, every
+    rank-one update deflates; eigenvalues 0 and Q orthogonal."""
+    h = inputs.hss_random(256, 128, 3, seed=1)
+    h.D[:] = 0.0
+    h.U[:] = 0.0
+    h.B[:] = 0.0
+    lam, F = sdc.HSSMatrix(h).eig()
+    assert float(lam.abs().max()) == 0.0
+    Q = F.apply_Q(torch.eye(256, dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.abs(Q.T @ Q - np.eye(256)).max() <= 1e-14
+
+
 def test_iteration_cap_reports_noconv_promptly():
     """max_iter = 1: roots stop after one step past the midpoint sweep; the
     status carries NOCONV and the call takes no longer than a normal one."""
