@@ -1,9 +1,10 @@
 """Run one named workload through the public API (for profilers such as ncu).
 
-    python -m paper_2108_04209_gb300.profile_case secular <nprob> [fmm_min_m]
+    python -m paper_2108_04209_gb300.profile_case secular <nprob> [fmm_min_m] [sched]
         two batched secular calls on the 4096-problem distribution
         (m ~ U{32..2048}, seed 1) restricted to <nprob> problems, with the
-        FMM threshold fmm_min_m (default: the library's);
+        FMM threshold fmm_min_m (default: the library's) and the secular
+        schedule sched (0 automatic, 1 whole problems, 2 pole split);
     python -m paper_2108_04209_gb300.profile_case eig <n> <leaf> <rank>
         superdc_eig twice on a random HSS matrix (seed 4);
     python -m paper_2108_04209_gb300.profile_case applyq <n> <leaf> <rank> <ncols>
@@ -27,10 +28,11 @@ def main(argv):
     if what == "secular":
         n = int(argv[2]) if len(argv) > 2 else 4096
         fm = int(argv[3]) if len(argv) > 3 else 0
+        sc = int(argv[4]) if len(argv) > 4 else 0
         b = inputs.secular_batch(n, 32, 2048, seed=1)
         o, d, z = (torch.from_numpy(x).to(dev) for x in (b.offsets, b.d, b.z))
         for _ in range(2):
-            sdc.secular_batched(o, d, z, 1.0, sdc.default_opts(tau=1e-12, fmm_min_m=fm))
+            sdc.secular_batched(o, d, z, 1.0, sdc.default_opts(tau=1e-12, fmm_min_m=fm, sched=sc))
         torch.cuda.synchronize()
         print("ok", int(b.offsets[-1]))
     elif what in ("eig", "applyq"):
