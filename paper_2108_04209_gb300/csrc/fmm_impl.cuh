@@ -1707,6 +1707,9 @@ k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
             }
             __syncthreads();
             if (act) {
+                // two sources per iteration: the next reciprocal's dependent
+                // chain overlaps this one's column FMAs (same order per column)
+#pragma unroll 2
                 for (int ii = 0; ii < cnt; ii++) {
                     const double r = rcp_nr2((sd[ii] - dK) - e);
 #pragma unroll
@@ -1807,6 +1810,7 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
             }
             __syncthreads();
             if (act) {
+#pragma unroll 2
                 for (int jj = 0; jj < cnt; jj++) {
                     const double r = rcp_nr2((di - sk[jj]) - se[jj]);
 #pragma unroll
