@@ -633,10 +633,19 @@ k_secular(const int64_t *__restrict__ off, const int4 *__restrict__ units,
 template <int TR>
 __global__ void __launch_bounds__(TR)
 k_lowner(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restrict__ tile_off, R1Out o,
-         const int32_t *__restrict__ fslot)
+         const int32_t *__restrict__ fslot, unsigned long long *__restrict__ queue)
 {
+    __shared__ int64_t s_tile;
     const int64_t ntiles = tile_off[nprob];
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t it = blockIdx.x;; it += gridDim.x) {
+        int64_t tile = it;
+        if (queue) {                          // tiles claimed one at a time (costs differ by m)
+            __syncthreads();
+            if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(queue, 1ull);
+            __syncthreads();
+            tile = s_tile;
+        }
+        if (tile >= ntiles) break;
         const int64_t p = sdc_upper_index(tile_off, nprob, tile);
         if (fslot && fslot[p] >= 0) continue;   // FMM problem
         const int64_t b0 = off[p];
@@ -682,10 +691,19 @@ k_lowner(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restri
 template <int TR>
 __global__ void __launch_bounds__(TR)
 k_bnorm(int64_t nprob, const int64_t *__restrict__ off, const int64_t *__restrict__ tile_off, R1Out o,
-         const int32_t *__restrict__ fslot)
+         const int32_t *__restrict__ fslot, unsigned long long *__restrict__ queue)
 {
+    __shared__ int64_t s_tile;
     const int64_t ntiles = tile_off[nprob];
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t it = blockIdx.x;; it += gridDim.x) {
+        int64_t tile = it;
+        if (queue) {                          // tiles claimed one at a time (costs differ by m)
+            __syncthreads();
+            if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(queue, 1ull);
+            __syncthreads();
+            tile = s_tile;
+        }
+        if (tile >= ntiles) break;
         const int64_t p = sdc_upper_index(tile_off, nprob, tile);
         if (fslot && fslot[p] >= 0) continue;   // FMM problem
         const int64_t b0 = off[p];
@@ -850,9 +868,12 @@ superdc_status r1_run(const R1Args &a_in, cudaStream_t st)
         PROF_LAUNCH("secular", st, (k_secular<4, false><<<(unsigned)slots, 128, 0, st>>>(
                                        a.off, units, ucount, ucount + 1, a.o, a.stop_c, a.max_iter)));
     superdc_status fs = fmm_secular(fp, a.off, a.o, a.stop_c, a.max_iter, st);
-    PROF_LAUNCH("lowner", st, k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, fslot));
+    unsigned long long *tq = nullptr;          // tile queues of the direct Loewner and b kernels
+    SDC_CHECK(sc.get(&tq, 2));
+    SDC_CHECK(cudaMemsetAsync(tq, 0, 2 * sizeof(unsigned long long), st));
+    PROF_LAUNCH("lowner", st, k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, fslot, tq));
     if (fs == SUPERDC_OK) fs = fmm_lowner(fp, a.off, a.o, st);
-    PROF_LAUNCH("bnorm", st, k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, fslot));
+    PROF_LAUNCH("bnorm", st, k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, fslot, tq + 1));
     if (fs == SUPERDC_OK) fs = fmm_bnorm(fp, a.off, a.o, st);
     PROF_LAUNCH("merge", st, k_merge<<<(unsigned)(nsm * 8), 256, 0, st>>>(a.nprob, a.off, a.total, a.o));
     const cudaError_t le = cudaGetLastError();
@@ -988,8 +1009,8 @@ extern "C" superdc_status superdc_secular_batched_noalloc(int64_t nprob, const i
     else
         k_secular<4, false><<<(unsigned)slots, 128, 0, st>>>(a.off, units, ucount, ucount + 1, a.o, a.stop_c,
                                                               a.max_iter);
-    k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, nullptr);
-    k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, nullptr);
+    k_lowner<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, nullptr, nullptr);
+    k_bnorm<128><<<grid, 128, 0, st>>>(a.nprob, a.off, tile_off, a.o, nullptr, nullptr);
     k_merge<<<(unsigned)(nsm * 8), 256, 0, st>>>(a.nprob, a.off, a.total, a.o);
     SDC_CHECK(cudaGetLastError());
     return SUPERDC_OK;
