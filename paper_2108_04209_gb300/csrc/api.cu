@@ -89,6 +89,10 @@ cudaMemPool_t sdc_pool()
         if (cudaMemPoolCreate(&pool, &pp) == cudaSuccess) {
             unsigned long long keep = SDC_POOL_KEEP;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            // no dependencies inserted between streams to reuse a block (the
+            // host entry's two streams would otherwise be serialised)
+            int no = 0;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
             pools[dev] = pool;
         } else {
             cudaGetLastError();
