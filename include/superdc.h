@@ -353,7 +353,10 @@ superdc_status superdc_build_hss_compress(int64_t n, int32_t leaf, int32_t rank,
 /* Eigendecomposition A = Q diag(lambda) Q^T (Algorithms 1-3):
  *   dividing stage (Algorithm 1, balanced eqs. (3.11)/(3.12), generator
  *   updates of Lemma 2.1); leaf eigendecompositions (Householder
- *   tridiagonalisation and implicit QL with Wilkinson's shift); conquering stage bottom-up over the tree levels: merge sort P_p
+ *   tridiagonalisation, then implicit QL with Wilkinson's shift, or for
+ *   leaves all of 128 rows a divide and conquer on the tridiagonal form:
+ *   blocks of 32 by QL, two levels of batched rank-one merges); conquering
+ *   stage bottom-up over the tree levels: merge sort P_p
  *   (eq. (4.31)), Zhat_p = diag(Q_c1^T, Q_c2^T) Z_p (eq. (2.8)), r rank-one
  *   steps per node, each step applied to the remaining columns.
  * lambda: DEVICE, n entries, ascending (caller-allocated).
