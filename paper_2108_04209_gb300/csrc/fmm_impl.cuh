@@ -551,7 +551,7 @@ __device__ __forceinline__ void m2m_box(const FmmDev &pl, int64_t p, int nb0, in
         const int64_t gc = gcb + 2 * b + ci;
         double cc, hc;
         box_ch(pl.blo[gc], pl.bhi[gc], cc, hc);
-        const double v = (cc + hc * xq[q] - cP) * ihP;
+        const double v = fma(hc * ihP, xq[q], (cc - cP) * ihP);    // as scale and shift (see l2l_box)
         double t0 = 1.0, t1 = v;
         Tv[t][0] = 1.0;
         Tv[t][1] = v;
@@ -883,7 +883,13 @@ __device__ __forceinline__ void l2l_box(const FmmDev &pl, int64_t p, int nb0, in
             double cP, hP, cT, hT;
             box_ch(pl.blo[gP], pl.bhi[gP], cP, hP);
             box_ch(pl.blo[g], pl.bhi[g], cT, hT);
-            const double v = (cT + hT * xq[tid] - cP) / hP;
+            // the node in the parent's variable as alpha x_q + beta: forming the
+            // node's position c + h x_q first would round it to the spacing of
+            // c, which on a box of one point (h = |c| 1e-15) moves the nodes by
+            // several percent of h; a chain of such boxes then re-evaluates the
+            // field's rounding noise off the nodes at every level (relative
+            // errors up to 1e-7 in zhat of the last pole)
+            const double v = fma(hT / hP, xq[tid], (cT - cP) / hP);
             double t0 = 1.0, t1 = v;
             Tv[tid][0] = 1.0;
             Tv[tid][1] = v;

@@ -10,8 +10,9 @@ Tolerances (derived from the arithmetic):
     For m up to a few thousand this is ~1e-12 relative; at m = 131072 and
     weakly coupled roots (z_k^2 small against the gap) it reaches ~1e-6;
   * vhat, b: the oracle's formulas (eqs. (4.23), (4.27)) evaluated on the
-    GPU's own origins and gaps, 1e-8 relative (products and sums of m
-    shifted differences on equal inputs: rounding only);
+    GPU's own origins and gaps, max(1e-11, 4 mk eps) relative (products and
+    sums of about 2 mk shifted differences on equal inputs: rounding only,
+    plus the FMM's far-field error);
   * deflation decisions, rotations and the kept/deflated layout: bit-exact
     (both sides evaluate them with the same IEEE operations in the same order);
   * the merge permutation: bit-exact unless two new eigenvalues lie within
@@ -23,8 +24,15 @@ from oracle import rank1 as r1
 
 LAM_RTOL = 1e-10
 ETA_RTOL = 1e-9
-VEC_RTOL = 1e-8
 EPS = 2.0 ** -52
+
+
+def vec_rtol(mk):
+    """Relative tolerance of zhat and b of a problem with mk kept poles: each
+    is a product (eq. (4.23)) or a sum (eq. (4.27)) of about 2 mk rounded
+    factors or terms of one sign, so at most about 4 mk eps relative; the far
+    field's log form adds ~1e-14 per far box; floor 1e-11."""
+    return max(1e-11, 4.0 * mk * EPS)
 
 
 def lam_check(lam, ref, anorm, nsteps, tau=0.0, decisions_differ=False, max_exceptions=8):
@@ -109,8 +117,8 @@ def check_roots(f, K_g, eta_g, vhat_g, b_g, stop_c=8.0):
     bb = r1.bnorm(f.dk, vh, K_g, eta_g)
     rv = np.abs(vhat_g - vh) / np.abs(vh)
     rb = np.abs(b_g - bb) / np.abs(bb)
-    assert rv.max() <= VEC_RTOL, rv.max()
-    assert rb.max() <= VEC_RTOL, rb.max()
+    assert rv.max() <= vec_rtol(mk), (rv.max(), int(rv.argmax()), mk)
+    assert rb.max() <= vec_rtol(mk), (rb.max(), int(rb.argmax()), mk)
     st.update(origin_same=float(same.mean()), eta_over_bound=float(np.max((err / bound)[same])),
               eta_rel=float(np.max(err[same] / np.maximum(np.abs(f.eta[same]), 1e-300))),
               vhat_rel=float(rv.max()), b_rel=float(rb.max()))
