@@ -539,7 +539,7 @@ __device__ __forceinline__ void m2m_box(const FmmDev &pl, int64_t p, int nb0, in
     if (tid < 2 * P) {                 // the threads that build Tv (uniform FP64 work costs every warp)
         double hP;
         box_ch(pl.blo[g], pl.bhi[g], cP, hP);
-        ihP = 1.0 / hP;
+        ihP = rcp_nr2(hP);
     }
     const int nbc = lev_nb(nb0, l - 1);
     const int64_t gcb = pl.box_base[p] + lev_base(nb0, l - 1);
@@ -889,7 +889,8 @@ __device__ __forceinline__ void l2l_box(const FmmDev &pl, int64_t p, int nb0, in
             // several percent of h; a chain of such boxes then re-evaluates the
             // field's rounding noise off the nodes at every level (relative
             // errors up to 1e-7 in zhat of the last pole)
-            const double v = fma(hT / hP, xq[tid], (cT - cP) / hP);
+            const double ihP = rcp_nr2(hP);
+            const double v = fma(hT * ihP, xq[tid], (cT - cP) * ihP);
             double t0 = 1.0, t1 = v;
             Tv[tid][0] = 1.0;
             Tv[tid][1] = v;
