@@ -1,7 +1,7 @@
 """Shared comparison helpers for the GPU parity tests (CUDA path vs oracle).
 
 Tolerances (derived from the arithmetic):
-  * eigenvalues: |lam - lam_o| <= 1e-10 * max(|lam_o|, 1e-6 scale)  (spec bound);
+  * eigenvalues: |lam - lam_o| <= 1e-10 * max(|lam_o|, 1e-6 scale)  (the target bound);
   * gaps eta (same origin): both sides stop when the test of eq. (4.12),
     |f| < c m eps (1 + |psi| + |phi|), holds (the oracle's bisection mode goes
     to adjacent doubles), so each gap lies within that tolerance over f' of
