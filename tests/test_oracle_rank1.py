@@ -104,6 +104,30 @@ def test_zhat_and_b_vs_mpmath(mode):
         assert abs(f.b[j] - bstar) <= 1e-10 * bstar
 
 
+@pytest.mark.parametrize("mode,rtol", [(0, 1e-12), (1, 1e-10)])
+def test_zhat_and_b_isolated_last_pole_and_close_pair(mode, rtol):
+    """The structure of a large merge whose last pole sits alone beyond a
+    wide gap, with a pair of poles 1e-9 apart inside: zhat from Loewner's
+    formula still reproduces |z| and b matches the 50-digit value (eqs.
+    (4.23), (4.27)); the last root lies right of d_{m-1} within sum z^2."""
+    rng = np.random.default_rng(17)
+    m = 40
+    d = np.sort(rng.uniform(0, 1, m - 1))
+    d[10:12] = d[10] + np.array([0.0, 1e-9])
+    d = np.append(np.sort(d), 3.0)
+    z = rng.standard_normal(m)
+    f = r1.rank1_step(d, z, tau=1e-14, mode=mode)
+    assert f.mk == m
+    assert np.all(np.abs(np.abs(f.vhat) - np.abs(f.zk)) <= rtol * np.abs(f.zk))
+    lam_star = mp_roots(f.dk, f.zk)
+    assert lam_star[-1] > f.dk[-1] and lam_star[-1] < f.dk[-1] + mpmath.fsum(mpmath.mpf(float(x)) ** 2 for x in f.zk)
+    for j in range(f.mk):
+        s = mpmath.fsum((mpmath.mpf(float(f.zk[i])) ** 2) / (mpmath.mpf(float(f.dk[i])) - lam_star[j]) ** 2
+                        for i in range(f.mk))
+        bstar = 1 / mpmath.sqrt(s)
+        assert abs(f.b[j] - bstar) <= rtol * bstar, j
+
+
 @pytest.mark.parametrize("m,seed,cluster,tau", [(30, 1, False, 1e-12), (64, 5, True, 1e-12),
                                                 (64, 6, True, 1e-10), (200, 8, True, 1e-9)])
 def test_factor_diagonalises(m, seed, cluster, tau):
