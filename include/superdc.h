@@ -43,7 +43,9 @@ typedef enum {
 /* Device status word bits (written by kernels, OR-ed). */
 #define SUPERDC_DEV_NONFINITE 1
 #define SUPERDC_DEV_NOCONV    2
-#define SUPERDC_DEV_INDEX     4
+#define SUPERDC_DEV_INDEX     4   /* checked build only (-DSUPERDC_CHECK, libsuperdc_check.so): an index
+                                   read from device data (a near-list box, a kept count) was out of
+                                   range; the access used 0 instead; reported as SUPERDC_ERR_CUDA */
 
 typedef struct {
     double  tau;          /* deflation tolerance of Remark 4.1 (absolute; strict '<' tests) */

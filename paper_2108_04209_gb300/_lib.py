@@ -47,10 +47,12 @@ _lib = None
 
 
 def lib():
-    """Load (building in-tree if needed) the CUDA library."""
+    """Load (building in-tree if needed) the CUDA library; with the
+    environment variable SUPERDC_CHECKED=1 the checked build (index guards
+    latch SUPERDC_DEV_INDEX, reported as SUPERDC_ERR_CUDA)."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _build.build(check=os.environ.get("SUPERDC_CHECKED", "0") == "1")
         if not os.path.exists(path):
             raise RuntimeError("libsuperdc.so missing at %s" % path)
         L = ctypes.CDLL(path)

@@ -39,18 +39,23 @@ def _stamp():
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(OUT, exist_ok=True)
-    stamp = _stamp()
-    sf = os.path.join(OUT, "stamp")
-    if not force and os.path.exists(LIB) and os.path.exists(sf) and open(sf).read() == stamp:
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra=(), check: bool = False) -> str:
+    """Compile and link the library; check=True makes the checked variant
+    _lib/libsuperdc_check.so (-DSUPERDC_CHECK: data-dependent indexes are
+    tested and latch SUPERDC_DEV_INDEX instead of being used out of range)."""
+    out = os.path.join(OUT, "check") if check else OUT
+    lib_path = os.path.join(OUT, "libsuperdc_check.so") if check else LIB
+    os.makedirs(out, exist_ok=True)
+    stamp = _stamp() + (" check" if check else "")
+    sf = os.path.join(out, "stamp")
+    if not force and os.path.exists(lib_path) and os.path.exists(sf) and open(sf).read() == stamp:
+        return lib_path
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC,
-                    "--expt-relaxed-constexpr"] + list(extra)
+                    "--expt-relaxed-constexpr"] + (["-DSUPERDC_CHECK"] if check else []) + list(extra)
     objs = []
 
     def comp(src):
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc(), "-c", src, "-o", obj] + flags
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -63,16 +68,16 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(comp, _sources()))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib_path + ".%d.tmp" % os.getpid()
     cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     open(sf, "w").write(stamp)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [], check="--check" in sys.argv))

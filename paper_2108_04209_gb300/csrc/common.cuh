@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <vector>
 #include "superdc.h"
+#include "check.cuh"
 
 #define SDC_EPS 2.220446049250313080847263336181640625e-16   // 2^-52
 

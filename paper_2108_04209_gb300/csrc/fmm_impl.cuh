@@ -127,6 +127,12 @@ __device__ __forceinline__ int near_box(const FmmDev &pl, int64_t g, int nn, int
 {
     return nn < 0 ? i : pl.near[pl.nstart[g] + i];
 }
+// a near box of a consumer kernel: in the checked build the list entry is
+// tested against the problem's leaf box count nb0 (latched into word)
+__device__ __forceinline__ int near_box_chk(const FmmDev &pl, int64_t g, int nn, int i, int nb0, int32_t *word)
+{
+    return SDC_IDX(near_box(pl, g, nn, i), nb0, word);
+}
 
 // Chebyshev nodes x_q = cos((2q+1) pi / 2P) and T_n(x_q) (Tx[q * P + n], by
 // the three-term recurrence, one row per thread); the caller synchronises
@@ -1031,7 +1037,7 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
         int near_terms = 0;
         __syncwarp();
         for (int i = 0; i < nn; i++) {
-            const int j0 = near_box(pl, g, nnr, i) * B;
+            const int j0 = near_box_chk(pl, g, nnr, i, (m + B - 1) / B, o.status) * B;
             const int cnt = min(B, m - j0);
             near_terms += cnt;
             for (int jj = lane; jj < cnt; jj += 32) {
@@ -1073,7 +1079,7 @@ k_secular_fmm(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_c
                 A.dphi = fma(uu, e1, cf[3 * P] - e2);
             }
             for (int i = 0; i < nn; i++) {
-                const int j0 = near_box(pl, g, nnr, i) * B;
+                const int j0 = near_box_chk(pl, g, nnr, i, (m + B - 1) / B, o.status) * B;
                 const int cnt = min(B, m - j0);
                 const double *bd = sd[warp] + i * B, *bw = sw[warp] + i * B;
                 if (p0) sweep<false>(bd, bw, 0, cnt, j0, kk, kwlo, kwhi, R.dK, R.y, A);
@@ -1181,7 +1187,7 @@ k_secular_tail(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double stop_
         Acc A = {0.0, 0.0, 0.0, 0.0};
         if (act) {
             for (int i = 0; i < nn; i++) {
-                const int j0 = near_box(pl, g, nnr, i) * B;
+                const int j0 = near_box_chk(pl, g, nnr, i, (m + B - 1) / B, o.status) * B;
                 const int cnt = min(B, m - j0);
                 const double *dd = o.dk + b0 + j0, *zz = o.zk + b0 + j0;
                 for (int jj = part; jj < cnt; jj += TAIL_LANES) {
@@ -1291,7 +1297,7 @@ k_secular_fmm_split(FmmDev pl, const int64_t *__restrict__ off, R1Out o, double 
                     A.dphi = clenshaw(cf + 3 * P, uu);
                 }
                 for (int i = warp; i < nn; i += SPW) {
-                    const int S = near_box(pl, g, nnr, i);
+                    const int S = near_box_chk(pl, g, nnr, i, (m + B - 1) / B, o.status);
                     const int j0 = S * B;
                     const int cnt = min(B, m - j0);
                     __syncwarp();
@@ -1529,7 +1535,7 @@ __global__ void __launch_bounds__(B) k_lowner_fmm(FmmDev pl, const int64_t *__re
         const int nn = near_len(nnr, (m + B - 1) / B);
         int64_t nsrc = 0;
         for (int s = 0; s < nn; s++) {
-            const int S = near_box(pl, g, nnr, s);
+            const int S = near_box_chk(pl, g, nnr, s, (m + B - 1) / B, o.status);
             const int j0 = S * B;
             const int cnt = min(B, (m - 1) - j0);
             nsrc += max(cnt, 0);
@@ -1592,7 +1598,7 @@ __global__ void __launch_bounds__(B) k_bnorm_fmm(FmmDev pl, const int64_t *__res
         const int nn = near_len(nnr, (m + B - 1) / B);
         int64_t nsrc = 0;
         for (int q = 0; q < nn; q++) {
-            const int S = near_box(pl, g, nnr, q);
+            const int S = near_box_chk(pl, g, nnr, q, (m + B - 1) / B, o.status);
             const int i0 = S * B;
             const int cnt = min(B, m - i0);
             nsrc += max(cnt, 0);

@@ -739,7 +739,7 @@ __global__ void k_merge(int64_t nprob, const int64_t *__restrict__ off, int64_t 
         const int64_t p = sdc_upper_index(off, nprob, x);
         const int64_t b0 = off[p];
         const int m = (int)(off[p + 1] - b0);
-        const int mk = o.mk[p];
+        const int mk = SDC_IDX(o.mk[p], m + 1, o.status);       // kept count in [0, m]
         const int s = (int)(x - b0);
         const double *dk = o.dk + b0, *dorg = o.dorg + b0, *eta = o.eta + b0;
         const int32_t *src = o.src + b0;
