@@ -299,6 +299,9 @@ extern "C" superdc_status superdc_secular_batched_backward(
     f.nprob = nprob; f.off = offsets; f.mk = fwd->mk; f.ngiv = fwd->ngiv; f.dk = fwd->dk; f.eta = fwd->eta;
     f.dorg = dorg; f.vhat = fwd->vhat; f.bnorm = fwd->bnorm; f.src = fwd->src; f.perm = fwd->perm; f.pinv = pinv;
     f.giv_ab = fwd->giv_ab; f.giv_cs = fwd->giv_cs;
+#ifdef SUPERDC_CHECK
+    f.status = fwd->status;
+#endif
     return r1_backward_fv(f, total, lam_bar, (int)ncols, X, ldx, Ybar, ldy, d_bar, z_bar, X_bar, ldxb, sqrt(rho), st);
 }
 
@@ -327,6 +330,9 @@ extern "C" superdc_status superdc_rank1_apply(int64_t nprob, const int64_t *offs
     f.nprob = nprob; f.off = offsets; f.mk = fwd->mk; f.ngiv = fwd->ngiv; f.dk = fwd->dk; f.eta = fwd->eta;
     f.dorg = dorg; f.vhat = fwd->vhat; f.bnorm = fwd->bnorm; f.src = fwd->src; f.perm = fwd->perm; f.pinv = pinv;
     f.giv_ab = fwd->giv_ab; f.giv_cs = fwd->giv_cs;
+#ifdef SUPERDC_CHECK
+    f.status = fwd->status;
+#endif
     f.fmm_min_m = fmm_resolve(opts->fmm_min_m);
     superdc_status s;
     if (trans) {

@@ -137,7 +137,7 @@ k_cauchy_T(FactorView f, const int64_t *__restrict__ tile_off, const double *__r
             const int cn = min(TI, m - i0);
             __syncthreads();
             for (int ii = threadIdx.x; ii < cn; ii += TJ) {
-                const int64_t row = b0 + f.src[b0 + i0 + ii];
+                const int64_t row = b0 + SDC_IDX(f.src[b0 + i0 + ii], f.off[p + 1] - b0, f.status);
                 const double v = f.vhat[b0 + i0 + ii];
                 sd[ii] = f.dk[b0 + i0 + ii];
 #pragma unroll
@@ -155,7 +155,7 @@ k_cauchy_T(FactorView f, const int64_t *__restrict__ tile_off, const double *__r
         }
         if (act) {
             const double bj = f.bnorm[b0 + j];
-            const int64_t row = b0 + f.pinv[b0 + j];
+            const int64_t row = b0 + SDC_IDX(f.pinv[b0 + j], f.off[p + 1] - b0, f.status);
 #pragma unroll
             for (int q = 0; q < NC; q++)
                 if (q < nc) Y[row + (int64_t)(col0 + q) * ldy] = bj * acc[q];
@@ -188,7 +188,7 @@ k_cauchy_N(FactorView f, const int64_t *__restrict__ tile_off, const double *__r
             const int cn = min(TI, m - j0);
             __syncthreads();
             for (int jj = threadIdx.x; jj < cn; jj += TJ) {
-                const int64_t row = b0 + f.pinv[b0 + j0 + jj];
+                const int64_t row = b0 + SDC_IDX(f.pinv[b0 + j0 + jj], f.off[p + 1] - b0, f.status);
                 const double bj = f.bnorm[b0 + j0 + jj];
                 sk[jj] = f.dorg[b0 + j0 + jj];
                 se[jj] = f.eta[b0 + j0 + jj];
@@ -207,7 +207,7 @@ k_cauchy_N(FactorView f, const int64_t *__restrict__ tile_off, const double *__r
         }
         if (act) {
             const double v = f.vhat[b0 + i];
-            const int64_t row = b0 + f.src[b0 + i];
+            const int64_t row = b0 + SDC_IDX(f.src[b0 + i], f.off[p + 1] - b0, f.status);
 #pragma unroll
             for (int q = 0; q < NC; q++)
                 if (q < nc) Y[row + (int64_t)(col0 + q) * ldy] = v * acc[q];
@@ -228,8 +228,10 @@ __global__ void k_defl_copy(FactorView f, int64_t total, const double *__restric
         const int64_t b0 = f.off[p];
         const int s = (int)(slotg - b0);
         if (s < f.mk[p]) continue;
-        if (trans) Y[b0 + f.pinv[slotg] + (int64_t)col * ldy] = X[b0 + f.src[slotg] + (int64_t)col * ldx];
-        else       Y[b0 + f.src[slotg] + (int64_t)col * ldy] = X[b0 + f.pinv[slotg] + (int64_t)col * ldx];
+        const int64_t ps = SDC_IDX(f.pinv[slotg], f.off[p + 1] - b0, f.status);
+        const int64_t sr = SDC_IDX(f.src[slotg], f.off[p + 1] - b0, f.status);
+        if (trans) Y[b0 + ps + (int64_t)col * ldy] = X[b0 + sr + (int64_t)col * ldx];
+        else       Y[b0 + sr + (int64_t)col * ldy] = X[b0 + ps + (int64_t)col * ldx];
     }
 }
 

@@ -16,6 +16,9 @@ struct FactorView {
     const double *giv_cs;
     int32_t fmm_min_m = 0;   // kept size from which a problem takes the FMM path (0: direct only)
     int64_t max_m = -1;      // upper bound on the problem sizes (-1: unknown)
+#ifdef SUPERDC_CHECK
+    int32_t *status = nullptr;   // device status word of the index guards (checked build)
+#endif
 };
 
 struct FmmPlan;

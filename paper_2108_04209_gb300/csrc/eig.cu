@@ -840,6 +840,9 @@ FactorView view(const superdc_eigfact *f, int l, int j)
     v.dk = S.dk; v.eta = S.eta; v.dorg = S.dorg; v.vhat = S.vhat; v.bnorm = S.bnorm;
     v.src = S.src; v.perm = nullptr; v.pinv = S.pinv; v.giv_ab = S.giv_ab; v.giv_cs = S.giv_cs;
     v.fmm_min_m = f->fmm_min_m;
+#ifdef SUPERDC_CHECK
+    v.status = f->status;
+#endif
     int64_t mx = 0;
     for (int i : h->lev_nodes[l]) mx = std::max<int64_t>(mx, h->size[i]);
     v.max_m = mx;
@@ -1516,6 +1519,9 @@ static superdc_status leaf_dc_run(superdc_eigfact *f, cudaStream_t st)
         fv.eta = w.dc_o.eta; fv.dorg = w.dc_o.dorg; fv.vhat = w.dc_o.vhat; fv.bnorm = w.dc_o.bnorm;
         fv.src = w.dc_o.src; fv.perm = w.dc_o.perm; fv.pinv = w.dc_o.pinv; fv.giv_ab = w.dc_o.giv_ab;
         fv.giv_cs = w.dc_o.giv_cs; fv.fmm_min_m = 0; fv.max_m = sz;
+#ifdef SUPERDC_CHECK
+        fv.status = w.dc_o.status;
+#endif
         s = cauchy_apply_T(fv, n, w.dc_X, n, Yout, n, sz, st);
         if (s != SUPERDC_OK) return s;
         std::swap(Yin, Yout);

@@ -1705,7 +1705,7 @@ k_cauchyT_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
         const int nn = near_len(nnr, (m + B - 1) / B);
         int64_t nsrc = 0;
         for (int s = 0; s < nn; s++) {
-            const int S = near_box(pl, g, nnr, s);
+            const int S = SDC_IDX(near_box(pl, g, nnr, s), (m + B - 1) / B, f.status);
             const int i0 = S * B;
             const int cnt = min(B, m - i0);
             nsrc += max(cnt, 0);
@@ -1807,7 +1807,7 @@ k_cauchyN_fmm(FmmDev pl, FactorView f, const double *__restrict__ X, int64_t ldx
         const int nn = near_len(nnr, (m + B - 1) / B);
         int64_t nsrc = 0;
         for (int s = 0; s < nn; s++) {
-            const int S = near_box(pl, g, nnr, s);
+            const int S = SDC_IDX(near_box(pl, g, nnr, s), (m + B - 1) / B, f.status);
             const int j0 = S * B;
             const int cnt = min(B, (m - 1) - j0);
             nsrc += max(cnt, 0);

@@ -67,7 +67,7 @@ def test_guard_macro_is_identity_unchecked(tmp_path):
     assert out[5] == "7 5"          # the default build uses the index as it is
 
 
-@pytest.mark.parametrize("unit", ["rank1.cu", "fmm32.cu"])
+@pytest.mark.parametrize("unit", ["rank1.cu", "fmm32.cu", "cauchy.cu"])
 def test_checked_units_compile(tmp_path, unit):
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
